@@ -1,0 +1,278 @@
+"""Per-cell reduced-order models and their matrix S-fraction coefficients.
+
+Steps (Algorithm alg1red, stage 1):
+ (0) face bases S_f (Section 4.1);
+ (1.1) projection subspace V_m and projected pencil A^m, B^m = I, S^m (Eq. npks, Eq. tfprj);
+ (1.2) block Lanczos of (A^m, S^m) to block-tridiagonal (T, R) (Appendix C, Eq. NtDtri);
+ (1.3) S-fraction coefficients Gamma^k, Gamma-hat^k by the block-diagonal change of
+       variables (Eq. GammaTrans);
+ (1.4) projected sources/receivers g~_f = S_f^T g|_f, q~_f = S_f^T q|_f (Eq. BEINCr, Eq. solatrec),
+ plus the face masses M_f of Eq. bdrytstep.
+
+Readings (where the paper is silent, garbled or inconsistent):
+* Face basis: the paper's POD/Gramian basis depends on a method it leaves to a
+  missing reference.  Here S_f holds the lowest-wavenumber discrete cosine (DCT-II)
+  modes of the face's node grid, Euclidean-orthonormal by construction (S_f^T S_f = I),
+  ordered by (a/n1)^2 + (b/n2)^2 then (a, b); these are the Neumann modes of a
+  uniform face and do not depend on the medium.  I/O faces keep S_f = I.
+* Krylov subspace (Eq. npks): the pencil form with K = (A+sB)^{-1} B and the
+  zero-power block B^{-1} P S (Remark Sinsubspace), i.e. the block Krylov space
+  span{B^{-1}C, K B^{-1}C, ..., K^{m-1} B^{-1}C}, C = P^Gamma S; note K B^{-1} C =
+  (A+sB)^{-1} C, so it holds (A+sB)^{-1}C, ..., and makes Gamma-hat^1 = C^T B^{-1} C
+  exact and block-diagonal over faces.  Built block by block (the paper's "block
+  Lanczos iteration" remark) with B-inner-product Gram-Schmidt, two passes.
+* Shift: s = -omega_max^2.
+* GammaTrans: the printed recursion is not symmetric; the symmetric form that
+  makes F~ = U^1 of Eq. GammaU1st/GammaUrem exact is used:
+      G_1 = beta_1^T,  Gamma^0 = 0,
+      Gamma-hat^k = G_k G_k^T,
+      Gamma^k = -G_k^{-T} alpha_k G_k^{-1} - Gamma^{k-1},
+      G_{k+1} = (G_k^T Gamma^k)^{-1} beta_{k+1}^T,
+  with beta from QR (positive diagonal).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from synth import RomCoefficients, RomTopology
+
+
+class RomError(RuntimeError):
+    """A failed precondition of the construction (deflation, breakdown, non-SPD)."""
+
+
+# --------------------------------------------------------------------------- face bases
+def dct_modes(n: int) -> np.ndarray:
+    """Orthonormal DCT-II vectors on n points: column a is c_a cos(pi a (j + 1/2) / n)."""
+    j = np.arange(n)[:, None]
+    a = np.arange(n)[None, :]
+    c = np.where(a == 0, np.sqrt(1.0 / n), np.sqrt(2.0 / n))
+    return c * np.cos(np.pi * a * (j + 0.5) / n)
+
+
+def face_mode_order(shape: Sequence[int]):
+    """Mode indices of a face grid, lowest tangential wavenumber first."""
+    if len(shape) == 0:
+        return [()]
+    if len(shape) == 1:
+        return [(a,) for a in range(shape[0])]
+    n1, n2 = shape
+    modes = [(a, b) for a in range(n1) for b in range(n2)]
+    modes.sort(key=lambda ab: (ab[0] * ab[0] * n2 * n2 + ab[1] * ab[1] * n1 * n1, ab[0], ab[1]))
+    return modes
+
+
+def face_basis(face, n_modes: int) -> np.ndarray:
+    """S_f (K_f x M_f) with S_f^T S_f = I (Section 4.1; see module readings)."""
+    K = len(face.nodes)
+    if face.kind == "io":
+        return np.eye(K)
+    shape = face.shape
+    M = min(n_modes, K)
+    order = face_mode_order(shape)[:M]
+    if len(shape) == 0:
+        return np.ones((1, 1))
+    if len(shape) == 1:
+        return dct_modes(shape[0])[:, [o[0] for o in order]]
+    p1, p2 = dct_modes(shape[0]), dct_modes(shape[1])
+    return np.stack([np.kron(p1[:, a], p2[:, b]) for (a, b) in order], axis=1)
+
+
+# --------------------------------------------------------------------------- Krylov ROM (Eq. npks, tfprj)
+def _b_orthonormalize(Y: np.ndarray, Bd: np.ndarray, prev: List[np.ndarray], scale: float) -> np.ndarray:
+    """Two-pass block Gram-Schmidt in the B inner product, then B-orthonormal basis of the block."""
+    for _ in range(2):
+        for Vp in prev:
+            Y = Y - Vp @ (Vp.T @ (Bd[:, None] * Y))
+    G = Y.T @ (Bd[:, None] * Y)
+    G = 0.5 * (G + G.T)
+    ev = np.linalg.eigvalsh(G)
+    if ev[0] <= 1e-20 * max(scale, ev[-1]):
+        raise RomError("Krylov deflation: block is (numerically) linearly dependent (Assumption ass1)")
+    R = np.linalg.cholesky(G).T
+    return sla.solve_triangular(R, Y.T, trans="T", lower=False).T
+
+
+def krylov_rom(A: sp.spmatrix, Bd: np.ndarray, C: np.ndarray, m: int, s: float):
+    """B-orthonormal basis V of span{B^{-1}C, K B^{-1}C, .., K^{m-1} B^{-1}C}, K=(A+sB)^{-1}B.
+
+    Returns V (N x mK), A^m = V^T A V, S^m = V^T C  (B^m = V^T B V = I).
+    """
+    N, K = C.shape
+    if m * K > N:
+        raise RomError("m * K exceeds the cell size")
+    lu = spla.splu((A + s * sp.diags(Bd)).tocsc())
+    X = C / Bd[:, None]
+    blocks: List[np.ndarray] = []
+    scale = float(np.max(np.abs(X.T @ (Bd[:, None] * X))))
+    for j in range(m):
+        if j > 0:
+            X = lu.solve(Bd[:, None] * blocks[-1])
+            scale = float(np.max(np.abs(X.T @ (Bd[:, None] * X))))
+        blocks.append(_b_orthonormalize(X, Bd, blocks, scale))
+    V = np.hstack(blocks)
+    Am = V.T @ (A @ V)
+    Am = 0.5 * (Am + Am.T)
+    Sm = V.T @ C
+    return V, Am, Sm
+
+
+# --------------------------------------------------------------------------- block Lanczos (Appendix C)
+def _qr_pos(W: np.ndarray):
+    """QR with a positive diagonal of R."""
+    Q, R = np.linalg.qr(W)
+    sgn = np.sign(np.diag(R))
+    sgn[sgn == 0] = 1.0
+    return Q * sgn, sgn[:, None] * R
+
+
+def block_lanczos(Am: np.ndarray, Sm: np.ndarray, m: int):
+    """Block tridiagonal form T = Q^T A^m Q, R = Q^T S^m = [beta_1, 0, ..]^T (Eq. NtDtri).
+
+    Returns (alpha[0..m-1], beta[0..m-1]) with alpha[k] = alpha_{k+1}, beta[k] = beta_{k+1};
+    A^m Q_k = Q_{k-1} beta_k^T + Q_k alpha_k + Q_{k+1} beta_{k+1}; full reorthogonalisation.
+    """
+    K = Sm.shape[1]
+    Q1, b1 = _qr_pos(Sm)
+    Qs = [Q1]
+    alphas, betas = [], [b1]
+    nrm = max(np.linalg.norm(Am, 2), 1e-300)
+    for k in range(m):
+        Qk = Qs[k]
+        W = Am @ Qk
+        if k > 0:
+            W = W - Qs[k - 1] @ betas[k].T
+        a = Qk.T @ W
+        a = 0.5 * (a + a.T)
+        alphas.append(a)
+        if k == m - 1:
+            break
+        W = W - Qk @ a
+        for _ in range(2):
+            for Qj in Qs:
+                W = W - Qj @ (Qj.T @ W)
+        Qn, bn = _qr_pos(W)
+        if np.min(np.abs(np.diag(bn))) < 1e-13 * nrm:
+            raise RomError("block Lanczos breakdown")
+        Qs.append(Qn)
+        betas.append(bn)
+    return alphas, betas
+
+
+# --------------------------------------------------------------------------- S-fraction coefficients (Eq. GammaTrans)
+def gamma_trans(alphas: List[np.ndarray], betas: List[np.ndarray]):
+    """Gamma^k, Gamma-hat^k (k = 1..m) from the block Lanczos coefficients (module readings)."""
+    m = len(alphas)
+    G = betas[0].T.copy()
+    Gprev = np.zeros_like(G)
+    gam, gh = [], []
+    for k in range(m):
+        Gh = G @ G.T
+        Gi = np.linalg.inv(G)
+        Gk = -Gi.T @ alphas[k] @ Gi - Gprev
+        Gk = 0.5 * (Gk + Gk.T)
+        Gh = 0.5 * (Gh + Gh.T)
+        for M, nm in ((Gk, "Gamma"), (Gh, "Gamma-hat")):
+            try:
+                np.linalg.cholesky(M)
+            except np.linalg.LinAlgError:
+                raise RomError("%s^%d is not SPD" % (nm, k + 1))
+        gam.append(Gk)
+        gh.append(Gh)
+        if k + 1 < m:
+            G = np.linalg.solve(G.T @ Gk, betas[k + 1].T)
+        Gprev = Gk
+    return gam, gh
+
+
+# --------------------------------------------------------------------------- whole-partition build
+@dataclasses.dataclass
+class CellRom:
+    gamma: List[np.ndarray]
+    gamma_hat: List[np.ndarray]
+    V: Optional[np.ndarray] = None
+    Am: Optional[np.ndarray] = None
+    Sm: Optional[np.ndarray] = None
+    C: Optional[np.ndarray] = None
+
+
+@dataclasses.dataclass
+class Rom:
+    """Everything the on-line stage needs, plus the face bases for projections."""
+
+    topology: RomTopology
+    coeffs: RomCoefficients
+    bases: List[np.ndarray]
+    cells: Dict[int, CellRom]
+
+
+def cell_input_matrix(part, cid: int, bases: List[np.ndarray]) -> np.ndarray:
+    """C = P^Gamma S_i: block-diagonal face bases on the cell's boundary rows, zero inside."""
+    c = part.build_cell(cid)
+    M = sum(bases[f].shape[1] for f in c.faces)
+    C = np.zeros((len(c.nodes), M))
+    r = o = 0
+    for f in c.faces:
+        S = bases[f]
+        C[r:r + S.shape[0], o:o + S.shape[1]] = S
+        r += S.shape[0]
+        o += S.shape[1]
+    return C
+
+
+def build_cell_rom(part, cid: int, bases: List[np.ndarray], m: int, s: float, keep=False) -> CellRom:
+    c = part.build_cell(cid)
+    C = cell_input_matrix(part, cid, bases)
+    V, Am, Sm = krylov_rom(c.A, c.B, C, m, s)
+    al, be = block_lanczos(Am, Sm, m)
+    gam, gh = gamma_trans(al, be)
+    if keep:
+        return CellRom(gam, gh, V, Am, Sm, C)
+    return CellRom(gam, gh)
+
+
+def face_masses(part, bases, cell_roms: Dict[int, CellRom]) -> List[np.ndarray]:
+    """M_f = sum_{i ∋ f} (Gamma-hat^1_{i,f})^{-1} (Eq. bdrytstep), the f-block of Gamma-hat^1_i."""
+    out = []
+    for f in part.faces:
+        M = np.zeros((bases[f.id].shape[1],) * 2)
+        for c in f.cells:
+            o = 0
+            for g in part.cells[c].faces:
+                if g == f.id:
+                    break
+                o += bases[g].shape[1]
+            mf = bases[f.id].shape[1]
+            blk = cell_roms[c].gamma_hat[0][o:o + mf, o:o + mf]
+            M += np.linalg.inv(blk)
+        out.append(0.5 * (M + M.T))
+    return out
+
+
+def build_rom(part, m, n_modes: int, s: float, keep=False) -> Rom:
+    """All cells (m scalar or per cell) -> topology, coefficients and face bases."""
+    bases = [face_basis(f, n_modes) for f in part.faces]
+    ms = [int(m)] * len(part.cells) if np.isscalar(m) else [int(x) for x in m]
+    cells = {c.id: build_cell_rom(part, c.id, bases, ms[c.id], s, keep) for c in part.cells}
+    fm = face_masses(part, bases, cells)
+    topo = RomTopology(np.array(ms, dtype=np.int64), [list(c.faces) for c in part.cells],
+                       np.array([b.shape[1] for b in bases], dtype=np.int64),
+                       [list(f.cells) for f in part.faces])
+    coeffs = RomCoefficients([cells[i].gamma for i in range(len(part.cells))],
+                             [cells[i].gamma_hat for i in range(len(part.cells))], fm)
+    return Rom(topo, coeffs, bases, cells)
+
+
+def project_io(part, bases: List[np.ndarray], vectors: np.ndarray) -> List[np.ndarray]:
+    """Per face S_f^T v|_f for prime-space columns v (Eq. BEINCr g~ and Eq. solatrec q~): (M_f, n)."""
+    return [bases[f.id].T @ vectors[f.nodes, :] for f in part.faces]
+
+
+def omega_max(f_max: float) -> float:
+    return 2.0 * np.pi * f_max
