@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the on-line stage: ROM source·cell-steps per second on one GPU.
+
+Workload: the 3D layered acoustic medium of 128^3 voxels (Neumann top, Dirichlet elsewhere,
+4 layers, lognormal perturbations), 512 coarse cells of 16^3 voxels, m = 4 S-fraction layers,
+15 DCT modes per interior face, 16 surface sources, 128 surface receivers, 4000 leapfrog steps
+at half the fine-grid CFL limit.  One bench step = one whole on-line simulation of that batch
+(512 cells x 16 sources x 4000 time steps), state reset at its start.
+
+Reported beside the headline (FP32 stepping with the Appendix D corner correction):
+FP64 stepping, the same GPU's fine-grid leapfrog (FP32), receiver-trace differences, the
+off-line build time, per-kernel roofline, the oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = dict(n=128, cell=16, m=4, n_modes=15, n_src=16, n_steps=4000)
+METRIC = "online ROM source·cell-steps/s vs fine-grid stencil at ≤1e-3 receiver error"
+UNIT = "source·cell-steps/s"
+
+
+def _workload():
+    return synth.workload_3d_layers(WORKLOAD["n"], WORKLOAD["cell"], m=WORKLOAD["m"], n_modes=WORKLOAD["n_modes"],
+                                    n_src=WORKLOAD["n_src"], n_steps=WORKLOAD["n_steps"])
+
+
+def _config(wl, extra=None):
+    nc = int(np.prod([wl.grid.n[a] // wl.cell[a] for a in range(3)]))
+    c = {"workload": "3d_layers_128: 128^3 voxels, %d cells of 16^3, m=%d, %d modes/face, %d sources, "
+                     "%d receivers, %d steps" % (nc, wl.m, wl.n_modes, len(wl.src_nodes), len(wl.rcv_nodes),
+                                                  wl.n_steps),
+         "cells": nc, "sources": int(len(wl.src_nodes)), "receivers": int(len(wl.rcv_nodes)),
+         "time_steps": int(wl.n_steps), "layers": wl.m, "face_modes": wl.n_modes}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_rate(n_src: int, n_steps_sample: int):
+    """The oracle's ROM leapfrog on the workload's cell/face shapes (random SPD coefficients of
+    the same sizes; the timing does not depend on the values), all cells and sources, a bounded
+    number of time steps.  Returns (rate in source·cell-steps/s, seconds, cells)."""
+    from oracle import online
+    io_cells = [(c, 2) for c in range(7 * 64, 8 * 64)]           # one 2-node I/O face per top cell
+    topo = synth.box_topology((8, 8, 8), modes=WORKLOAD["n_modes"], m=WORKLOAD["m"], io_cells=io_cells, seed=7)
+    co = synth.random_coefficients(topo, seed=7)
+    src, rcv = synth.random_io(topo, n_src, 8, seed=7, density=0.02)
+    gt = online.dense_io(topo, src, n_src, "src")
+    qt = online.dense_io(topo, rcv, 8, "rcv")
+    w = synth.ricker(np.arange(n_steps_sample) * 0.05, 1.0)
+    t0 = time.perf_counter()
+    online.rom_leapfrog(topo, co, gt, qt, w, 0.05, n_steps_sample)
+    dt = time.perf_counter() - t0
+    return topo.n_cells * n_src * n_steps_sample / dt, dt, topo.n_cells
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = _workload()
+    n_src = len(wl.src_nodes)
+    sample = 20
+    times = []
+    for _ in range(args.warmup):
+        oracle_rate(n_src, 5)
+    for _ in range(args.steps):
+        rate, dt, nc = oracle_rate(n_src, sample)
+        times.append(dt)
+    units = nc * n_src * sample
+    value = units / statistics.mean(times)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(wl, {"precision": "fp64 (oracle, numpy)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "all %d cells x %d sources x %d time steps per bench step" % (nc, n_src, sample)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- native
+def _kernel_model(rom_info, topo_K, topo_m, n_src, es):
+    """Algorithmic bytes and flops of one cell-kernel launch (one time step, all cells)."""
+    byts = flops = 0.0
+    for K, m in zip(topo_K, topo_m):
+        coef = (2 * m - 1) * K * K * es                         # Gamma^1..m, Gamma-hat^2..m, read once
+        state = (K + 3 * (m - 1) * K + K) * n_src * es           # U^1 gather, U^k, U^k_old, U^k_new, F^1 out
+        byts += coef + state
+        flops += 2.0 * (2 * m - 1) * K * K * n_src
+    return byts, flops
+
+
+def _traffic_record(kernel_src: str):
+    """ncu DRAM bytes per launch of the cell kernel, if recorded for this exact kernel source."""
+    path = os.path.join(ROOT, "profiles", "cell_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return rec.get("bytes_per_launch") if rec.get("source_sha256") == sha else None
+
+
+def run_native(args):
+    import torch
+    import paper_1604_06750_gb300 as P
+    from paper_1604_06750_gb300 import build as B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    P.lib()
+    wl = _workload()
+    dev = torch.device("cuda", local)
+    # ---- off-line (not timed in the metric)
+    t0 = time.perf_counter()
+    L = P.Operator(wl.grid, wl.sigma, wl.rho)
+    io = np.concatenate([wl.src_nodes, wl.rcv_nodes]).astype(np.int32)
+    LP = P.Partition(L, wl.cell, io)
+    lam = L.lambda_max(1e-7)
+    tau = wl.cfl_fraction * 2.0 / math.sqrt(lam)
+    s = -(2 * math.pi * wl.f_max) ** 2
+    t1 = time.perf_counter()
+    LR = P.Rom.build(LP, wl.m, wl.n_modes, s, cg_tol=1e-12)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    LR.set_io_nodes(LP, wl.src_nodes, wl.rcv_nodes)
+    cm, cfp, cf, fM, fc, _, _, _ = LR.export()
+    Ks = [int(sum(fM[cf[cfp[c]:cfp[c + 1]]])) for c in range(len(cm))]
+    nst, S, R = wl.n_steps, len(wl.src_nodes), len(wl.rcv_nodes)
+    ncell = len(cm)
+    units = ncell * S * nst
+    w = synth.ricker(np.arange(nst) * tau, wl.f_peak)
+    wd = torch.tensor(w, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sim = P.Sim(LR, P.FP32, tau, corner_correction=True)
+    kper = int(sim.info()[6])
+    tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+    flush = torch.empty(int(512e6) // 4, device=dev, dtype=torch.float32)
+    # ---- warm-up (captures the CUDA graph)
+    for _ in range(args.warmup):
+        sim.reset()
+        sim.step(nst, wd, tr, use_graph=True)
+    torch.cuda.synchronize()
+    # ---- timed region
+    clocks = Clocks(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                                    # L2 flush between bench steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.reset()
+        sim.step(nst, wd, tr, use_graph=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    t_step = statistics.mean(times)
+    if dist:
+        t = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = world * units / t_step
+    tr32 = tr.double().cpu().numpy()
+    # ---- per-kernel timing (eager, CUDA events on the launching stream)
+    sim.reset()
+    prof_steps = 400
+    ms = sim.step_profile(prof_steps, wd, tr)
+    _, algo_flops = _kernel_model(None, Ks, cm, S, 4)
+    algo_bytes, _ = _kernel_model(None, Ks, cm, S, 4)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12             # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
+    cell_s = ms[0] / 1e3
+    achieved_gbs = algo_bytes / cell_s / 1e9
+    achieved_tf = algo_flops / cell_s / 1e12
+    ridge = alu_peak * 1e12 / (hbm * 1e9)
+    intensity = algo_flops / algo_bytes
+    traffic = _traffic_record(os.path.join(ROOT, "paper_1604_06750_gb300", "csrc", "online.cu"))
+    if intensity < ridge:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                "traffic": traffic}
+    else:
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / alu_peak, "traffic": traffic}
+    roof.update({"kernel": "k_cell<float,16>", "algorithmic_bytes_per_launch": algo_bytes,
+                 "algorithmic_flops_per_launch": algo_flops, "intensity_flop_per_byte": intensity,
+                 "ms_per_launch": ms[0], "fp32_alu_frac": achieved_tf / alu_peak,
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
+                 "other_kernels_ms": {"k_face": ms[1], "k_corner": ms[2]}})
+    # ---- FP64 stepping (same coefficients), one run
+    sim64 = P.Sim(LR, P.FP64, tau, corner_correction=True)
+    tr64 = torch.zeros((nst, R, S), device=dev, dtype=torch.float64)
+    sim64.step(nst, wd, tr64, use_graph=True)
+    torch.cuda.synchronize()
+    sim64.reset()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim64.step(nst, wd, tr64, use_graph=True)
+    e1.record(stream)
+    e1.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    ref64 = tr64.cpu().numpy()
+    # ---- fine-grid leapfrog on the same GPU (FP32), same tau and steps
+    fine = P.FineSim(L, P.FP32, tau, wl.src_nodes, wl.rcv_nodes)
+    trf = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+    fine.step(nst, wd, trf, use_graph=True)
+    torch.cuda.synchronize()
+    fine.reset()
+    flush.fill_(1.0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fine.step(nst, wd, trf, use_graph=True)
+    e1.record(stream)
+    e1.synchronize()
+    tfine = e0.elapsed_time(e1) / 1e3
+    fine_tr = trf.double().cpu().numpy()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    # ---- end to end through the C ABI with host buffers (H2D waveform, D2H traces)
+    e2e_times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        host_tr = sim.run_host(w)
+        e2e_times.append(time.perf_counter() - a)
+    e2e = {"value": world * units / statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": int(w.nbytes),
+           "d2h_bytes_per_step": int(host_tr.nbytes)}
+    # ---- oracle on the host cores, bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1:
+        rate, dt, nc = oracle_rate(S, 20)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "all %d cells x %d sources x 20 time steps (numpy, random SPD coefficients of the "
+                         "workload's block sizes)" % (nc, S)}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(wl, {"precision": "fp32 state and coefficients", "corner_correction": True,
+                                   "l2": "flushed between steps (512 MB write)",
+                                   "parallelism": "independent source batches per GPU" if world > 1 else "single GPU"}),
+            "clocks": ck, "gpu_launches": int(args.steps * nst * kper),
+            "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+            "fp64": {"value": units / t64, "unit": UNIT, "ms": 1e3 * t64},
+            "fine_grid": {"value": units / tfine, "unit": UNIT, "ms": 1e3 * tfine,
+                          "note": "FP32 5/7-point leapfrog on the same grid, same tau and steps; cells counted on "
+                                  "the same partition"},
+            "speedup_vs_fine_grid": tfine / t_step,
+            "receiver_rel_l2": {"fp32_vs_fp64_rom": rel(tr32, ref64), "rom_fp64_vs_fine_fp32": rel(ref64, fine_tr)},
+            "offline_s": {"assemble_partition_cfl": t1 - t0, "gpu_rom_build": t2 - t1},
+            "tau": tau}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

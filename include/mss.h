@@ -1,0 +1,276 @@
+/*
+ * mss.h -- C ABI of the GB300 implementation of the multiscale S-fraction
+ * reduced-order method (Druskin, Mamonov, Zaslavsky, "Multi-scale S-fraction
+ * reduced-order models for massive wavefield simulations").
+ *
+ * The semi-discrete problem is A u - B u_tt = g w(t) (Section 1, Eq. wave_fll).
+ * The library covers both stages of Algorithm alg1red:
+ *   stage 1 (off-line): assemble A, B (Section 1); partition into coarse cells
+ *     and remove the corner set (Sections 2-3, Appendix B); build each cell's
+ *     rational Krylov ROM and its matrix S-fraction coefficients (Sections 4-5,
+ *     Appendix C); project sources and receivers (Eqs. BEINCr, solatrec);
+ *   stage 2 (on-line): leapfrog stepping of the coupled ROM for many sources
+ *     at once (Eqs. intrtstep_td, bdrytstep), sampled at receivers.
+ * plus the fine-grid leapfrog on the GPU for comparison.
+ *
+ * Conventions
+ *   - Every call returns mss_status; 0 is success.  On failure nothing the
+ *     call was asked to create is returned, and mss_last_error() (thread
+ *     local) holds a one-line reason.
+ *   - Handles (mss_operator, mss_partition, mss_rom, mss_sim, mss_fine) are
+ *     opaque and owned by the library; free them with the matching *_destroy.
+ *     Device memory they hold is allocated with cudaMalloc on the current
+ *     device at creation time and freed by *_destroy.
+ *   - Caller buffers are plain pointers.  "host" buffers are read or written
+ *     before the call returns.  "device" buffers must stay valid until the
+ *     work queued on the given stream has finished; the library never frees
+ *     them.  Streams are cudaStream_t passed as void* (NULL = legacy stream).
+ *   - Grid arrays are indexed in array order [z][y][x] (3D) or [y][x] (2D),
+ *     x fastest.  Node coordinates are given in the same order.
+ *   - All off-line arithmetic is FP64.
+ */
+#ifndef MSS_H
+#define MSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mss_status;
+enum {
+  MSS_OK = 0,
+  MSS_ERR_INVALID_ARG = 1,       /* bad size, pointer, index or parameter            */
+  MSS_ERR_NOT_SPD = 2,           /* A not <= 0 or B not > 0 (Section 1)              */
+  MSS_ERR_KRYLOV_DEFLATION = 3,  /* Krylov blocks linearly dependent (Assumption ass1) */
+  MSS_ERR_LANCZOS_BREAKDOWN = 4, /* block Lanczos breakdown (Appendix C)             */
+  MSS_ERR_COEF_NOT_SPD = 5,      /* a Gamma^k or Gamma-hat^k not SPD (Eq. S-fraction) */
+  MSS_ERR_CFL = 6,               /* time step above the leapfrog stability limit     */
+  MSS_ERR_TIMEOUT = 7,           /* a bounded device-side wait gave up               */
+  MSS_ERR_CUDA = 8,              /* a CUDA runtime call failed                       */
+  MSS_ERR_OOM = 9,               /* device or host allocation failed                 */
+  MSS_ERR_NOT_CONVERGED = 10,    /* an iterative off-line solve missed its tolerance  */
+  MSS_ERR_STATE = 11             /* call not valid in the handle's current state     */
+};
+
+enum { MSS_DIRICHLET = 0, MSS_NEUMANN = 1 };
+enum { MSS_FP64 = 0, MSS_FP32 = 1 };
+
+const char *mss_status_string(mss_status s);
+/* Reason of the last failed call on this thread ("" if none). */
+const char *mss_last_error(void);
+/* Library version string. */
+const char *mss_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* Fine grid (Section 1, Eq. wave_fll and the acoustic equation below it).    */
+/* ------------------------------------------------------------------------- */
+
+/* Box of voxels: n[a] voxels of edge h along array axis a (a < dim, dim = 1..3);
+ * bc[a][0], bc[a][1] = MSS_DIRICHLET (wall nodes removed) or MSS_NEUMANN (kept)
+ * for the low / high wall of axis a. */
+typedef struct mss_grid {
+  int32_t dim;
+  int32_t n[3];
+  double h;
+  int32_t bc[3][2];
+} mss_grid;
+
+typedef struct mss_operator mss_operator;
+
+/* Assemble the conservative node-based discretisation of div(sigma grad u) - rho u_tt:
+ * voxel v adds -(sigma_v h^(d-2)/2^(d-1)) (e_k - e_l)(e_k - e_l)^T to A for each of its
+ * edges (k,l) and rho_v h^d/2^d to the mass of each of its 2^d corner nodes (Section 1).
+ * sigma, rho: host, prod(n) doubles, > 0.  Unknowns: kept nodes in node order.
+ * Errors: INVALID_ARG (sizes), NOT_SPD (a sigma or rho <= 0 or not finite). */
+mss_status mss_assemble(const mss_grid *g, const double *sigma, const double *rho, mss_operator **out);
+/* info[0] = unknowns N, info[1] = nonzeros of A (CSR, diagonal included). */
+mss_status mss_operator_info(const mss_operator *op, int64_t info[2]);
+/* Copy A as CSR (rowptr[N+1], col[nnz], val[nnz], columns ascending) and diag(B)[N] to host buffers. */
+mss_status mss_operator_export(const mss_operator *op, int64_t *rowptr, int64_t *col, double *val, double *bdiag);
+/* Unknown number of a node (array-order coordinates), -1 if removed by a Dirichlet wall. */
+mss_status mss_operator_node(const mss_operator *op, const int32_t *node, int64_t *unknown);
+/* Largest eigenvalue of -B^{-1} A by Lanczos on the host (FP64; stops when the top Ritz value changes by < tol relative). */
+mss_status mss_operator_lambda_max(const mss_operator *op, double tol, double *lambda_max);
+void mss_operator_destroy(mss_operator *op);
+
+/* ------------------------------------------------------------------------- */
+/* Partition (Section 2 Eq. part / splitN_c; Section 3 Eq. nocorners,        */
+/* Example cs_multidom_ex; Appendix B; I/O faces for Eq. gsupport).            */
+/* ------------------------------------------------------------------------- */
+typedef struct mss_partition mss_partition;
+
+/* Box cells of cell[a] voxels (>= 2, dividing n[a]); cell i receives the terms of its own
+ * voxels (voxel ownership).  Interior faces are numbered axis-major, then by the lower
+ * cell in C order; a node on more than one face is replaced by one hanging node per face,
+ * every cell splitting its share of the node's row (edge weights, Dirichlet losses, mass)
+ * equally among its faces holding the node.  io_nodes (host, n_io x dim, may repeat) that
+ * fall strictly inside a cell become that cell's one-sided I/O face (nodes in unknown order).
+ * sigma, rho: the arrays given to mss_assemble.  Errors: INVALID_ARG. */
+mss_status mss_partition_create(const mss_operator *op, const double *sigma, const double *rho,
+                                const int32_t *cell, int32_t n_io, const int32_t *io_nodes,
+                                mss_partition **out);
+/* info: [0] cells, [1] faces, [2] interior faces, [3] prime nodes N', [4] corner-set nodes,
+ *       [5] total face nodes, [6] total cell nodes, [7] max cell nodes. */
+mss_status mss_partition_info(const mss_partition *p, int64_t info[8]);
+/* Faces: kind[f] (0 interior, 1 I/O), cells[2f..2f+1] (-1 if none), shape[2f..2f+1] (face
+ * node grid, 1 for missing axes), node_ptr[F+1], nodes[] (prime ids, face order),
+ * parents[] (original unknowns).  Host buffers sized from mss_partition_info. */
+mss_status mss_partition_faces(const mss_partition *p, int32_t *kind, int32_t *cells, int32_t *shape,
+                               int64_t *node_ptr, int64_t *nodes, int64_t *parents);
+/* Cell c: face_ptr/faces (ascending), nodes (prime ids: boundary face by face, then interior),
+ * K = boundary node count, A_c as CSR in that local order, diag(B_c).  Pass NULL to query
+ * counts: counts[0] = nodes, counts[1] = nonzeros, counts[2] = faces, counts[3] = K. */
+mss_status mss_partition_cell(const mss_partition *p, int32_t c, int64_t counts[4], int32_t *faces,
+                              int64_t *nodes, int64_t *rowptr, int64_t *col, double *val, double *bdiag);
+void mss_partition_destroy(mss_partition *p);
+
+/* ------------------------------------------------------------------------- */
+/* Cell ROMs and S-fraction coefficients (Sections 4-6, Appendix C).          */
+/* ------------------------------------------------------------------------- */
+typedef struct mss_rom mss_rom;
+
+/* Off-line parameters.  m: S-fraction layers per cell (cell_m overrides per cell);
+ * n_modes: modes kept per interior face (lowest-wavenumber DCT-II modes of the face grid;
+ * I/O faces keep all nodes); shift s < 0 of the rational Krylov space (Eq. npks);
+ * cg_tol / cg_maxit: relative residual and iteration cap of the shifted solves. */
+typedef struct mss_rom_params {
+  int32_t m;
+  int32_t n_modes;
+  double shift;
+  double cg_tol;
+  int32_t cg_maxit;
+  int32_t reserved;
+} mss_rom_params;
+
+/* Build every cell's ROM on the current device in FP64 (Algorithm alg1red stage 1):
+ * V = B-orthonormal basis of span{B^{-1}C, K B^{-1}C, .., K^{m-1}B^{-1}C}, K = (A+sB)^{-1}B,
+ * C = P^Gamma S (Eq. npks, Remark Sinsubspace); A^m = V^T A V, S^m = V^T C (Eq. tfprj);
+ * block Lanczos (Eq. NtDtri); Gamma^k, Gamma-hat^k (Eq. GammaTrans, symmetric form);
+ * face masses M_f = sum_i (Gamma-hat^1_{i,f})^{-1} (Eq. bdrytstep); Appendix D data.
+ * Errors: INVALID_ARG, KRYLOV_DEFLATION, LANCZOS_BREAKDOWN, COEF_NOT_SPD, NOT_CONVERGED,
+ * CUDA, OOM.  Synchronises the stream before returning. */
+mss_status mss_build_roms(const mss_partition *p, const mss_rom_params *prm, const int32_t *cell_m,
+                          void *stream, mss_rom **out);
+
+/* Coefficient set given by the caller (host, FP64), for ROMs built elsewhere.
+ * cell_m[C], cell_face_ptr[C+1], cell_faces[] (faces of each cell in boundary-vector order),
+ * face_M[F], face_cells[2F] (lower cell first, -1 for a one-sided face);
+ * gamma: per cell m_i blocks K_i x K_i (Gamma^1..Gamma^m, row-major, concatenated over cells);
+ * gamma_hat: per cell m_i blocks (Gamma-hat^1..Gamma-hat^m); face_mass: per face M_f x M_f.
+ * K_i = sum of M_f over the cell's faces.  Matrices must be symmetric. */
+typedef struct mss_rom_desc {
+  int32_t n_cells;
+  int32_t n_faces;
+  const int32_t *cell_m;
+  const int32_t *cell_face_ptr;
+  const int32_t *cell_faces;
+  const int32_t *face_M;
+  const int32_t *face_cells;
+  const double *gamma;
+  const double *gamma_hat;
+  const double *face_mass;
+} mss_rom_desc;
+/* Errors: INVALID_ARG (inconsistent topology), COEF_NOT_SPD (a Gamma-hat^k or M_f fails Cholesky). */
+mss_status mss_rom_import(const mss_rom_desc *d, mss_rom **out);
+/* info: [0] cells, [1] faces, [2] max K, [3] max m, [4] coefficient doubles,
+ *       [5] face-mass doubles, [6] total face modes, [7] corner groups. */
+mss_status mss_rom_info(const mss_rom *r, int64_t info[8]);
+/* Copy the coefficients to host in the mss_rom_desc layout (sizes from mss_rom_info):
+ * cell_m, cell_face_ptr, cell_faces, face_M, face_cells, gamma, gamma_hat, face_mass. */
+mss_status mss_rom_export(const mss_rom *r, int32_t *cell_m, int32_t *cell_face_ptr, int32_t *cell_faces,
+                          int32_t *face_M, int32_t *face_cells, double *gamma, double *gamma_hat,
+                          double *face_mass);
+/* Face bases S_f (K_f x M_f, row-major, concatenated over faces) of a ROM built by
+ * mss_build_roms; sizes: sum K_f M_f. */
+mss_status mss_rom_face_bases(const mss_rom *r, int64_t *count, double *bases);
+
+/* Projected inputs/outputs (Eq. BEINCr g~_f = S_f^T g|_f, Eq. solatrec q~_f = S_f^T q|_f) from
+ * point sources/receivers at fine-grid nodes with weights (NULL = 1); a node of the corner set
+ * is spread over its hanging copies with weights b_{k_f}/b_k.  Needs a ROM built by
+ * mss_build_roms from the same partition.  Replaces any previous I/O of the ROM. */
+mss_status mss_rom_set_io_nodes(mss_rom *r, const mss_partition *p, int32_t n_src, const int32_t *src_nodes,
+                                const double *src_w, int32_t n_rcv, const int32_t *rcv_nodes,
+                                const double *rcv_w);
+/* Projected inputs/outputs given directly as entries (face, index, M_f values):
+ * src_face[e], src_index[e], src_vals (concatenated M_f values per entry), likewise receivers. */
+mss_status mss_rom_set_io(mss_rom *r, int32_t n_src, int32_t n_src_entries, const int32_t *src_face,
+                          const int32_t *src_index, const double *src_vals, int32_t n_rcv,
+                          int32_t n_rcv_entries, const int32_t *rcv_face, const int32_t *rcv_index,
+                          const double *rcv_vals);
+/* Appendix D corner correction data: group_ptr[G+1]; per member: face, the S_f row of the
+ * hanging node (M_f values, concatenated), weight b_{k_f}/b_k.  Built automatically by
+ * mss_build_roms; this call replaces it (n_groups = 0 clears it). */
+mss_status mss_rom_set_corners(mss_rom *r, int32_t n_groups, const int32_t *group_ptr, const int32_t *face,
+                               const double *rows, const double *weight);
+void mss_rom_destroy(mss_rom *r);
+
+/* ------------------------------------------------------------------------- */
+/* On-line stage (Algorithm alg1red stage 2; Eqs. intrtstep_td, bdrytstep,    */
+/* contred, solatrec).                                                        */
+/* ------------------------------------------------------------------------- */
+typedef struct mss_sim mss_sim;
+
+/* Per step n (t_n = n tau), for every cell i and source:
+ *   F^k_i = Gamma^k_i (U^{k+1}_i - U^k_i), k = 1..m_i, U^1_i = the cell's faces' u~_f, U^{m+1} = 0
+ *   U^k_i <- 2 U^k_i - U^k_i,old + tau^2 Gamma-hat^k_i (F^k_i - F^{k-1}_i),          k = 2..m_i
+ *   u~_f  <- 2 u~_f - u~_f,old + tau^2 M_f^{-1} (sum_{i on f} F^1_i|_f - g~_f w(t_n))
+ *   then (if enabled) the Appendix D correction of the new u~;
+ * trace sample n = sum_f q~_f^T u~_f at step n (before it is advanced).
+ * precision: MSS_FP64 or MSS_FP32 (state, coefficients and arithmetic).
+ * corner_correction: 0/1.  Needs I/O set on the ROM (n_src >= 1).
+ * The sim copies what it needs from the ROM (the ROM may be destroyed afterwards).
+ * Errors: INVALID_ARG, STATE (ROM without I/O), CFL (tau <= 0), CUDA, OOM. */
+mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32_t corner_correction,
+                          mss_sim **out);
+/* info: [0] sources, [1] receivers, [2] precision, [3] steps taken, [4] state values per level,
+ *       [5] device bytes held, [6] kernels launched per step, [7] source tile. */
+mss_status mss_sim_info(const mss_sim *s, int64_t info[8]);
+/* Zero the state (u = u_old = 0) and the step counter. */
+mss_status mss_sim_reset(mss_sim *s, void *stream);
+/* Advance n_steps.  waveform: device, FP64, w(t_j) for j = steps_taken .. steps_taken+n_steps-1
+ * (indexed from the pointer: waveform[j - steps_taken]); traces: device, [n_steps][n_rcv][n_src]
+ * of double (FP64) or float (FP32).  use_graph: capture the loop as a CUDA graph (cached per
+ * (n_steps, pointers)).  Errors: INVALID_ARG, CUDA. */
+mss_status mss_step(mss_sim *s, int64_t n_steps, const double *waveform, void *traces, int32_t use_graph,
+                    void *stream);
+/* End-to-end call on host buffers: copies waveform (host, n_steps doubles) to the device,
+ * resets the state, steps, and copies the traces back into traces_host (same layout as
+ * mss_step), all on the stream; returns after the copy has completed. */
+mss_status mss_run_host(mss_sim *s, int64_t n_steps, const double *waveform_host, void *traces_host,
+                        void *stream);
+/* Per-kernel timing of the step loop: runs n_steps eagerly on the stream with CUDA events around
+ * every kernel and returns the mean device duration (ms) of each kernel kind:
+ * ms[0] cell kernel, ms[1] face+receiver kernel, ms[2] corner kernel (0 when disabled).
+ * Same waveform/trace conventions as mss_step; the state advances like mss_step. */
+mss_status mss_step_profile(mss_sim *s, int64_t n_steps, const double *waveform, void *traces, double ms[3],
+                            void *stream);
+/* Two time levels of the state as FP64 on host, faces first (total face modes x n_src) then
+ * hidden layers (cell by cell, layer by layer, K_i x n_src); count = mss_sim_info[4] each.
+ * save: now[], old[] <- state; load: state <- now[], old[] (and the step counter).
+ * Resuming from a saved state continues bit-identically on the same precision. */
+mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_t *steps_taken);
+mss_status mss_sim_load_state(mss_sim *s, const double *now, const double *old, int64_t steps_taken);
+void mss_sim_destroy(mss_sim *s);
+
+/* ------------------------------------------------------------------------- */
+/* Fine-grid leapfrog on the GPU (Section 1; the comparison baseline):        */
+/* u^{n+1} = 2u^n - u^{n-1} + tau^2 B^{-1}(A u^n - g w(t_n)), sample q^T u^n.  */
+/* ------------------------------------------------------------------------- */
+typedef struct mss_fine mss_fine;
+/* Point sources/receivers at nodes (host, n x dim), unit weights.  Sources batched:
+ * state layout [node][source].  precision: MSS_FP64 or MSS_FP32. */
+mss_status mss_fine_create(const mss_operator *op, int32_t precision, double tau, int32_t n_src,
+                           const int32_t *src_nodes, int32_t n_rcv, const int32_t *rcv_nodes, mss_fine **out);
+mss_status mss_fine_reset(mss_fine *f, void *stream);
+/* Same waveform/trace conventions as mss_step. */
+mss_status mss_fine_step(mss_fine *f, int64_t n_steps, const double *waveform, void *traces, int32_t use_graph,
+                         void *stream);
+void mss_fine_destroy(mss_fine *f);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSS_H */

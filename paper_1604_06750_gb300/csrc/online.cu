@@ -1,0 +1,798 @@
+// On-line stage of the multiscale S-fraction ROM (Algorithm alg1red, stage 2).
+//
+// One time step is two or three kernels:
+//   k_cell   -- per (cell, source tile): F^k = Gamma^k (U^{k+1} - U^k), k = 1..m (fluxes of
+//               Eq. intrtstep_td), the face slices of F^1 published to the flux buffer (the
+//               exchange of step 2.1), and the hidden-layer leapfrog
+//               U^k <- 2U^k - U^k_old + tau^2 Gamma-hat^k (F^k - F^{k-1}), k = 2..m (step 2.2);
+//   k_face   -- per (face, source tile): u~_f <- 2u~_f - u~_f,old + tau^2 M_f^{-1}(sum of the
+//               cells' F^1 slices - g~_f w(t_n)) (Eq. bdrytstep, step 2.3); extra blocks sample
+//               the receivers (Eq. solatrec) from the state before the update;
+//   k_corner -- optional Appendix D correction of the new face level.
+// U^1 of a cell is gathered from the face state (Eq. contred: one state per face, shared by
+// both cells).  Coefficient matrices are symmetric; the thread that owns output row r reads
+// Gamma[c][r] for c = 0..K-1, so the threads of a warp read consecutive addresses.
+// The time loop can be captured as a CUDA graph (cached per call signature).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+#include <tuple>
+
+#include "cuda_util.h"
+
+namespace mss {
+
+template <typename T>
+struct StepArgs {
+  // cells
+  const int32_t *cell_K, *cell_m;
+  const int64_t *cell_coef, *cell_ghat, *cell_state, *cell_row;
+  const int64_t *row_face_row;   // per cell boundary row: global face row
+  const int8_t *row_side;        // 0 = lower cell of the face, 1 = upper cell
+  // faces
+  const int32_t *face_M, *face_two;
+  const int64_t *face_row, *face_minv;
+  const int32_t *fsrc_ptr, *fsrc_index;
+  const int64_t *fsrc_val;
+  // receivers
+  const int32_t *rcv_ptr, *rcv_face;
+  const int64_t *rcv_off;
+  // corners: members listed per face (fm_*), per corner group (grp_ptr), member data (mem_*)
+  const int32_t *fm_ptr, *fm_member, *mem_group, *mem_face, *grp_ptr;
+  const int64_t *mem_row;
+  // values
+  const T *coef, *minv, *src_val, *rcv_val, *cg_rows, *cg_w;
+  T *fstate0, *fstate1, *cstate0, *cstate1, *flux, *ftmp;
+  int S, n_cells, n_faces, n_rcv, corners;
+  T tau2;
+};
+
+constexpr int kCellThreads = 256;
+constexpr int kFaceThreads = 128;
+
+template <typename T, int ST>
+__global__ void __launch_bounds__(kCellThreads) k_cell(const StepArgs<T> a, const int cur) {
+  const int cell = blockIdx.x;
+  const int s0 = blockIdx.y * ST;
+  const int K = a.cell_K[cell], m = a.cell_m[cell];
+  const int ns = min(ST, a.S - s0);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *U = reinterpret_cast<T *>(smem_raw);        // layers 1..m, [k][r][s]
+  T *D = U + (size_t)m * K * ST;                 // U^{k+1} - U^k, later F^k - F^{k-1}
+  T *F = D + (size_t)m * K * ST;                 // fluxes F^k
+  const T *fs = cur ? a.fstate1 : a.fstate0;
+  const T *cs = cur ? a.cstate1 : a.cstate0;
+  T *cso = cur ? a.cstate0 : a.cstate1;
+  const int64_t rp = a.cell_row[cell];
+  const int64_t so = a.cell_state[cell];
+  const int S = a.S;
+  for (int i = threadIdx.x; i < K * ST; i += blockDim.x) {
+    const int r = i / ST, s = i - r * ST;
+    U[i] = s < ns ? fs[a.row_face_row[rp + r] * S + s0 + s] : T(0);
+  }
+  for (int i = threadIdx.x; i < (m - 1) * K * ST; i += blockDim.x) {
+    const int r = i / ST, s = i - r * ST;
+    U[(size_t)K * ST + i] = s < ns ? cs[(so + r) * S + s0 + s] : T(0);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m * K * ST; i += blockDim.x) {
+    const int k = i / (K * ST);
+    D[i] = (k + 1 < m ? U[i + (size_t)K * ST] : T(0)) - U[i];
+  }
+  __syncthreads();
+  const T *G = a.coef + a.cell_coef[cell];
+  for (int it = threadIdx.x; it < m * K; it += blockDim.x) {
+    const int k = it / K, r = it - k * K;
+    const T *Gk = G + (size_t)k * K * K + r;
+    const T *Dk = D + (size_t)k * K * ST;
+    T acc[ST];
+#pragma unroll
+    for (int s = 0; s < ST; ++s) acc[s] = T(0);
+    for (int c = 0; c < K; ++c) {
+      const T g = Gk[(size_t)c * K];
+#pragma unroll
+      for (int s = 0; s < ST; ++s) acc[s] += g * Dk[c * ST + s];
+    }
+#pragma unroll
+    for (int s = 0; s < ST; ++s) F[(size_t)k * K * ST + r * ST + s] = acc[s];
+  }
+  __syncthreads();
+  // exchange: this cell's F^1 on each of its faces
+  for (int i = threadIdx.x; i < K * ST; i += blockDim.x) {
+    const int r = i / ST, s = i - r * ST;
+    if (s < ns) a.flux[(a.row_face_row[rp + r] * 2 + a.row_side[rp + r]) * S + s0 + s] = F[i];
+  }
+  for (int i = threadIdx.x; i < (m - 1) * K * ST; i += blockDim.x) {
+    const size_t j = (size_t)K * ST + i;
+    D[j] = F[j] - F[j - (size_t)K * ST];
+  }
+  __syncthreads();
+  const T *H = a.coef + a.cell_ghat[cell];
+  const T tau2 = a.tau2;
+  for (int it = threadIdx.x; it < (m - 1) * K; it += blockDim.x) {
+    const int k = 1 + it / K, r = it - (k - 1) * K;
+    const T *Hk = H + (size_t)(k - 1) * K * K + r;
+    const T *Ek = D + (size_t)k * K * ST;
+    T acc[ST];
+#pragma unroll
+    for (int s = 0; s < ST; ++s) acc[s] = T(0);
+    for (int c = 0; c < K; ++c) {
+      const T h = Hk[(size_t)c * K];
+#pragma unroll
+      for (int s = 0; s < ST; ++s) acc[s] += h * Ek[c * ST + s];
+    }
+    const T *Uk = U + (size_t)k * K * ST + r * ST;
+#pragma unroll
+    for (int s = 0; s < ST; ++s) {
+      if (s < ns) {
+        const int64_t idx = (so + (int64_t)(k - 1) * K + r) * S + s0 + s;
+        cso[idx] = T(2) * Uk[s] - cso[idx] + tau2 * acc[s];
+      }
+    }
+  }
+}
+
+template <typename T, int ST>
+__global__ void __launch_bounds__(kFaceThreads) k_face(const StepArgs<T> a, const int cur, const double *w,
+                                                       T *traces) {
+  const int b = blockIdx.x;
+  const int s0 = blockIdx.y * ST;
+  const int ns = min(ST, a.S - s0);
+  const int S = a.S;
+  const T *fs = cur ? a.fstate1 : a.fstate0;
+  if (b < a.n_faces) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sum = reinterpret_cast<T *>(smem_raw);
+    const int f = b, M = a.face_M[f];
+    const int64_t row0 = a.face_row[f];
+    const bool two = a.face_two[f] != 0;
+    const T wn = (T)(*w);
+    for (int i = threadIdx.x; i < M * ST; i += blockDim.x) {
+      const int r = i / ST, s = i - r * ST;
+      T v = T(0);
+      if (s < ns) {
+        v = a.flux[((row0 + r) * 2) * S + s0 + s];
+        if (two) v += a.flux[((row0 + r) * 2 + 1) * S + s0 + s];
+        for (int e = a.fsrc_ptr[f]; e < a.fsrc_ptr[f + 1]; ++e)
+          if (a.fsrc_index[e] == s0 + s) v -= a.src_val[a.fsrc_val[e] + r] * wn;
+      }
+      sum[i] = v;
+    }
+    __syncthreads();
+    const T *Mi = a.minv + a.face_minv[f];
+    const T *old = cur ? a.fstate0 : a.fstate1;
+    T *dst = a.corners ? a.ftmp : (cur ? a.fstate0 : a.fstate1);
+    for (int i = threadIdx.x; i < M * ST; i += blockDim.x) {
+      const int r = i / ST, s = i - r * ST;
+      if (s >= ns) continue;
+      T acc = T(0);
+      for (int c = 0; c < M; ++c) acc += Mi[(size_t)r * M + c] * sum[c * ST + s];
+      const int64_t idx = (row0 + r) * S + s0 + s;
+      dst[idx] = T(2) * fs[idx] - old[idx] + a.tau2 * acc;
+    }
+  } else {
+    // receivers: sample the state at this step, before it is advanced
+    const int per = kFaceThreads / ST;
+    const int r = (b - a.n_faces) * per + (int)threadIdx.x / ST;
+    const int s = (int)threadIdx.x % ST;
+    if (r >= a.n_rcv || s >= ns) return;
+    T acc = T(0);
+    for (int e = a.rcv_ptr[r]; e < a.rcv_ptr[r + 1]; ++e) {
+      const int f = a.rcv_face[e];
+      const int M = a.face_M[f];
+      const int64_t row0 = a.face_row[f];
+      const T *q = a.rcv_val + a.rcv_off[e];
+      for (int c = 0; c < M; ++c) acc += q[c] * fs[(row0 + c) * S + s0 + s];
+    }
+    traces[(int64_t)r * S + s0 + s] = acc;
+  }
+}
+
+// Appendix D: for every hanging node l on face f (group g of copies of one corner-set node),
+// delta_l = sum_{l' in g} w_l' (s_l' . u~_{f_l'}) - s_l . u~_f, then u~_f += sum_l s_l delta_l.
+// Reads the uncorrected new level (ftmp), writes the corrected one into the state.
+template <typename T, int ST>
+__global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, const int cur) {
+  const int f = blockIdx.x;
+  const int s0 = blockIdx.y * ST;
+  const int ns = min(ST, a.S - s0);
+  const int S = a.S;
+  const int M = a.face_M[f];
+  const int64_t row0 = a.face_row[f];
+  T *dst = cur ? a.fstate0 : a.fstate1;
+  const int j0 = a.fm_ptr[f], nm = a.fm_ptr[f + 1] - j0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *delta = reinterpret_cast<T *>(smem_raw);
+  for (int i = threadIdx.x; i < nm * ST; i += blockDim.x) {
+    const int j = i / ST, s = i - j * ST;
+    T d = T(0);
+    if (s < ns) {
+      const int l = a.fm_member[j0 + j];
+      const int g = a.mem_group[l];
+      T mean = T(0), own = T(0);
+      for (int l2 = a.grp_ptr[g]; l2 < a.grp_ptr[g + 1]; ++l2) {
+        const int f2 = a.mem_face[l2];
+        const int M2 = a.face_M[f2];
+        const T *row = a.cg_rows + a.mem_row[l2];
+        const int64_t r0 = a.face_row[f2];
+        T dot = T(0);
+        for (int c = 0; c < M2; ++c) dot += row[c] * a.ftmp[(r0 + c) * S + s0 + s];
+        mean += a.cg_w[l2] * dot;
+        if (l2 == l) own = dot;
+      }
+      d = mean - own;
+    }
+    delta[i] = d;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < M * ST; i += blockDim.x) {
+    const int r = i / ST, s = i - r * ST;
+    if (s >= ns) continue;
+    const int64_t idx = (row0 + r) * S + s0 + s;
+    T v = a.ftmp[idx];
+    for (int j = 0; j < nm; ++j) {
+      const int l = a.fm_member[j0 + j];
+      v += a.cg_rows[a.mem_row[l] + r] * delta[j * ST + s];
+    }
+    dst[idx] = v;
+  }
+}
+
+// ------------------------------------------------------------------ simulation object
+struct SimDev {
+  DevMem cell_K, cell_m, cell_coef, cell_ghat, cell_state, cell_row, row_face_row, row_side;
+  DevMem face_M, face_two, face_row, face_minv, fsrc_ptr, fsrc_index, fsrc_val;
+  DevMem rcv_ptr, rcv_face, rcv_off;
+  DevMem fm_ptr, fm_member, mem_group, mem_face, grp_ptr, mem_row;
+  DevMem coef, minv, src_val, rcv_val, cg_rows, cg_w;
+  DevMem fstate[2], cstate[2], flux, ftmp, wbuf, tbuf;
+};
+
+struct GraphKey {
+  int64_t n;
+  const void *w, *t;
+  int cur;
+  bool operator<(const GraphKey &o) const {
+    return std::tie(n, w, t, cur) < std::tie(o.n, o.w, o.t, o.cur);
+  }
+};
+
+}  // namespace mss
+
+struct mss_sim {
+  int prec = MSS_FP64;
+  int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
+  int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0;
+  int64_t face_rows = 0, cell_rows = 0;
+  int64_t steps = 0;
+  int cur = 0;
+  double tau = 0;
+  size_t cell_smem = 0, face_smem = 0, corner_smem = 0;
+  int64_t dev_bytes = 0;
+  mss::SimDev d;
+  std::map<mss::GraphKey, cudaGraphExec_t> graphs;
+  int device = 0;
+  cudaStream_t cap = nullptr;          // capture/replay stream, joined to the caller's stream by events
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  ~mss_sim() {
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+namespace mss {
+
+template <typename T>
+static StepArgs<T> make_args(const mss_sim &s) {
+  const SimDev &d = s.d;
+  StepArgs<T> a;
+  a.cell_K = d.cell_K.as<int32_t>();
+  a.cell_m = d.cell_m.as<int32_t>();
+  a.cell_coef = d.cell_coef.as<int64_t>();
+  a.cell_ghat = d.cell_ghat.as<int64_t>();
+  a.cell_state = d.cell_state.as<int64_t>();
+  a.cell_row = d.cell_row.as<int64_t>();
+  a.row_face_row = d.row_face_row.as<int64_t>();
+  a.row_side = d.row_side.as<int8_t>();
+  a.face_M = d.face_M.as<int32_t>();
+  a.face_two = d.face_two.as<int32_t>();
+  a.face_row = d.face_row.as<int64_t>();
+  a.face_minv = d.face_minv.as<int64_t>();
+  a.fsrc_ptr = d.fsrc_ptr.as<int32_t>();
+  a.fsrc_index = d.fsrc_index.as<int32_t>();
+  a.fsrc_val = d.fsrc_val.as<int64_t>();
+  a.rcv_ptr = d.rcv_ptr.as<int32_t>();
+  a.rcv_face = d.rcv_face.as<int32_t>();
+  a.rcv_off = d.rcv_off.as<int64_t>();
+  a.fm_ptr = d.fm_ptr.as<int32_t>();
+  a.fm_member = d.fm_member.as<int32_t>();
+  a.mem_group = d.mem_group.as<int32_t>();
+  a.mem_face = d.mem_face.as<int32_t>();
+  a.grp_ptr = d.grp_ptr.as<int32_t>();
+  a.mem_row = d.mem_row.as<int64_t>();
+  a.coef = d.coef.as<T>();
+  a.minv = d.minv.as<T>();
+  a.src_val = d.src_val.as<T>();
+  a.rcv_val = d.rcv_val.as<T>();
+  a.cg_rows = d.cg_rows.as<T>();
+  a.cg_w = d.cg_w.as<T>();
+  a.fstate0 = d.fstate[0].as<T>();
+  a.fstate1 = d.fstate[1].as<T>();
+  a.cstate0 = d.cstate[0].as<T>();
+  a.cstate1 = d.cstate[1].as<T>();
+  a.flux = d.flux.as<T>();
+  a.ftmp = d.ftmp.as<T>();
+  a.S = s.n_src;
+  a.n_cells = s.n_cells;
+  a.n_faces = s.n_faces;
+  a.n_rcv = s.n_rcv;
+  a.corners = s.corners;
+  a.tau2 = (T)(s.tau * s.tau);
+  return a;
+}
+
+template <typename T, int ST>
+static void set_smem_attrs(const mss_sim &s) {
+  MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
+  MSS_CUDA(cudaFuncSetAttribute(k_face<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.face_smem));
+  MSS_CUDA(cudaFuncSetAttribute(k_corner<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.corner_smem));
+}
+
+template <typename T, int ST>
+static void launch_steps(mss_sim &s, int64_t n, const double *w, T *traces, cudaStream_t st) {
+  const StepArgs<T> a = make_args<T>(s);
+  const int per = kFaceThreads / ST;
+  const int rcv_blocks = (s.n_rcv + per - 1) / per;
+  const dim3 gc(s.n_cells, s.tiles), gf(s.n_faces + rcv_blocks, s.tiles), gk(s.n_faces, s.tiles);
+  int cur = s.cur;
+  for (int64_t j = 0; j < n; ++j) {
+    k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
+    k_face<T, ST><<<gf, kFaceThreads, s.face_smem, st>>>(a, cur, w + j, traces + j * (int64_t)s.n_rcv * s.n_src);
+    if (s.corners) k_corner<T, ST><<<gk, kFaceThreads, s.corner_smem, st>>>(a, cur);
+    cur ^= 1;
+  }
+  MSS_CUDA(cudaGetLastError());
+}
+
+template <typename T, int ST>
+static void step_impl(mss_sim &s, int64_t n, const double *w, void *traces, int use_graph, cudaStream_t st) {
+  set_smem_attrs<T, ST>(s);
+  if (!use_graph) {
+    launch_steps<T, ST>(s, n, w, (T *)traces, st);
+  } else {
+    // capture and replay on the sim's own stream (the legacy stream cannot be captured)
+    MSS_CUDA(cudaEventRecord(s.ev_in, st));
+    MSS_CUDA(cudaStreamWaitEvent(s.cap, s.ev_in, 0));
+    GraphKey key{n, w, traces, s.cur};
+    auto it = s.graphs.find(key);
+    if (it == s.graphs.end()) {
+      cudaGraph_t g = nullptr;
+      MSS_CUDA(cudaStreamBeginCapture(s.cap, cudaStreamCaptureModeThreadLocal));
+      try {
+        launch_steps<T, ST>(s, n, w, (T *)traces, s.cap);
+      } catch (...) {
+        cudaStreamEndCapture(s.cap, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      MSS_CUDA(cudaStreamEndCapture(s.cap, &g));
+      cudaGraphExec_t ge;
+      cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      MSS_CUDA(e);
+      it = s.graphs.emplace(key, ge).first;
+    }
+    MSS_CUDA(cudaGraphLaunch(it->second, s.cap));
+    MSS_CUDA(cudaEventRecord(s.ev_out, s.cap));
+    MSS_CUDA(cudaStreamWaitEvent(st, s.ev_out, 0));
+  }
+  s.cur = (int)((s.cur + n) & 1);
+  s.steps += n;
+}
+
+template <typename T, int ST>
+static void profile_impl(mss_sim &s, int64_t n, const double *w, T *traces, double ms[3], cudaStream_t st) {
+  set_smem_attrs<T, ST>(s);
+  const StepArgs<T> a = make_args<T>(s);
+  const int per = kFaceThreads / ST;
+  const int rcv_blocks = (s.n_rcv + per - 1) / per;
+  const dim3 gc(s.n_cells, s.tiles), gf(s.n_faces + rcv_blocks, s.tiles), gk(s.n_faces, s.tiles);
+  cudaEvent_t ev[4];
+  for (auto &e : ev) MSS_CUDA(cudaEventCreate(&e));
+  double acc[3] = {0, 0, 0};
+  int cur = s.cur;
+  try {
+    for (int64_t j = 0; j < n; ++j) {
+      MSS_CUDA(cudaEventRecord(ev[0], st));
+      k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
+      MSS_CUDA(cudaEventRecord(ev[1], st));
+      k_face<T, ST><<<gf, kFaceThreads, s.face_smem, st>>>(a, cur, w + j, traces + j * (int64_t)s.n_rcv * s.n_src);
+      MSS_CUDA(cudaEventRecord(ev[2], st));
+      if (s.corners) k_corner<T, ST><<<gk, kFaceThreads, s.corner_smem, st>>>(a, cur);
+      MSS_CUDA(cudaEventRecord(ev[3], st));
+      MSS_CUDA(cudaEventSynchronize(ev[3]));
+      for (int k = 0; k < 3; ++k) {
+        float t = 0;
+        MSS_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+        acc[k] += t;
+      }
+      cur ^= 1;
+    }
+    MSS_CUDA(cudaGetLastError());
+  } catch (...) {
+    for (auto &e : ev) cudaEventDestroy(e);
+    throw;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  for (int k = 0; k < 3; ++k) ms[k] = n > 0 ? acc[k] / (double)n : 0.0;
+  if (!s.corners) ms[2] = 0.0;
+  s.cur = (int)((s.cur + n) & 1);
+  s.steps += n;
+}
+
+template <typename T>
+static void profile_dispatch(mss_sim &s, int64_t n, const double *w, void *traces, double ms[3], cudaStream_t st) {
+  switch (s.ST) {
+    case 1: profile_impl<T, 1>(s, n, w, (T *)traces, ms, st); break;
+    case 2: profile_impl<T, 2>(s, n, w, (T *)traces, ms, st); break;
+    case 4: profile_impl<T, 4>(s, n, w, (T *)traces, ms, st); break;
+    case 8: profile_impl<T, 8>(s, n, w, (T *)traces, ms, st); break;
+    default: profile_impl<T, 16>(s, n, w, (T *)traces, ms, st); break;
+  }
+}
+
+template <typename T>
+static void step_dispatch(mss_sim &s, int64_t n, const double *w, void *traces, int use_graph, cudaStream_t st) {
+  switch (s.ST) {
+    case 1: step_impl<T, 1>(s, n, w, traces, use_graph, st); break;
+    case 2: step_impl<T, 2>(s, n, w, traces, use_graph, st); break;
+    case 4: step_impl<T, 4>(s, n, w, traces, use_graph, st); break;
+    case 8: step_impl<T, 8>(s, n, w, traces, use_graph, st); break;
+    default: step_impl<T, 16>(s, n, w, traces, use_graph, st); break;
+  }
+}
+
+template <typename T>
+static void upload_as(DevMem &m, const std::vector<double> &v) {
+  std::vector<T> t(v.begin(), v.end());
+  upload(m, t);
+}
+
+// Invert the SPD face masses on the host (Gauss-Jordan with partial pivoting, FP64).
+static std::vector<double> inverse(const double *A, int n) {
+  std::vector<double> a(A, A + (size_t)n * n), inv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)p * n + c])) p = r;
+    MSS_REQUIRE(a[(size_t)p * n + c] != 0, MSS_ERR_COEF_NOT_SPD, "singular face mass");
+    if (p != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[(size_t)p * n + k], a[(size_t)c * n + k]);
+        std::swap(inv[(size_t)p * n + k], inv[(size_t)c * n + k]);
+      }
+    const double piv = a[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      a[(size_t)c * n + k] /= piv;
+      inv[(size_t)c * n + k] /= piv;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[(size_t)r * n + c];
+      if (f == 0) continue;
+      for (int k = 0; k < n; ++k) {
+        a[(size_t)r * n + k] -= f * a[(size_t)c * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
+      }
+    }
+  }
+  return inv;
+}
+
+static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corners) {
+  MSS_REQUIRE(prec == MSS_FP64 || prec == MSS_FP32, MSS_ERR_INVALID_ARG, "precision must be FP64 or FP32");
+  MSS_REQUIRE(tau > 0 && std::isfinite(tau), MSS_ERR_CFL, "tau must be positive");
+  MSS_REQUIRE(R.has_io, MSS_ERR_STATE, "ROM has no sources/receivers (mss_rom_set_io*)");
+  MSS_CUDA(cudaGetDevice(&s.device));
+  MSS_CUDA(cudaStreamCreateWithFlags(&s.cap, cudaStreamNonBlocking));
+  MSS_CUDA(cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming));
+  MSS_CUDA(cudaEventCreateWithFlags(&s.ev_out, cudaEventDisableTiming));
+  s.prec = prec;
+  s.tau = tau;
+  s.n_cells = R.n_cells;
+  s.n_faces = R.n_faces;
+  s.n_src = R.n_src;
+  s.n_rcv = R.n_rcv;
+  s.corners = (corners && !R.cg_ptr.empty()) ? 1 : 0;
+  const int S = s.n_src;
+  s.ST = S <= 1 ? 1 : S <= 2 ? 2 : S <= 4 ? 4 : S <= 8 ? 8 : 16;
+  const size_t es = prec == MSS_FP64 ? 8 : 4;
+  // shrink the source tile until the cell kernel fits shared memory
+  s.max_K = *std::max_element(R.cell_K.begin(), R.cell_K.end());
+  s.max_m = *std::max_element(R.cell_m.begin(), R.cell_m.end());
+  s.max_M = *std::max_element(R.face_M.begin(), R.face_M.end());
+  int dev_smem = 0;
+  MSS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s.device));
+  while (s.ST > 1 && 3 * (size_t)s.max_m * s.max_K * s.ST * es > (size_t)dev_smem) s.ST /= 2;
+  s.cell_smem = 3 * (size_t)s.max_m * s.max_K * s.ST * es;
+  MSS_REQUIRE(s.cell_smem <= (size_t)dev_smem, MSS_ERR_INVALID_ARG, "cell too large for shared memory");
+  s.face_smem = std::max<size_t>(16, (size_t)s.max_M * s.ST * es);
+  s.tiles = (S + s.ST - 1) / s.ST;
+  // topology
+  std::vector<int64_t> face_row(R.n_faces + 1, 0), face_minv(R.n_faces, 0);
+  std::vector<int32_t> face_two(R.n_faces, 0);
+  for (int f = 0; f < R.n_faces; ++f) {
+    face_row[f + 1] = face_row[f] + R.face_M[f];
+    face_minv[f] = R.fmass_off[f];
+    face_two[f] = R.face_cells[2 * f + 1] >= 0 ? 1 : 0;
+  }
+  s.face_rows = face_row[R.n_faces];
+  std::vector<int64_t> cell_coef(R.n_cells), cell_ghat(R.n_cells), cell_state(R.n_cells), cell_row(R.n_cells);
+  std::vector<int64_t> row_face_row;
+  std::vector<int8_t> row_side;
+  std::vector<double> coef;
+  int64_t srows = 0;
+  for (int c = 0; c < R.n_cells; ++c) {
+    const int K = R.cell_K[c], m = R.cell_m[c];
+    cell_coef[c] = (int64_t)coef.size();
+    const double *g = R.gamma.data() + R.coef_off[c];
+    coef.insert(coef.end(), g, g + (int64_t)m * K * K);
+    cell_ghat[c] = (int64_t)coef.size();
+    const double *h = R.gamma_hat.data() + R.coef_off[c] + (int64_t)K * K;
+    coef.insert(coef.end(), h, h + (int64_t)(m - 1) * K * K);
+    cell_state[c] = srows;
+    srows += (int64_t)(m - 1) * K;
+    cell_row[c] = (int64_t)row_face_row.size();
+    for (int k = R.cell_face_ptr[c]; k < R.cell_face_ptr[c + 1]; ++k) {
+      const int f = R.cell_faces[k];
+      const int8_t side = R.face_cells[2 * f] == c ? 0 : 1;
+      for (int r = 0; r < R.face_M[f]; ++r) {
+        row_face_row.push_back(face_row[f] + r);
+        row_side.push_back(side);
+      }
+    }
+  }
+  s.cell_rows = srows;
+  std::vector<double> minv(R.fmass_off[R.n_faces]);
+  for (int f = 0; f < R.n_faces; ++f) {
+    auto inv = inverse(R.face_mass.data() + R.fmass_off[f], R.face_M[f]);
+    std::copy(inv.begin(), inv.end(), minv.begin() + R.fmass_off[f]);
+  }
+  // sources grouped per face
+  std::vector<int32_t> fsrc_ptr(R.n_faces + 1, 0), fsrc_index;
+  std::vector<int64_t> fsrc_val;
+  std::vector<int64_t> src_off(R.src_face.size() + 1, 0);
+  for (size_t e = 0; e < R.src_face.size(); ++e) src_off[e + 1] = src_off[e] + R.face_M[R.src_face[e]];
+  for (int f = 0; f < R.n_faces; ++f) {
+    for (size_t e = 0; e < R.src_face.size(); ++e)
+      if (R.src_face[e] == f) {
+        fsrc_index.push_back(R.src_index[e]);
+        fsrc_val.push_back(src_off[e]);
+      }
+    fsrc_ptr[f + 1] = (int32_t)fsrc_index.size();
+  }
+  // receivers grouped per receiver
+  std::vector<int32_t> rcv_ptr(R.n_rcv + 1, 0), rcv_face;
+  std::vector<int64_t> rcv_off, rv_off(R.rcv_face.size() + 1, 0);
+  for (size_t e = 0; e < R.rcv_face.size(); ++e) rv_off[e + 1] = rv_off[e] + R.face_M[R.rcv_face[e]];
+  for (int r = 0; r < R.n_rcv; ++r) {
+    for (size_t e = 0; e < R.rcv_face.size(); ++e)
+      if (R.rcv_index[e] == r) {
+        rcv_face.push_back(R.rcv_face[e]);
+        rcv_off.push_back(rv_off[e]);
+      }
+    rcv_ptr[r + 1] = (int32_t)rcv_face.size();
+  }
+  // corner groups
+  std::vector<int32_t> fm_ptr(R.n_faces + 1, 0), fm_member, mem_group, mem_face, grp_ptr;
+  std::vector<int64_t> mem_row;
+  if (s.corners) {
+    const int G = (int)R.cg_ptr.size() - 1;
+    grp_ptr = R.cg_ptr;
+    mem_face = R.cg_face;
+    int64_t o = 0;
+    for (size_t l = 0; l < R.cg_face.size(); ++l) {
+      mem_row.push_back(o);
+      o += R.face_M[R.cg_face[l]];
+    }
+    mem_group.assign(R.cg_face.size(), 0);
+    for (int g = 0; g < G; ++g)
+      for (int l = R.cg_ptr[g]; l < R.cg_ptr[g + 1]; ++l) mem_group[l] = g;
+    std::vector<std::vector<int32_t>> per(R.n_faces);
+    for (size_t l = 0; l < R.cg_face.size(); ++l) per[R.cg_face[l]].push_back((int32_t)l);
+    for (int f = 0; f < R.n_faces; ++f) {
+      fm_member.insert(fm_member.end(), per[f].begin(), per[f].end());
+      fm_ptr[f + 1] = (int32_t)fm_member.size();
+      s.max_nm = std::max<int>(s.max_nm, (int)per[f].size());
+    }
+  }
+  s.corner_smem = std::max<size_t>(16, (size_t)s.max_nm * s.ST * es);
+  SimDev &d = s.d;
+  upload(d.cell_K, R.cell_K);
+  upload(d.cell_m, R.cell_m);
+  upload(d.cell_coef, cell_coef);
+  upload(d.cell_ghat, cell_ghat);
+  upload(d.cell_state, cell_state);
+  upload(d.cell_row, cell_row);
+  upload(d.row_face_row, row_face_row);
+  upload(d.row_side, row_side);
+  upload(d.face_M, R.face_M);
+  upload(d.face_two, face_two);
+  upload(d.face_row, face_row);
+  upload(d.face_minv, face_minv);
+  upload(d.fsrc_ptr, fsrc_ptr);
+  upload(d.fsrc_index, fsrc_index);
+  upload(d.fsrc_val, fsrc_val);
+  upload(d.rcv_ptr, rcv_ptr);
+  upload(d.rcv_face, rcv_face);
+  upload(d.rcv_off, rcv_off);
+  upload(d.fm_ptr, fm_ptr);
+  upload(d.fm_member, fm_member);
+  upload(d.mem_group, mem_group);
+  upload(d.mem_face, mem_face);
+  upload(d.grp_ptr, grp_ptr);
+  upload(d.mem_row, mem_row);
+  auto up = [&](DevMem &m, const std::vector<double> &v) {
+    if (prec == MSS_FP64) upload_as<double>(m, v);
+    else upload_as<float>(m, v);
+  };
+  up(d.coef, coef);
+  up(d.minv, minv);
+  up(d.src_val, R.src_vals);
+  up(d.rcv_val, R.rcv_vals);
+  up(d.cg_rows, s.corners ? R.cg_rows : std::vector<double>());
+  up(d.cg_w, s.corners ? R.cg_weight : std::vector<double>());
+  for (int l = 0; l < 2; ++l) {
+    d.fstate[l].alloc((size_t)s.face_rows * S * es);
+    d.cstate[l].alloc((size_t)std::max<int64_t>(1, s.cell_rows) * S * es);
+  }
+  d.flux.alloc((size_t)s.face_rows * 2 * S * es);
+  d.ftmp.alloc(s.corners ? (size_t)s.face_rows * S * es : 16);
+  MSS_CUDA(cudaMemset(d.flux.p, 0, d.flux.bytes));
+  int64_t bytes = 0;
+  for (DevMem *m : {&d.cell_K, &d.cell_m, &d.cell_coef, &d.cell_ghat, &d.cell_state, &d.cell_row, &d.row_face_row,
+                    &d.row_side, &d.face_M, &d.face_two, &d.face_row, &d.face_minv, &d.fsrc_ptr, &d.fsrc_index,
+                    &d.fsrc_val, &d.rcv_ptr, &d.rcv_face, &d.rcv_off, &d.fm_ptr, &d.fm_member, &d.mem_group,
+                    &d.mem_face, &d.grp_ptr, &d.mem_row, &d.coef, &d.minv, &d.src_val, &d.rcv_val, &d.cg_rows,
+                    &d.cg_w, &d.fstate[0], &d.fstate[1], &d.cstate[0], &d.cstate[1], &d.flux, &d.ftmp})
+    bytes += (int64_t)m->bytes;
+  s.dev_bytes = bytes;
+}
+
+static void sim_reset(mss_sim &s, cudaStream_t st) {
+  for (int l = 0; l < 2; ++l) {
+    MSS_CUDA(cudaMemsetAsync(s.d.fstate[l].p, 0, s.d.fstate[l].bytes, st));
+    MSS_CUDA(cudaMemsetAsync(s.d.cstate[l].p, 0, s.d.cstate[l].bytes, st));
+  }
+  s.cur = 0;
+  s.steps = 0;
+}
+
+// Host FP64 <-> device state of precision T.
+static void state_io(mss_sim &s, double *now, double *old, const double *inow, const double *iold) {
+  const size_t es = s.prec == MSS_FP64 ? 8 : 4;
+  const int64_t nf = s.face_rows * s.n_src, nc = s.cell_rows * s.n_src;
+  std::vector<unsigned char> buf((size_t)(nf + nc) * es);
+  for (int lv = 0; lv < 2; ++lv) {
+    const int slot = lv == 0 ? s.cur : (s.cur ^ 1);
+    if (now || old) {
+      double *dst = lv == 0 ? now : old;
+      MSS_CUDA(cudaMemcpy(buf.data(), s.d.fstate[slot].p, nf * es, cudaMemcpyDeviceToHost));
+      if (nc) MSS_CUDA(cudaMemcpy(buf.data() + nf * es, s.d.cstate[slot].p, nc * es, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < nf + nc; ++i)
+        dst[i] = es == 8 ? reinterpret_cast<double *>(buf.data())[i] : reinterpret_cast<float *>(buf.data())[i];
+    } else {
+      const double *src = lv == 0 ? inow : iold;
+      for (int64_t i = 0; i < nf + nc; ++i) {
+        if (es == 8) reinterpret_cast<double *>(buf.data())[i] = src[i];
+        else reinterpret_cast<float *>(buf.data())[i] = (float)src[i];
+      }
+      MSS_CUDA(cudaMemcpy(s.d.fstate[slot].p, buf.data(), nf * es, cudaMemcpyHostToDevice));
+      if (nc) MSS_CUDA(cudaMemcpy(s.d.cstate[slot].p, buf.data() + nf * es, nc * es, cudaMemcpyHostToDevice));
+    }
+  }
+}
+
+}  // namespace mss
+
+using namespace mss;
+
+extern "C" {
+
+mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32_t corner_correction, mss_sim **out) {
+  return guard([&] {
+    MSS_REQUIRE(r && out, MSS_ERR_INVALID_ARG, "null argument");
+    auto s = std::make_unique<mss_sim>();
+    sim_create(*s, r->r, precision, tau, corner_correction);
+    sim_reset(*s, 0);
+    MSS_CUDA(cudaStreamSynchronize(0));
+    *out = s.release();
+  });
+}
+
+mss_status mss_sim_info(const mss_sim *s, int64_t info[8]) {
+  return guard([&] {
+    MSS_REQUIRE(s && info, MSS_ERR_INVALID_ARG, "null argument");
+    info[0] = s->n_src;
+    info[1] = s->n_rcv;
+    info[2] = s->prec;
+    info[3] = s->steps;
+    info[4] = (s->face_rows + s->cell_rows) * s->n_src;
+    info[5] = s->dev_bytes;
+    info[6] = s->corners ? 3 : 2;
+    info[7] = s->ST;
+  });
+}
+
+mss_status mss_sim_reset(mss_sim *s, void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(s, MSS_ERR_INVALID_ARG, "null sim");
+    sim_reset(*s, (cudaStream_t)stream);
+  });
+}
+
+mss_status mss_step(mss_sim *s, int64_t n_steps, const double *waveform, void *traces, int32_t use_graph,
+                    void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(s && waveform && traces && n_steps >= 0, MSS_ERR_INVALID_ARG, "bad argument");
+    if (n_steps == 0) return;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->prec == MSS_FP64) step_dispatch<double>(*s, n_steps, waveform, traces, use_graph, st);
+    else step_dispatch<float>(*s, n_steps, waveform, traces, use_graph, st);
+  });
+}
+
+mss_status mss_step_profile(mss_sim *s, int64_t n_steps, const double *waveform, void *traces, double ms[3],
+                            void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(s && waveform && traces && ms && n_steps > 0, MSS_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->prec == MSS_FP64) profile_dispatch<double>(*s, n_steps, waveform, traces, ms, st);
+    else profile_dispatch<float>(*s, n_steps, waveform, traces, ms, st);
+  });
+}
+
+mss_status mss_run_host(mss_sim *s, int64_t n_steps, const double *waveform_host, void *traces_host, void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(s && waveform_host && traces_host && n_steps > 0, MSS_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = s->prec == MSS_FP64 ? 8 : 4;
+    const size_t tb = (size_t)n_steps * s->n_rcv * s->n_src * es;
+    if (s->d.wbuf.bytes < (size_t)n_steps * 8) s->d.wbuf.alloc((size_t)n_steps * 8);
+    if (s->d.tbuf.bytes < tb) s->d.tbuf.alloc(tb);
+    MSS_CUDA(cudaMemcpyAsync(s->d.wbuf.p, waveform_host, (size_t)n_steps * 8, cudaMemcpyHostToDevice, st));
+    sim_reset(*s, st);
+    if (s->prec == MSS_FP64) step_dispatch<double>(*s, n_steps, s->d.wbuf.as<double>(), s->d.tbuf.p, 1, st);
+    else step_dispatch<float>(*s, n_steps, s->d.wbuf.as<double>(), s->d.tbuf.p, 1, st);
+    MSS_CUDA(cudaMemcpyAsync(traces_host, s->d.tbuf.p, tb, cudaMemcpyDeviceToHost, st));
+    MSS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_t *steps_taken) {
+  return guard([&] {
+    MSS_REQUIRE(s && now && old, MSS_ERR_INVALID_ARG, "null argument");
+    MSS_CUDA(cudaDeviceSynchronize());
+    state_io(const_cast<mss_sim &>(*s), now, old, nullptr, nullptr);
+    if (steps_taken) *steps_taken = s->steps;
+  });
+}
+
+mss_status mss_sim_load_state(mss_sim *s, const double *now, const double *old, int64_t steps_taken) {
+  return guard([&] {
+    MSS_REQUIRE(s && now && old && steps_taken >= 0, MSS_ERR_INVALID_ARG, "bad argument");
+    MSS_CUDA(cudaDeviceSynchronize());
+    state_io(*s, nullptr, nullptr, now, old);
+    s->steps = steps_taken;
+  });
+}
+
+void mss_sim_destroy(mss_sim *s) { delete s; }
+
+}  // extern "C"
