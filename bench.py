@@ -12,6 +12,7 @@ FP64 stepping, the same GPU's fine-grid leapfrog (FP32), receiver-trace differen
 off-line build time, per-kernel roofline, the oracle timed on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --profile N      # same workload, N eager time steps, for ncu captures
 """
 from __future__ import annotations
 
@@ -216,6 +217,11 @@ def run_native(args):
     sim = P.Sim(LR, P.FP32, tau, corner_correction=True)
     kper = int(sim.info()[6])
     tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+    if args.profile:
+        sim.step(args.profile, wd, tr, use_graph=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_steps": args.profile, "kernels_per_step": kper}))
+        return
     flush = torch.empty(int(512e6) // 4, device=dev, dtype=torch.float32)
     # ---- warm-up (captures the CUDA graph)
     for _ in range(args.warmup):
@@ -325,9 +331,9 @@ def run_native(args):
     # ---- oracle on the host cores, bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1:
-        rate, dt, nc = oracle_rate(S, 20)
-        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "all %d cells x %d sources x 20 time steps (numpy, random SPD coefficients of the "
+        rate, dt, nc = oracle_rate(S, 100)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "seconds": dt,
+               "sample": "all %d cells x %d sources x 100 time steps (numpy, random SPD coefficients of the "
                          "workload's block sizes)" % (nc, S)}
     if rank != 0:
         if dist:
@@ -360,6 +366,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--profile", type=int, default=0, help="run N eager time steps after setup and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
