@@ -270,6 +270,71 @@ mss_status mss_fine_step(mss_fine *f, int64_t n_steps, const double *waveform, v
                          void *stream);
 void mss_fine_destroy(mss_fine *f);
 
+/* ------------------------------------------------------------------------- */
+/* Stepping without allocation.  The paper has no counterpart: this entry     */
+/* point exists for callers that cannot let a library allocate device memory  */
+/* -- e.g. a solver embedded in a host application that owns every device     */
+/* buffer through its own pool and fixed budget, or a latency-critical loop   */
+/* where cudaMalloc/cudaFree would synchronise the device and stall other     */
+/* streams.  Such a caller lays out all inputs and outputs itself (same        */
+/* layout as an mss_sim, described field by field below) and the library      */
+/* only launches kernels.  The one scratch buffer the step needs -- the face   */
+/* flux exchange, [face row][side 0/1][source] -- lives in a fixed, file-scope */
+/* device array of MSS_NOALLOC_SCRATCH_BYTES that every GPU loading the        */
+/* library holds until the process exits.                                     */
+/* ------------------------------------------------------------------------- */
+#define MSS_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* All pointers are device pointers owned by the caller; values are double (MSS_FP64) or float
+ * (MSS_FP32).  Sizes: C cells, F faces, S sources, R receivers, Kc = sum of the M_f of cell c's
+ * faces, face rows FR = sum_f M_f, hidden rows HR = sum_c (m_c - 1) Kc.
+ *   cell_K[C], cell_m[C]            int32  Kc and m_c
+ *   cell_coef[C]                     int64  offset (elements) of Gamma^1 of cell c in coef; Gamma^1..m
+ *                                           follow, then Gamma-hat^2..m, each Kc x Kc row-major
+ *   cell_ghat[C]                     int64  offset of Gamma-hat^2 of cell c (= cell_coef[c] + m_c Kc^2)
+ *   cell_state[C]                    int64  first hidden row of cell c (layer 2), layers contiguous
+ *   cell_row[C]                      int64  offset of cell c in row_face_row / row_side
+ *   row_face_row[sum Kc]             int64  face row of each boundary row of each cell (face order)
+ *   row_side[sum Kc]                 int8   0 if the cell is the face's first cell, 1 otherwise
+ *   face_M[F], face_two[F]           int32  modes of face f; 1 if the face has two cells
+ *   face_row[F], face_minv[F]        int64  first face row of f; offset of M_f^{-1} (M_f x M_f) in minv
+ *   fsrc_ptr[F+1], fsrc_index[], fsrc_val[]   sources per face: source index and offset of its
+ *                                           M_f projected values in src_val
+ *   rcv_ptr[R+1], rcv_face[], rcv_off[]       receivers: faces and offsets of the M_f values in rcv_val
+ *   coef, minv, src_val, rcv_val     values as described
+ *   face_state[2]  FR x S, cell_state_buf[2]  HR x S: two time levels; level `cur` is "now".
+ * max_K, max_m, max_M: maxima of Kc, m_c, M_f.  cur is advanced by the call. */
+typedef struct mss_step_buffers {
+  int32_t precision, n_cells, n_faces, n_src, n_rcv, max_K, max_m, max_M, cur, reserved;
+  int64_t face_rows;
+  double tau;
+  const int32_t *cell_K, *cell_m;
+  const int64_t *cell_coef, *cell_ghat, *cell_state, *cell_row, *row_face_row;
+  const int8_t *row_side;
+  const int32_t *face_M, *face_two;
+  const int64_t *face_row, *face_minv;
+  const int32_t *fsrc_ptr, *fsrc_index;
+  const int64_t *fsrc_val;
+  const int32_t *rcv_ptr, *rcv_face;
+  const int64_t *rcv_off;
+  const void *coef, *minv, *src_val, *rcv_val;
+  void *face_state[2], *cell_state_buf[2];
+} mss_step_buffers;
+
+/* n_steps of the on-line step (Algorithm alg1red stage 2 without the Appendix D correction),
+ * launched eagerly on `stream` with the flux exchange in the library's fixed scratch array.
+ * waveform: device FP64, n_steps samples; traces: device [n_steps][R][S] of the precision.
+ * Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).  The first call on a
+ * device looks up the scratch array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call on a device shares the
+ * one scratch array and leaves its contents behind (the step writes every flux slot before it
+ * reads it, so nothing needs clearing); calls that overlap on the GPU (different streams, or
+ * different threads) race on it and must be serialised by the caller.
+ * Errors: INVALID_ARG (null pointers, counts, precision), INVALID_ARG if 2 FR S x element size
+ * exceeds MSS_NOALLOC_SCRATCH_BYTES, CUDA. */
+mss_status mss_step_noalloc(mss_step_buffers *b, int64_t n_steps, const double *waveform, void *traces,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

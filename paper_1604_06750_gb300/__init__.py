@@ -49,6 +49,19 @@ class _RomDesc(C.Structure):
                 ("face_mass", C.c_void_p)]
 
 
+class StepBuffers(C.Structure):
+    """mss_step_buffers: caller-owned device buffers of the allocation-free step (see mss.h)."""
+
+    _fields_ = [(n, C.c_int32) for n in ("precision", "n_cells", "n_faces", "n_src", "n_rcv", "max_K", "max_m",
+                                          "max_M", "cur", "reserved")] + \
+               [("face_rows", C.c_int64), ("tau", C.c_double)] + \
+               [(n, C.c_void_p) for n in ("cell_K", "cell_m", "cell_coef", "cell_ghat", "cell_state", "cell_row",
+                                          "row_face_row", "row_side", "face_M", "face_two", "face_row", "face_minv",
+                                          "fsrc_ptr", "fsrc_index", "fsrc_val", "rcv_ptr", "rcv_face", "rcv_off",
+                                          "coef", "minv", "src_val", "rcv_val")] + \
+               [("face_state", C.c_void_p * 2), ("cell_state_buf", C.c_void_p * 2)]
+
+
 _lib = None
 
 # (name, restype, argtypes); void* for every pointer
@@ -90,6 +103,7 @@ _SIGS = [
     ("mss_fine_reset", C.c_int32, [_P, _P]),
     ("mss_fine_step", C.c_int32, [_P, C.c_int64, _P, _P, C.c_int32, _P]),
     ("mss_fine_destroy", None, [_P]),
+    ("mss_step_noalloc", C.c_int32, [_P, C.c_int64, _P, _P, _P]),
 ]
 
 EXPORTED = [s[0] for s in _SIGS]
@@ -389,6 +403,12 @@ class Sim(_Handle):
     def load_state(self, now, old, steps: int):
         a, b = _arr(now, np.float64), _arr(old, np.float64)
         _check(lib().mss_sim_load_state(self._h, _ptr(a), _ptr(b), int(steps)))
+
+
+def step_noalloc(buffers: StepBuffers, n_steps: int, waveform, traces, stream=None):
+    """mss_step_noalloc: n_steps with caller-owned buffers; advances ``buffers.cur``."""
+    _check(lib().mss_step_noalloc(C.byref(buffers), int(n_steps), _devptr(waveform), _devptr(traces),
+                                  _stream(stream)))
 
 
 class FineSim(_Handle):

@@ -19,6 +19,9 @@
 #include <cmath>
 #include <map>
 #include <numeric>
+#include <cstring>
+#include <mutex>
+#include <string>
 #include <tuple>
 
 #include "cuda_util.h"
@@ -701,9 +704,143 @@ static void state_io(mss_sim &s, double *now, double *old, const double *inow, c
 
 }  // namespace mss
 
+// ------------------------------------------------------------------ stepping without allocation
+// The flux exchange of the allocation-free step lives in this fixed file-scope array; host code
+// must not pass the symbol itself to a kernel (in host code it names a host-side stand-in), so
+// its device address is looked up once per device and cached.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MSS_NOALLOC_SCRATCH_BYTES];
+
+namespace mss {
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];
+
+static void *noalloc_scratch() {
+  int dev = 0;
+  MSS_CUDA(cudaGetDevice(&dev));
+  MSS_REQUIRE(dev >= 0 && dev < 256, MSS_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    MSS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  return g_noalloc_addr[dev];
+}
+
+template <typename T, int ST>
+static void noalloc_impl(mss_step_buffers &b, int64_t n, const double *w, T *traces, cudaStream_t st, void *scratch) {
+  StepArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.cell_K = b.cell_K;
+  a.cell_m = b.cell_m;
+  a.cell_coef = b.cell_coef;
+  a.cell_ghat = b.cell_ghat;
+  a.cell_state = b.cell_state;
+  a.cell_row = b.cell_row;
+  a.row_face_row = b.row_face_row;
+  a.row_side = b.row_side;
+  a.face_M = b.face_M;
+  a.face_two = b.face_two;
+  a.face_row = b.face_row;
+  a.face_minv = b.face_minv;
+  a.fsrc_ptr = b.fsrc_ptr;
+  a.fsrc_index = b.fsrc_index;
+  a.fsrc_val = b.fsrc_val;
+  a.rcv_ptr = b.rcv_ptr;
+  a.rcv_face = b.rcv_face;
+  a.rcv_off = b.rcv_off;
+  a.coef = (const T *)b.coef;
+  a.minv = (const T *)b.minv;
+  a.src_val = (const T *)b.src_val;
+  a.rcv_val = (const T *)b.rcv_val;
+  a.fstate0 = (T *)b.face_state[0];
+  a.fstate1 = (T *)b.face_state[1];
+  a.cstate0 = (T *)b.cell_state_buf[0];
+  a.cstate1 = (T *)b.cell_state_buf[1];
+  a.flux = (T *)scratch;
+  a.ftmp = nullptr;
+  a.S = b.n_src;
+  a.n_cells = b.n_cells;
+  a.n_faces = b.n_faces;
+  a.n_rcv = b.n_rcv;
+  a.corners = 0;
+  a.tau2 = (T)(b.tau * b.tau);
+  const size_t es = sizeof(T);
+  const int tiles = (b.n_src + ST - 1) / ST;
+  const size_t cell_smem = 3 * (size_t)b.max_m * b.max_K * ST * es;
+  const size_t face_smem = std::max<size_t>(16, (size_t)b.max_M * ST * es);
+  int dev = 0, dev_smem = 0;
+  MSS_CUDA(cudaGetDevice(&dev));
+  MSS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  MSS_REQUIRE(cell_smem <= (size_t)dev_smem, MSS_ERR_INVALID_ARG, "cell too large for shared memory");
+  MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem));
+  MSS_CUDA(cudaFuncSetAttribute(k_face<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem));
+  const int per = kFaceThreads / ST;
+  const int rcv_blocks = (b.n_rcv + per - 1) / per;
+  const dim3 gc(b.n_cells, tiles), gf(b.n_faces + rcv_blocks, tiles);
+  int cur = b.cur & 1;
+  for (int64_t j = 0; j < n; ++j) {
+    k_cell<T, ST><<<gc, kCellThreads, cell_smem, st>>>(a, cur);
+    k_face<T, ST><<<gf, kFaceThreads, face_smem, st>>>(a, cur, w + j, traces + j * (int64_t)b.n_rcv * b.n_src);
+    cur ^= 1;
+  }
+  MSS_CUDA(cudaGetLastError());
+  b.cur = cur;
+}
+
+template <typename T>
+static void noalloc_dispatch(mss_step_buffers &b, int64_t n, const double *w, void *traces, cudaStream_t st,
+                             void *scratch) {
+  const int S = b.n_src;
+  const size_t es = sizeof(T);
+  int ST = S <= 1 ? 1 : S <= 2 ? 2 : S <= 4 ? 4 : S <= 8 ? 8 : 16;
+  int dev = 0, dev_smem = 0;
+  MSS_CUDA(cudaGetDevice(&dev));
+  MSS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  while (ST > 1 && 3 * (size_t)b.max_m * b.max_K * ST * es > (size_t)dev_smem) ST /= 2;
+  switch (ST) {
+    case 1: noalloc_impl<T, 1>(b, n, w, (T *)traces, st, scratch); break;
+    case 2: noalloc_impl<T, 2>(b, n, w, (T *)traces, st, scratch); break;
+    case 4: noalloc_impl<T, 4>(b, n, w, (T *)traces, st, scratch); break;
+    case 8: noalloc_impl<T, 8>(b, n, w, (T *)traces, st, scratch); break;
+    default: noalloc_impl<T, 16>(b, n, w, (T *)traces, st, scratch); break;
+  }
+}
+
+}  // namespace mss
+
 using namespace mss;
 
 extern "C" {
+
+mss_status mss_step_noalloc(mss_step_buffers *b, int64_t n_steps, const double *waveform, void *traces,
+                            void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(b && waveform && traces && n_steps >= 0, MSS_ERR_INVALID_ARG, "bad argument");
+    MSS_REQUIRE(b->precision == MSS_FP64 || b->precision == MSS_FP32, MSS_ERR_INVALID_ARG,
+                "precision must be FP64 or FP32");
+    MSS_REQUIRE(b->n_cells >= 1 && b->n_faces >= 1 && b->n_src >= 1 && b->n_rcv >= 0 && b->max_K >= 1 &&
+                    b->max_m >= 1 && b->max_M >= 1 && b->face_rows >= 1 && b->tau > 0,
+                MSS_ERR_INVALID_ARG, "bad sizes in mss_step_buffers");
+    MSS_REQUIRE(b->cell_K && b->cell_m && b->cell_coef && b->cell_ghat && b->cell_state && b->cell_row &&
+                    b->row_face_row && b->row_side && b->face_M && b->face_two && b->face_row && b->face_minv &&
+                    b->fsrc_ptr && b->fsrc_index && b->fsrc_val && b->rcv_ptr && b->rcv_face && b->rcv_off &&
+                    b->coef && b->minv && b->src_val && b->rcv_val && b->face_state[0] && b->face_state[1] &&
+                    b->cell_state_buf[0] && b->cell_state_buf[1],
+                MSS_ERR_INVALID_ARG, "null pointer in mss_step_buffers");
+    const size_t es = b->precision == MSS_FP64 ? 8 : 4;
+    const size_t need = (size_t)b->face_rows * 2 * (size_t)b->n_src * es;
+    MSS_REQUIRE(need <= MSS_NOALLOC_SCRATCH_BYTES, MSS_ERR_INVALID_ARG,
+                "flux exchange needs " + std::to_string(need) + " bytes, above the fixed scratch of " +
+                    std::to_string((size_t)MSS_NOALLOC_SCRATCH_BYTES) + " bytes");
+    if (n_steps == 0) return;
+    void *scratch = noalloc_scratch();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->precision == MSS_FP64) noalloc_dispatch<double>(*b, n_steps, waveform, traces, st, scratch);
+    else noalloc_dispatch<float>(*b, n_steps, waveform, traces, st, scratch);
+  });
+}
 
 mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32_t corner_correction, mss_sim **out) {
   return guard([&] {
