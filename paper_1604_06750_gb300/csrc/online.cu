@@ -8,7 +8,8 @@
 //   k_face   -- per (face, source tile): u~_f <- 2u~_f - u~_f,old + tau^2 M_f^{-1}(sum of the
 //               cells' F^1 slices - g~_f w(t_n)) (Eq. bdrytstep, step 2.3); extra blocks sample
 //               the receivers (Eq. solatrec) from the state before the update;
-//   k_corner -- optional Appendix D correction of the new face level.
+//   k_corner -- optional Appendix D correction of the new face level, on the faces that carry
+//               hanging nodes (their values u^ are computed by k_face).
 // U^1 of a cell is gathered from the face state (Eq. contred: one state per face, shared by
 // both cells).  Coefficient matrices are symmetric; the thread that owns output row r reads
 // Gamma[c][r] for c = 0..K-1, so the threads of a warp read consecutive addresses.
@@ -43,97 +44,152 @@ struct StepArgs {
   // receivers
   const int32_t *rcv_ptr, *rcv_face;
   const int64_t *rcv_off;
-  // corners: members listed per face (fm_*), per corner group (grp_ptr), member data (mem_*)
-  const int32_t *fm_ptr, *fm_member, *mem_group, *mem_face, *grp_ptr;
+  // corners: members listed per face (fm_*), per corner group (grp_ptr), member data (mem_*),
+  // faces that carry members (cfaces)
+  const int32_t *fm_ptr, *fm_member, *mem_group, *mem_face, *grp_ptr, *cfaces;
   const int64_t *mem_row;
   // values
   const T *coef, *minv, *src_val, *rcv_val, *cg_rows, *cg_w;
-  T *fstate0, *fstate1, *cstate0, *cstate1, *flux, *ftmp;
+  T *fstate0, *fstate1, *cstate0, *cstate1, *flux, *uhat;
   int S, n_cells, n_faces, n_rcv, corners;
   T tau2;
 };
 
 constexpr int kCellThreads = 256;
 constexpr int kFaceThreads = 128;
+constexpr int kChunk = 8;      // coefficients loaded ahead per thread (register pipeline)
+
+// acc[s] = sum_c G[c*K] * X[c*ST + s] for the thread's output row (G already offset by the row).
+// The column stream of G is software-pipelined in registers: the next kChunk loads are issued
+// before the current kChunk values are consumed, so ~2 kChunk loads per thread are in flight.
+template <typename T, int ST>
+__device__ __forceinline__ void row_times_block(const T *__restrict__ G, int K, const T *__restrict__ X,
+                                                T (&acc)[ST]) {
+#pragma unroll
+  for (int s = 0; s < ST; ++s) acc[s] = T(0);
+  T g[kChunk], gn[kChunk];
+#pragma unroll
+  for (int j = 0; j < kChunk; ++j) g[j] = j < K ? __ldg(G + (size_t)j * K) : T(0);
+  for (int c0 = 0; c0 < K; c0 += kChunk) {
+    const int c1 = c0 + kChunk;
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) gn[j] = (c1 + j < K) ? __ldg(G + (size_t)(c1 + j) * K) : T(0);
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+      if (c0 + j < K) {
+        const T *x = X + (c0 + j) * ST;
+#pragma unroll
+        for (int s = 0; s < ST; ++s) acc[s] += g[j] * x[s];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) g[j] = gn[j];
+  }
+}
+
+// 16-byte vector type of T (4 floats or 2 doubles)
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
 
 template <typename T, int ST>
-__global__ void __launch_bounds__(kCellThreads) k_cell(const StepArgs<T> a, const int cur) {
+__global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 4 : 2) k_cell(const StepArgs<T> a, const int cur) {
   const int cell = blockIdx.x;
   const int s0 = blockIdx.y * ST;
   const int K = a.cell_K[cell], m = a.cell_m[cell];
   const int ns = min(ST, a.S - s0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *U = reinterpret_cast<T *>(smem_raw);        // layers 1..m, [k][r][s]
-  T *D = U + (size_t)m * K * ST;                 // U^{k+1} - U^k, later F^k - F^{k-1}
-  T *F = D + (size_t)m * K * ST;                 // fluxes F^k
+  T *X = reinterpret_cast<T *>(smem_raw);        // U (layers 1..m, [k][r][s]), then F^k
+  T *D = X + (size_t)m * K * ST;                 // U^{k+1} - U^k, then F^k - F^{k-1}
+  int64_t *rows = reinterpret_cast<int64_t *>(D + (size_t)m * K * ST);   // K boundary rows: face row*2+side
   const T *fs = cur ? a.fstate1 : a.fstate0;
   const T *cs = cur ? a.cstate1 : a.cstate0;
   T *cso = cur ? a.cstate0 : a.cstate1;
   const int64_t rp = a.cell_row[cell];
   const int64_t so = a.cell_state[cell];
   const int S = a.S;
-  for (int i = threadIdx.x; i < K * ST; i += blockDim.x) {
-    const int r = i / ST, s = i - r * ST;
-    U[i] = s < ns ? fs[a.row_face_row[rp + r] * S + s0 + s] : T(0);
-  }
-  for (int i = threadIdx.x; i < (m - 1) * K * ST; i += blockDim.x) {
-    const int r = i / ST, s = i - r * ST;
-    U[(size_t)K * ST + i] = s < ns ? cs[(so + r) * S + s0 + s] : T(0);
+  for (int r = threadIdx.x; r < K; r += blockDim.x) rows[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
+  __syncthreads();
+  using V = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  // vector path needs whole vectors of sources inside the tile and aligned rows
+  const bool vec = (ST >= VN) && (ST % VN == 0) && (ns == ST) && (S % VN == 0) && (s0 % VN == 0);
+  if (vec) {
+    constexpr int NV = ST >= VN ? ST / VN : 1;
+    for (int i = threadIdx.x; i < K * NV; i += blockDim.x) {
+      const int r = i / NV, v = i - r * NV;
+      reinterpret_cast<V *>(X)[i] = *reinterpret_cast<const V *>(fs + (rows[r] >> 1) * S + s0 + v * VN);
+    }
+    for (int i = threadIdx.x; i < (m - 1) * K * NV; i += blockDim.x) {
+      const int r = i / NV, v = i - r * NV;
+      reinterpret_cast<V *>(X + (size_t)K * ST)[i] = *reinterpret_cast<const V *>(cs + (so + r) * S + s0 + v * VN);
+    }
+  } else {
+    for (int i = threadIdx.x; i < K * ST; i += blockDim.x) {
+      const int r = i / ST, s = i - r * ST;
+      X[i] = s < ns ? fs[(rows[r] >> 1) * S + s0 + s] : T(0);
+    }
+    for (int i = threadIdx.x; i < (m - 1) * K * ST; i += blockDim.x) {
+      const int r = i / ST, s = i - r * ST;
+      X[(size_t)K * ST + i] = s < ns ? cs[(so + r) * S + s0 + s] : T(0);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < m * K * ST; i += blockDim.x) {
     const int k = i / (K * ST);
-    D[i] = (k + 1 < m ? U[i + (size_t)K * ST] : T(0)) - U[i];
+    D[i] = (k + 1 < m ? X[i + (size_t)K * ST] : T(0)) - X[i];
   }
   __syncthreads();
+  // fluxes F^k = Gamma^k D^k into X (U is not needed any more: the "now" level is re-read below)
   const T *G = a.coef + a.cell_coef[cell];
   for (int it = threadIdx.x; it < m * K; it += blockDim.x) {
     const int k = it / K, r = it - k * K;
-    const T *Gk = G + (size_t)k * K * K + r;
-    const T *Dk = D + (size_t)k * K * ST;
     T acc[ST];
+    row_times_block<T, ST>(G + (size_t)k * K * K + r, K, D + (size_t)k * K * ST, acc);
 #pragma unroll
-    for (int s = 0; s < ST; ++s) acc[s] = T(0);
-    for (int c = 0; c < K; ++c) {
-      const T g = Gk[(size_t)c * K];
-#pragma unroll
-      for (int s = 0; s < ST; ++s) acc[s] += g * Dk[c * ST + s];
-    }
-#pragma unroll
-    for (int s = 0; s < ST; ++s) F[(size_t)k * K * ST + r * ST + s] = acc[s];
+    for (int s = 0; s < ST; ++s) X[(size_t)k * K * ST + r * ST + s] = acc[s];
   }
   __syncthreads();
-  // exchange: this cell's F^1 on each of its faces
-  for (int i = threadIdx.x; i < K * ST; i += blockDim.x) {
-    const int r = i / ST, s = i - r * ST;
-    if (s < ns) a.flux[(a.row_face_row[rp + r] * 2 + a.row_side[rp + r]) * S + s0 + s] = F[i];
+  // exchange: this cell's F^1 on each of its faces; E^k = F^k - F^{k-1} into D
+  if (vec) {
+    constexpr int NV = ST >= VN ? ST / VN : 1;
+    for (int i = threadIdx.x; i < K * NV; i += blockDim.x) {
+      const int r = i / NV, v = i - r * NV;
+      *reinterpret_cast<V *>(a.flux + rows[r] * S + s0 + v * VN) = reinterpret_cast<const V *>(X)[i];
+    }
+  } else {
+    for (int i = threadIdx.x; i < K * ST; i += blockDim.x) {
+      const int r = i / ST, s = i - r * ST;
+      if (s < ns) a.flux[rows[r] * S + s0 + s] = X[i];
+    }
   }
   for (int i = threadIdx.x; i < (m - 1) * K * ST; i += blockDim.x) {
     const size_t j = (size_t)K * ST + i;
-    D[j] = F[j] - F[j - (size_t)K * ST];
+    D[j] = X[j] - X[j - (size_t)K * ST];
   }
   __syncthreads();
   const T *H = a.coef + a.cell_ghat[cell];
   const T tau2 = a.tau2;
   for (int it = threadIdx.x; it < (m - 1) * K; it += blockDim.x) {
     const int k = 1 + it / K, r = it - (k - 1) * K;
-    const T *Hk = H + (size_t)(k - 1) * K * K + r;
-    const T *Ek = D + (size_t)k * K * ST;
     T acc[ST];
+    row_times_block<T, ST>(H + (size_t)(k - 1) * K * K + r, K, D + (size_t)k * K * ST, acc);
+    const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0;
+    if (vec) {
 #pragma unroll
-    for (int s = 0; s < ST; ++s) acc[s] = T(0);
-    for (int c = 0; c < K; ++c) {
-      const T h = Hk[(size_t)c * K];
+      for (int v = 0; v < (ST >= VN ? ST / VN : 0); ++v) {
+        const V now = *reinterpret_cast<const V *>(cs + base + v * VN);
+        V old = *reinterpret_cast<const V *>(cso + base + v * VN);
+        T *o = reinterpret_cast<T *>(&old);
+        const T *nw = reinterpret_cast<const T *>(&now);
 #pragma unroll
-      for (int s = 0; s < ST; ++s) acc[s] += h * Ek[c * ST + s];
-    }
-    const T *Uk = U + (size_t)k * K * ST + r * ST;
-#pragma unroll
-    for (int s = 0; s < ST; ++s) {
-      if (s < ns) {
-        const int64_t idx = (so + (int64_t)(k - 1) * K + r) * S + s0 + s;
-        cso[idx] = T(2) * Uk[s] - cso[idx] + tau2 * acc[s];
+        for (int e = 0; e < VN; ++e) o[e] = T(2) * nw[e] - o[e] + tau2 * acc[v * VN + e];
+        *reinterpret_cast<V *>(cso + base + v * VN) = old;
       }
+    } else {
+#pragma unroll
+      for (int s = 0; s < ST; ++s)
+        if (s < ns) cso[base + s] = T(2) * cs[base + s] - cso[base + s] + tau2 * acc[s];
     }
   }
 }
@@ -148,8 +204,9 @@ __global__ void __launch_bounds__(kFaceThreads) k_face(const StepArgs<T> a, cons
   const T *fs = cur ? a.fstate1 : a.fstate0;
   if (b < a.n_faces) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sum = reinterpret_cast<T *>(smem_raw);
     const int f = b, M = a.face_M[f];
+    T *sum = reinterpret_cast<T *>(smem_raw);    // M x ST flux sums
+    T *nv = sum + (size_t)M * ST;                // M x ST new face values (corner correction only)
     const int64_t row0 = a.face_row[f];
     const bool two = a.face_two[f] != 0;
     const T wn = (T)(*w);
@@ -166,15 +223,34 @@ __global__ void __launch_bounds__(kFaceThreads) k_face(const StepArgs<T> a, cons
     }
     __syncthreads();
     const T *Mi = a.minv + a.face_minv[f];
-    const T *old = cur ? a.fstate0 : a.fstate1;
-    T *dst = a.corners ? a.ftmp : (cur ? a.fstate0 : a.fstate1);
+    T *dst = cur ? a.fstate0 : a.fstate1;        // the old level becomes the new one
     for (int i = threadIdx.x; i < M * ST; i += blockDim.x) {
       const int r = i / ST, s = i - r * ST;
-      if (s >= ns) continue;
       T acc = T(0);
       for (int c = 0; c < M; ++c) acc += Mi[(size_t)r * M + c] * sum[c * ST + s];
-      const int64_t idx = (row0 + r) * S + s0 + s;
-      dst[idx] = T(2) * fs[idx] - old[idx] + a.tau2 * acc;
+      if (s < ns) {
+        const int64_t idx = (row0 + r) * S + s0 + s;
+        const T v = T(2) * fs[idx] - dst[idx] + a.tau2 * acc;
+        dst[idx] = v;
+        if (a.corners) nv[i] = v;
+      } else if (a.corners) {
+        nv[i] = T(0);
+      }
+    }
+    if (a.corners) {
+      // values of this face's hanging nodes, u^_l = s_l . u~_f (Appendix D step 1), pre-correction
+      const int j0 = a.fm_ptr[f], nm = a.fm_ptr[f + 1] - j0;
+      if (nm == 0) return;
+      __syncthreads();
+      for (int i = threadIdx.x; i < nm * ST; i += blockDim.x) {
+        const int j = i / ST, s = i - j * ST;
+        if (s >= ns) continue;
+        const int l = a.fm_member[j0 + j];
+        const T *row = a.cg_rows + a.mem_row[l];
+        T d = T(0);
+        for (int c = 0; c < M; ++c) d += row[c] * nv[c * ST + s];
+        a.uhat[(int64_t)l * S + s0 + s] = d;
+      }
     }
   } else {
     // receivers: sample the state at this step, before it is advanced
@@ -194,12 +270,12 @@ __global__ void __launch_bounds__(kFaceThreads) k_face(const StepArgs<T> a, cons
   }
 }
 
-// Appendix D: for every hanging node l on face f (group g of copies of one corner-set node),
-// delta_l = sum_{l' in g} w_l' (s_l' . u~_{f_l'}) - s_l . u~_f, then u~_f += sum_l s_l delta_l.
-// Reads the uncorrected new level (ftmp), writes the corrected one into the state.
+// Appendix D steps 2-3 on the faces that carry hanging nodes: delta_l = sum_{l' in g} w_l' u^_l'
+// - u^_l from the pre-correction values u^ (computed by k_face), then u~_f += sum_l s_l delta_l,
+// in place on the new level (each block touches only its own face's rows).
 template <typename T, int ST>
 __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, const int cur) {
-  const int f = blockIdx.x;
+  const int f = a.cfaces[blockIdx.x];
   const int s0 = blockIdx.y * ST;
   const int ns = min(ST, a.S - s0);
   const int S = a.S;
@@ -208,25 +284,21 @@ __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, co
   T *dst = cur ? a.fstate0 : a.fstate1;
   const int j0 = a.fm_ptr[f], nm = a.fm_ptr[f + 1] - j0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *delta = reinterpret_cast<T *>(smem_raw);
+  T *delta = reinterpret_cast<T *>(smem_raw);   // nm x ST
+  T *rowsm = delta + (size_t)nm * ST;           // nm x M member rows of S_f
+  for (int i = threadIdx.x; i < nm * M; i += blockDim.x) {
+    const int j = i / M, c = i - j * M;
+    rowsm[i] = a.cg_rows[a.mem_row[a.fm_member[j0 + j]] + c];
+  }
   for (int i = threadIdx.x; i < nm * ST; i += blockDim.x) {
     const int j = i / ST, s = i - j * ST;
     T d = T(0);
     if (s < ns) {
       const int l = a.fm_member[j0 + j];
       const int g = a.mem_group[l];
-      T mean = T(0), own = T(0);
-      for (int l2 = a.grp_ptr[g]; l2 < a.grp_ptr[g + 1]; ++l2) {
-        const int f2 = a.mem_face[l2];
-        const int M2 = a.face_M[f2];
-        const T *row = a.cg_rows + a.mem_row[l2];
-        const int64_t r0 = a.face_row[f2];
-        T dot = T(0);
-        for (int c = 0; c < M2; ++c) dot += row[c] * a.ftmp[(r0 + c) * S + s0 + s];
-        mean += a.cg_w[l2] * dot;
-        if (l2 == l) own = dot;
-      }
-      d = mean - own;
+      T mean = T(0);
+      for (int l2 = a.grp_ptr[g]; l2 < a.grp_ptr[g + 1]; ++l2) mean += a.cg_w[l2] * a.uhat[(int64_t)l2 * S + s0 + s];
+      d = mean - a.uhat[(int64_t)l * S + s0 + s];
     }
     delta[i] = d;
   }
@@ -234,13 +306,9 @@ __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, co
   for (int i = threadIdx.x; i < M * ST; i += blockDim.x) {
     const int r = i / ST, s = i - r * ST;
     if (s >= ns) continue;
-    const int64_t idx = (row0 + r) * S + s0 + s;
-    T v = a.ftmp[idx];
-    for (int j = 0; j < nm; ++j) {
-      const int l = a.fm_member[j0 + j];
-      v += a.cg_rows[a.mem_row[l] + r] * delta[j * ST + s];
-    }
-    dst[idx] = v;
+    T v = T(0);
+    for (int j = 0; j < nm; ++j) v += rowsm[j * M + r] * delta[j * ST + s];
+    dst[(row0 + r) * S + s0 + s] += v;
   }
 }
 
@@ -251,7 +319,7 @@ struct SimDev {
   DevMem rcv_ptr, rcv_face, rcv_off;
   DevMem fm_ptr, fm_member, mem_group, mem_face, grp_ptr, mem_row;
   DevMem coef, minv, src_val, rcv_val, cg_rows, cg_w;
-  DevMem fstate[2], cstate[2], flux, ftmp, wbuf, tbuf;
+  DevMem fstate[2], cstate[2], flux, uhat, cfaces, wbuf, tbuf;
 };
 
 struct GraphKey {
@@ -268,7 +336,7 @@ struct GraphKey {
 struct mss_sim {
   int prec = MSS_FP64;
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
-  int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0;
+  int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
   int64_t face_rows = 0, cell_rows = 0;
   int64_t steps = 0;
   int cur = 0;
@@ -329,7 +397,8 @@ static StepArgs<T> make_args(const mss_sim &s) {
   a.cstate0 = d.cstate[0].as<T>();
   a.cstate1 = d.cstate[1].as<T>();
   a.flux = d.flux.as<T>();
-  a.ftmp = d.ftmp.as<T>();
+  a.uhat = d.uhat.as<T>();
+  a.cfaces = d.cfaces.as<int32_t>();
   a.S = s.n_src;
   a.n_cells = s.n_cells;
   a.n_faces = s.n_faces;
@@ -351,7 +420,7 @@ static void launch_steps(mss_sim &s, int64_t n, const double *w, T *traces, cuda
   const StepArgs<T> a = make_args<T>(s);
   const int per = kFaceThreads / ST;
   const int rcv_blocks = (s.n_rcv + per - 1) / per;
-  const dim3 gc(s.n_cells, s.tiles), gf(s.n_faces + rcv_blocks, s.tiles), gk(s.n_faces, s.tiles);
+  const dim3 gc(s.n_cells, s.tiles), gf(s.n_faces + rcv_blocks, s.tiles), gk(std::max(1, s.n_cfaces), s.tiles);
   int cur = s.cur;
   for (int64_t j = 0; j < n; ++j) {
     k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
@@ -404,7 +473,7 @@ static void profile_impl(mss_sim &s, int64_t n, const double *w, T *traces, doub
   const StepArgs<T> a = make_args<T>(s);
   const int per = kFaceThreads / ST;
   const int rcv_blocks = (s.n_rcv + per - 1) / per;
-  const dim3 gc(s.n_cells, s.tiles), gf(s.n_faces + rcv_blocks, s.tiles), gk(s.n_faces, s.tiles);
+  const dim3 gc(s.n_cells, s.tiles), gf(s.n_faces + rcv_blocks, s.tiles), gk(std::max(1, s.n_cfaces), s.tiles);
   cudaEvent_t ev[4];
   for (auto &e : ev) MSS_CUDA(cudaEventCreate(&e));
   double acc[3] = {0, 0, 0};
@@ -522,10 +591,11 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   s.max_M = *std::max_element(R.face_M.begin(), R.face_M.end());
   int dev_smem = 0;
   MSS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s.device));
-  while (s.ST > 1 && 3 * (size_t)s.max_m * s.max_K * s.ST * es > (size_t)dev_smem) s.ST /= 2;
-  s.cell_smem = 3 * (size_t)s.max_m * s.max_K * s.ST * es;
+  auto cell_smem = [&](int st) { return 2 * (size_t)s.max_m * s.max_K * st * es + 8 * (size_t)s.max_K; };
+  while (s.ST > 1 && cell_smem(s.ST) > (size_t)dev_smem) s.ST /= 2;
+  s.cell_smem = cell_smem(s.ST);
   MSS_REQUIRE(s.cell_smem <= (size_t)dev_smem, MSS_ERR_INVALID_ARG, "cell too large for shared memory");
-  s.face_smem = std::max<size_t>(16, (size_t)s.max_M * s.ST * es);
+  s.face_smem = std::max<size_t>(16, 2 * (size_t)s.max_M * s.ST * es);
   s.tiles = (S + s.ST - 1) / s.ST;
   // topology
   std::vector<int64_t> face_row(R.n_faces + 1, 0), face_minv(R.n_faces, 0);
@@ -593,7 +663,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
     rcv_ptr[r + 1] = (int32_t)rcv_face.size();
   }
   // corner groups
-  std::vector<int32_t> fm_ptr(R.n_faces + 1, 0), fm_member, mem_group, mem_face, grp_ptr;
+  std::vector<int32_t> fm_ptr(R.n_faces + 1, 0), fm_member, mem_group, mem_face, grp_ptr, cfaces;
   std::vector<int64_t> mem_row;
   if (s.corners) {
     const int G = (int)R.cg_ptr.size() - 1;
@@ -613,9 +683,11 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
       fm_member.insert(fm_member.end(), per[f].begin(), per[f].end());
       fm_ptr[f + 1] = (int32_t)fm_member.size();
       s.max_nm = std::max<int>(s.max_nm, (int)per[f].size());
+      if (!per[f].empty()) cfaces.push_back(f);
     }
   }
-  s.corner_smem = std::max<size_t>(16, (size_t)s.max_nm * s.ST * es);
+  s.n_cfaces = (int)cfaces.size();
+  s.corner_smem = std::max<size_t>(16, (size_t)s.max_nm * (s.ST + s.max_M) * es);
   SimDev &d = s.d;
   upload(d.cell_K, R.cell_K);
   upload(d.cell_m, R.cell_m);
@@ -641,6 +713,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   upload(d.mem_face, mem_face);
   upload(d.grp_ptr, grp_ptr);
   upload(d.mem_row, mem_row);
+  upload(d.cfaces, cfaces);
   auto up = [&](DevMem &m, const std::vector<double> &v) {
     if (prec == MSS_FP64) upload_as<double>(m, v);
     else upload_as<float>(m, v);
@@ -656,14 +729,14 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
     d.cstate[l].alloc((size_t)std::max<int64_t>(1, s.cell_rows) * S * es);
   }
   d.flux.alloc((size_t)s.face_rows * 2 * S * es);
-  d.ftmp.alloc(s.corners ? (size_t)s.face_rows * S * es : 16);
+  d.uhat.alloc(s.corners ? R.cg_face.size() * (size_t)S * es : 16);
   MSS_CUDA(cudaMemset(d.flux.p, 0, d.flux.bytes));
   int64_t bytes = 0;
   for (DevMem *m : {&d.cell_K, &d.cell_m, &d.cell_coef, &d.cell_ghat, &d.cell_state, &d.cell_row, &d.row_face_row,
                     &d.row_side, &d.face_M, &d.face_two, &d.face_row, &d.face_minv, &d.fsrc_ptr, &d.fsrc_index,
                     &d.fsrc_val, &d.rcv_ptr, &d.rcv_face, &d.rcv_off, &d.fm_ptr, &d.fm_member, &d.mem_group,
                     &d.mem_face, &d.grp_ptr, &d.mem_row, &d.coef, &d.minv, &d.src_val, &d.rcv_val, &d.cg_rows,
-                    &d.cg_w, &d.fstate[0], &d.fstate[1], &d.cstate[0], &d.cstate[1], &d.flux, &d.ftmp})
+                    &d.cg_w, &d.fstate[0], &d.fstate[1], &d.cstate[0], &d.cstate[1], &d.flux, &d.uhat, &d.cfaces})
     bytes += (int64_t)m->bytes;
   s.dev_bytes = bytes;
 }
@@ -759,7 +832,8 @@ static void noalloc_impl(mss_step_buffers &b, int64_t n, const double *w, T *tra
   a.cstate0 = (T *)b.cell_state_buf[0];
   a.cstate1 = (T *)b.cell_state_buf[1];
   a.flux = (T *)scratch;
-  a.ftmp = nullptr;
+  a.uhat = nullptr;
+  a.cfaces = nullptr;
   a.S = b.n_src;
   a.n_cells = b.n_cells;
   a.n_faces = b.n_faces;
@@ -768,8 +842,8 @@ static void noalloc_impl(mss_step_buffers &b, int64_t n, const double *w, T *tra
   a.tau2 = (T)(b.tau * b.tau);
   const size_t es = sizeof(T);
   const int tiles = (b.n_src + ST - 1) / ST;
-  const size_t cell_smem = 3 * (size_t)b.max_m * b.max_K * ST * es;
-  const size_t face_smem = std::max<size_t>(16, (size_t)b.max_M * ST * es);
+  const size_t cell_smem = 2 * (size_t)b.max_m * b.max_K * ST * es + 8 * (size_t)b.max_K;
+  const size_t face_smem = std::max<size_t>(16, 2 * (size_t)b.max_M * ST * es);
   int dev = 0, dev_smem = 0;
   MSS_CUDA(cudaGetDevice(&dev));
   MSS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -798,7 +872,7 @@ static void noalloc_dispatch(mss_step_buffers &b, int64_t n, const double *w, vo
   int dev = 0, dev_smem = 0;
   MSS_CUDA(cudaGetDevice(&dev));
   MSS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  while (ST > 1 && 3 * (size_t)b.max_m * b.max_K * ST * es > (size_t)dev_smem) ST /= 2;
+  while (ST > 1 && 2 * (size_t)b.max_m * b.max_K * ST * es + 8 * (size_t)b.max_K > (size_t)dev_smem) ST /= 2;
   switch (ST) {
     case 1: noalloc_impl<T, 1>(b, n, w, (T *)traces, st, scratch); break;
     case 2: noalloc_impl<T, 2>(b, n, w, (T *)traces, st, scratch); break;
