@@ -56,7 +56,10 @@ enum {
 };
 
 enum { MSS_DIRICHLET = 0, MSS_NEUMANN = 1 };
-enum { MSS_FP64 = 0, MSS_FP32 = 1 };
+/* Precisions of the on-line stage.  MSS_FP32_TC: FP32 state, cell products on the tensor cores
+ * (tcgen05, BF16 operands split into hi + lo parts, three products, FP32 accumulation);
+ * MSS_BF16_TC: the same with one BF16 product.  Tensor-core modes need K_i <= 128. */
+enum { MSS_FP64 = 0, MSS_FP32 = 1, MSS_FP32_TC = 2, MSS_BF16_TC = 3 };
 
 const char *mss_status_string(mss_status s);
 /* Reason of the last failed call on this thread ("" if none). */
@@ -219,10 +222,12 @@ typedef struct mss_sim mss_sim;
  *   u~_f  <- 2 u~_f - u~_f,old + tau^2 M_f^{-1} (sum_{i on f} F^1_i|_f - g~_f w(t_n))
  *   then (if enabled) the Appendix D correction of the new u~;
  * trace sample n = sum_f q~_f^T u~_f at step n (before it is advanced).
- * precision: MSS_FP64 or MSS_FP32 (state, coefficients and arithmetic).
+ * precision: MSS_FP64, MSS_FP32 (state, coefficients and arithmetic), MSS_FP32_TC or MSS_BF16_TC
+ * (FP32 state, tensor-core cell products; traces are float).
  * corner_correction: 0/1.  Needs I/O set on the ROM (n_src >= 1).
  * The sim copies what it needs from the ROM (the ROM may be destroyed afterwards).
- * Errors: INVALID_ARG, STATE (ROM without I/O), CFL (tau <= 0), CUDA, OOM. */
+ * Errors: INVALID_ARG, STATE (ROM without I/O), CFL (tau <= 0), CUDA, OOM, TIMEOUT (a tensor-core
+ * kernel's bounded wait gave up; reported by the next mss_step / mss_sim_info call). */
 mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32_t corner_correction,
                           mss_sim **out);
 /* info: [0] sources, [1] receivers, [2] precision, [3] steps taken, [4] state values per level,

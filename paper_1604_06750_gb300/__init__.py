@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmss.so")
 
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_TC, BF16_TC = 0, 1, 2, 3
 DIRICHLET, NEUMANN = 0, 1
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "KRYLOV_DEFLATION", 4: "LANCZOS_BREAKDOWN",

@@ -1,0 +1,327 @@
+// Cell phase of the on-line step on the 5th-generation tensor cores (sm_103a).
+//
+// Per (cell, source tile of NT sources), one CTA of 256 threads computes what k_cell computes:
+//   F^k = Gamma^k (U^{k+1} - U^k), k = 1..m;  publish F^1;  E^k = F^k - F^{k-1};
+//   U^k <- 2U^k - U^k_old + tau^2 Gamma-hat^k E^k, k = 2..m            (Eq. intrtstep_td)
+// with every matrix product on tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation in TMEM).
+// FP32 accuracy is kept by splitting both operands into BF16 hi + lo parts and summing three
+// products, A_hi B_hi + A_hi B_lo + A_lo B_hi (terms = 3); terms = 1 is plain BF16.
+//
+// Operands live in shared memory in the canonical no-swizzle K-major layout of 8-row x 16-byte
+// core matrices: element (row, k) of a tile with Kp columns sits at
+//   (row/8) * (16 Kp) + (k/8) * 128 + (row%8) * 16 + (k%8) * 2 bytes,
+// i.e. leading (K-direction) core stride 128 B, stride (row-direction) core stride 16 Kp B.
+// The coefficient matrices are stored in HBM already in this layout (rows rounded up to 8,
+// columns to 16, zero padded, hi then lo), so each one is a single 1-D TMA bulk copy
+// (cp.async.bulk) into a two-slot ring; the A tile is 128 rows (rows >= K stay zero).
+// B = U^{k+1} - U^k (then E^k) is staged by the threads from FP32 state, split into hi/lo.
+// The MMA issuer is one thread; TMEM holds m accumulators of NT columns.  Every wait on an
+// mbarrier is bounded; on timeout the CTA records an error, drains its own copies (bounded),
+// frees its TMEM and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+
+namespace mss {
+
+struct TcArgs {
+  const unsigned char *blob;   // per cell: 2m-1 matrices, each hi (Kr x Kp bf16) then lo, core layout
+  const int64_t *blob_off;     // per cell, bytes
+  const int32_t *Kp, *Kr;      // columns rounded up to 16, rows rounded up to 8
+  int *err;                    // set to 1 by a CTA whose wait timed out
+  int slot_bytes;              // one A slot: hi + lo of 128 rows x KpMax
+  int bbuf_bytes;              // one B buffer: hi + lo of NT rows x KpMax
+  int max_m;
+  int terms;                   // 3: split BF16 (FP32-class products), 1: plain BF16
+  unsigned tmem_cols;
+};
+
+constexpr int kTcThreads = 256;
+constexpr unsigned long long kWaitNs = 100000000ull;   // 100 ms: a wait longer than this is declared hung
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned a, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned a, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Bounded wait: false after kWaitNs, or (err != nullptr) as soon as any CTA has recorded an error.
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity, const int *err) {
+  if (mbar_try_wait(a, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try_wait(a, parity)) return true;
+    if ((it & 255) == 0) {
+      if (err && *(volatile const int *)err) return false;
+      if (globaltimer_ns() - t0 > kWaitNs) return false;
+    }
+    if (it > 32) __nanosleep(64);
+  }
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// shared-memory matrix descriptor: no swizzle, leading (K) core stride lbo, row core stride sbo
+__device__ __forceinline__ uint64_t sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(unsigned dtmem, uint64_t a, uint64_t b, uint32_t idesc, unsigned accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_ld8(unsigned taddr, float (&v)[8]) {
+  unsigned r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ unsigned core_off(int row, int k, int Kp) {
+  return (unsigned)((row >> 3) * (16 * Kp) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo, unsigned off, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+  *reinterpret_cast<__nv_bfloat16 *>(hi + off) = h;
+  *reinterpret_cast<__nv_bfloat16 *>(lo + off) = l;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float> a, const TcArgs t, const int cur) {
+  const int cell = blockIdx.x;
+  const int s0 = blockIdx.y * NT;
+  const int K = a.cell_K[cell], m = a.cell_m[cell];
+  const int Kp = t.Kp[cell], Kr = t.Kr[cell];
+  const int S = a.S;
+  const int ns = min(NT, S - s0);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char *slot[2] = {smem, smem + t.slot_bytes};
+  unsigned char *bb = smem + 2 * t.slot_bytes;                 // B buffers: max_m x bbuf_bytes
+  int64_t *rows = reinterpret_cast<int64_t *>(bb + (size_t)t.max_m * t.bbuf_bytes);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(rows + 128);   // full0 full1 empty0 empty1 done
+  unsigned *tmem_base_sm = reinterpret_cast<unsigned *>(bars + 5);
+  int *abort_sm = reinterpret_cast<int *>(tmem_base_sm + 1);
+  const unsigned full[2] = {smem_u32(bars + 0), smem_u32(bars + 1)};
+  const unsigned empty[2] = {smem_u32(bars + 2), smem_u32(bars + 3)};
+  const unsigned done = smem_u32(bars + 4);
+  const float *fs = cur ? a.fstate1 : a.fstate0;
+  const float *cs = cur ? a.cstate1 : a.cstate0;
+  float *cso = cur ? a.cstate0 : a.cstate1;
+  const int64_t rp = a.cell_row[cell], so = a.cell_state[cell];
+  const int nmat = 2 * m - 1;
+  const unsigned mat_half = (unsigned)Kr * Kp * 2;             // bytes of hi (or lo) of one matrix in HBM
+  const unsigned char *cblob = t.blob + t.blob_off[cell];
+  const uint32_t idesc = idesc_bf16(128, NT);
+
+  __shared__ int bail;
+  if (tid == 0) bail = *(volatile const int *)t.err;
+  __syncthreads();
+  if (bail) return;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_base_sm)),
+                 "r"(t.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 5; ++i) mbar_init(smem_u32(bars + i), 1);
+    *abort_sm = 0;
+    fence_mbar_init();
+  }
+  for (int r = tid; r < K; r += kTcThreads) rows[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
+  // zero the pad rows (Kr..127) of both slots (hi and lo); the copies never write them
+  for (int s = 0; s < 2; ++s) {
+    unsigned char *h = slot[s], *l = slot[s] + 256 * Kp;
+    const int pad0 = Kr * Kp * 2, pad1 = 128 * Kp * 2;
+    for (int i = pad0 / 16 + tid; i < pad1 / 16; i += kTcThreads) {
+      reinterpret_cast<int4 *>(h)[i] = make_int4(0, 0, 0, 0);
+      reinterpret_cast<int4 *>(l)[i] = make_int4(0, 0, 0, 0);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *tmem_base_sm;
+  // producer: first two matrices into the ring
+  int issued = 0;     // matrices whose copy has been issued (thread 0 only)
+  int consumed = 0;   // matrices whose copy has landed and been waited for (thread 0 only)
+  auto issue = [&](int p) {
+    const int sl = p & 1;
+    const unsigned char *src = cblob + (size_t)p * 2 * mat_half;
+    mbar_expect_tx(full[sl], 2 * mat_half);
+    bulk_g2s(smem_u32(slot[sl]), src, mat_half, full[sl]);
+    bulk_g2s(smem_u32(slot[sl] + 256 * Kp), src + mat_half, mat_half, full[sl]);
+  };
+  if (tid == 0) {
+    issue(0);
+    issued = 1;
+    if (nmat > 1) { issue(1); issued = 2; }
+  }
+  // stage B = U^{k+1} - U^k, k = 0..m-1 (U^0 = faces, U^m = 0), hi/lo, K-major core layout
+  for (int i = tid; i < m * Kp * NT; i += kTcThreads) {
+    const int k = i / (Kp * NT);
+    const int rem = i - k * Kp * NT;
+    const int r = rem / NT, c = rem - r * NT;
+    float v = 0.f;
+    if (r < K && c < ns) {
+      const float u0 = k == 0 ? fs[(rows[r] >> 1) * S + s0 + c] : cs[(so + (int64_t)(k - 1) * K + r) * S + s0 + c];
+      const float u1 = k + 1 < m ? cs[(so + (int64_t)k * K + r) * S + s0 + c] : 0.f;
+      v = u1 - u0;
+    }
+    unsigned char *h = bb + (size_t)k * t.bbuf_bytes;
+    split_store(h, h + NT * Kp * 2, core_off(c, r, Kp), v);
+  }
+  fence_async_smem();
+  __syncthreads();
+  const unsigned lbo = 128, sbo = 16u * Kp;
+  const int ksteps = Kp / 16;
+  // products p = 0..nmat-1: fluxes (p < m, B = buffer p, D column p*NT), then accelerations
+  // (p >= m, B = buffer p-m, D column (p-m)*NT); the B buffers of the second group are written
+  // by the first epilogue.
+  auto run_products = [&](int p0, int p1) {
+    for (int p = p0; p < p1; ++p) {
+      const int sl = p & 1;
+      const int bi = p < m ? p : p - m;
+      if (!mbar_wait(full[sl], (p >> 1) & 1, t.err)) { *abort_sm = 1; break; }
+      consumed = p + 1;
+      tc_fence_after();
+      const unsigned ah = smem_u32(slot[sl]), al = ah + 256 * Kp;
+      const unsigned bh = smem_u32(bb + (size_t)bi * t.bbuf_bytes), bl = bh + NT * Kp * 2;
+      const unsigned dcol = tmem + (unsigned)(bi * NT);
+      for (int kk = 0; kk < ksteps; ++kk) {
+        const unsigned o = kk * 256;
+        mma_bf16(dcol, sdesc(ah + o, lbo, sbo), sdesc(bh + o, lbo, sbo), idesc, kk > 0 ? 1u : 0u);
+        if (t.terms == 3) {
+          mma_bf16(dcol, sdesc(ah + o, lbo, sbo), sdesc(bl + o, lbo, sbo), idesc, 1u);
+          mma_bf16(dcol, sdesc(al + o, lbo, sbo), sdesc(bh + o, lbo, sbo), idesc, 1u);
+        }
+      }
+      tc_commit(empty[sl]);
+      // refill the slot of the previous product (its MMAs were queued before this one's)
+      const int q = p - 1;
+      if (q >= 0 && q + 2 < nmat && issued == q + 2) {
+        if (!mbar_wait(empty[q & 1], (q >> 1) & 1, t.err)) { *abort_sm = 1; break; }
+        issue(q + 2);
+        issued = q + 3;
+      }
+    }
+    tc_commit(done);
+  };
+  if (tid == 0) run_products(0, m);
+  const int q = warp & 3, half = warp >> 2;
+  const int r = 32 * q + lane;                     // accumulator row = TMEM lane
+  const unsigned lane_addr = (unsigned)(32 * q) << 16;
+  const int c0 = half * (NT / 2);
+  bool ok = mbar_wait(done, 0, t.err);
+  tc_fence_after();
+  // all flux MMAs are complete, so the slot of the last one can take the next matrix now
+  if (tid == 0 && ok && !*abort_sm && issued == m + 1 && m + 1 < nmat) {
+    issue(m + 1);
+    issued = m + 2;
+  }
+  // epilogue 1: publish F^1; E^k = F^k - F^{k-1} (k = 1..m-1) into B buffer k-1.
+  // tcgen05.ld is warp-wide: the decision is made uniform over the CTA first.
+  const bool go1 = __syncthreads_and(ok && !*abort_sm) != 0;
+  if (go1) {
+    for (int cc = 0; cc < NT / 2; cc += 8) {
+      float prev[8], curv[8];
+      for (int k = 0; k < m; ++k) {
+        tc_ld8(tmem + lane_addr + (unsigned)(k * NT + c0 + cc), curv);
+        if (k == 0) {
+          if (r < K) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (c0 + cc + j < ns) a.flux[rows[r] * S + s0 + c0 + cc + j] = curv[j];
+          }
+        } else if (r < Kp) {
+          unsigned char *h = bb + (size_t)(k - 1) * t.bbuf_bytes;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            split_store(h, h + NT * Kp * 2, core_off(c0 + cc + j, r, Kp), r < K ? curv[j] - prev[j] : 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) prev[j] = curv[j];
+      }
+    }
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (!go1 && tid == 0) *abort_sm = 1;
+  if (tid == 0 && go1 && m > 1) run_products(m, nmat);
+  ok = (go1 && m > 1) ? mbar_wait(done, 1, t.err) : go1;
+  tc_fence_after();
+  // epilogue 2: hidden-layer leapfrog (loads in every lane, stores for rows < K)
+  const bool go2 = __syncthreads_and(ok && !*abort_sm) != 0;
+  if (go2) {
+    const float tau2 = a.tau2;
+    for (int k = 1; k < m; ++k) {
+      for (int cc = 0; cc < NT / 2; cc += 8) {
+        float acc[8];
+        tc_ld8(tmem + lane_addr + (unsigned)((k - 1) * NT + c0 + cc), acc);
+        if (r < K) {
+          const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + c0 + cc;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (c0 + cc + j < ns) cso[base + j] = 2.f * cs[base + j] - cso[base + j] + tau2 * acc[j];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    *abort_sm = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *abort_sm) {
+    atomicExch(t.err, 1);
+    // drain this CTA's own copies still in flight (bounded) before the shared memory goes away
+    for (int p = consumed; p < issued; ++p) mbar_wait(full[p & 1], (p >> 1) & 1, nullptr);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(t.tmem_cols) : "memory");
+  }
+}
+
+}  // namespace mss

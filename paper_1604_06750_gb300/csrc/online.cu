@@ -24,6 +24,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 
 #include "cuda_util.h"
 
@@ -312,6 +313,12 @@ __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, co
   }
 }
 
+}  // namespace mss
+
+#include "cell_tc.cuh"
+
+namespace mss {
+
 // ------------------------------------------------------------------ simulation object
 struct SimDev {
   DevMem cell_K, cell_m, cell_coef, cell_ghat, cell_state, cell_row, row_face_row, row_side;
@@ -320,6 +327,7 @@ struct SimDev {
   DevMem fm_ptr, fm_member, mem_group, mem_face, grp_ptr, mem_row;
   DevMem coef, minv, src_val, rcv_val, cg_rows, cg_w;
   DevMem fstate[2], cstate[2], flux, uhat, cfaces, wbuf, tbuf;
+  DevMem tc_blob, tc_off, tc_Kp, tc_Kr, tc_err;
 };
 
 struct GraphKey {
@@ -335,6 +343,9 @@ struct GraphKey {
 
 struct mss_sim {
   int prec = MSS_FP64;
+  int tc = 0, tc_terms = 3, tc_nt = 16;       // tensor-core cell kernel
+  size_t tc_smem = 0;
+  mss::TcArgs tca{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
   int64_t face_rows = 0, cell_rows = 0;
@@ -410,9 +421,35 @@ static StepArgs<T> make_args(const mss_sim &s) {
 
 template <typename T, int ST>
 static void set_smem_attrs(const mss_sim &s) {
+  if (s.tc) {
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
+  }
   MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
   MSS_CUDA(cudaFuncSetAttribute(k_face<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.face_smem));
   MSS_CUDA(cudaFuncSetAttribute(k_corner<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.corner_smem));
+}
+
+template <int NT>
+static void launch_tc(const mss_sim &s, const StepArgs<float> &a, int cur, cudaStream_t st) {
+  const dim3 g(s.n_cells, (s.n_src + NT - 1) / NT);
+  k_cell_tc<NT><<<g, kTcThreads, s.tc_smem, st>>>(a, s.tca, cur);
+}
+
+template <typename T, int ST>
+static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (s.tc) {
+      switch (s.tc_nt) {
+        case 16: launch_tc<16>(s, a, cur, st); return;
+        case 32: launch_tc<32>(s, a, cur, st); return;
+        default: launch_tc<64>(s, a, cur, st); return;
+      }
+    }
+  }
+  const dim3 gc(s.n_cells, s.tiles);
+  k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
 }
 
 template <typename T, int ST>
@@ -423,7 +460,7 @@ static void launch_steps(mss_sim &s, int64_t n, const double *w, T *traces, cuda
   const dim3 gc(s.n_cells, s.tiles), gf(s.n_faces + rcv_blocks, s.tiles), gk(std::max(1, s.n_cfaces), s.tiles);
   int cur = s.cur;
   for (int64_t j = 0; j < n; ++j) {
-    k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
+    launch_cell<T, ST>(s, a, cur, st);
     k_face<T, ST><<<gf, kFaceThreads, s.face_smem, st>>>(a, cur, w + j, traces + j * (int64_t)s.n_rcv * s.n_src);
     if (s.corners) k_corner<T, ST><<<gk, kFaceThreads, s.corner_smem, st>>>(a, cur);
     cur ^= 1;
@@ -481,7 +518,7 @@ static void profile_impl(mss_sim &s, int64_t n, const double *w, T *traces, doub
   try {
     for (int64_t j = 0; j < n; ++j) {
       MSS_CUDA(cudaEventRecord(ev[0], st));
-      k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
+      launch_cell<T, ST>(s, a, cur, st);
       MSS_CUDA(cudaEventRecord(ev[1], st));
       k_face<T, ST><<<gf, kFaceThreads, s.face_smem, st>>>(a, cur, w + j, traces + j * (int64_t)s.n_rcv * s.n_src);
       MSS_CUDA(cudaEventRecord(ev[2], st));
@@ -567,8 +604,56 @@ static std::vector<double> inverse(const double *A, int n) {
   return inv;
 }
 
+static inline uint16_t host_bf16(float f) {   // round to nearest even
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+static inline float host_bf16_to_f(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Coefficients of every cell in the tensor-core kernel's layout: per cell the 2m-1 matrices
+// Gamma^1..Gamma^m, Gamma-hat^2..Gamma-hat^m, each as BF16 hi then lo, Kr x Kp, K-major core
+// matrices (see cell_tc.cuh).
+static void build_tc_blob(const Rom &R, std::vector<uint16_t> &blob, std::vector<int64_t> &off, std::vector<int32_t> &Kp,
+                          std::vector<int32_t> &Kr) {
+  blob.clear();
+  off.assign(R.n_cells, 0);
+  Kp.assign(R.n_cells, 0);
+  Kr.assign(R.n_cells, 0);
+  for (int c = 0; c < R.n_cells; ++c) {
+    const int K = R.cell_K[c], m = R.cell_m[c];
+    const int kp = (K + 15) / 16 * 16, kr = (K + 7) / 8 * 8;
+    Kp[c] = kp;
+    Kr[c] = kr;
+    off[c] = (int64_t)blob.size() * 2;
+    const size_t half = (size_t)kr * kp;
+    for (int p = 0; p < 2 * m - 1; ++p) {
+      const double *A = p < m ? R.gamma.data() + R.coef_off[c] + (size_t)p * K * K
+                              : R.gamma_hat.data() + R.coef_off[c] + (size_t)(p - m + 1) * K * K;
+      const size_t base = blob.size();
+      blob.resize(base + 2 * half, 0);
+      for (int r = 0; r < K; ++r)
+        for (int k = 0; k < K; ++k) {
+          const float v = (float)A[(size_t)r * K + k];
+          const uint16_t h = host_bf16(v);
+          const uint16_t l = host_bf16(v - host_bf16_to_f(h));
+          const size_t o = ((size_t)(r >> 3) * (16 * kp) + (size_t)(k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2) / 2;
+          blob[base + o] = h;
+          blob[base + half + o] = l;
+        }
+    }
+  }
+}
+
 static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corners) {
-  MSS_REQUIRE(prec == MSS_FP64 || prec == MSS_FP32, MSS_ERR_INVALID_ARG, "precision must be FP64 or FP32");
+  MSS_REQUIRE(prec == MSS_FP64 || prec == MSS_FP32 || prec == MSS_FP32_TC || prec == MSS_BF16_TC, MSS_ERR_INVALID_ARG,
+              "precision must be MSS_FP64, MSS_FP32, MSS_FP32_TC or MSS_BF16_TC");
   MSS_REQUIRE(tau > 0 && std::isfinite(tau), MSS_ERR_CFL, "tau must be positive");
   MSS_REQUIRE(R.has_io, MSS_ERR_STATE, "ROM has no sources/receivers (mss_rom_set_io*)");
   MSS_CUDA(cudaGetDevice(&s.device));
@@ -597,6 +682,46 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   MSS_REQUIRE(s.cell_smem <= (size_t)dev_smem, MSS_ERR_INVALID_ARG, "cell too large for shared memory");
   s.face_smem = std::max<size_t>(16, 2 * (size_t)s.max_M * s.ST * es);
   s.tiles = (S + s.ST - 1) / s.ST;
+  if (prec == MSS_FP32_TC || prec == MSS_BF16_TC) {
+    MSS_REQUIRE(s.max_K <= 128, MSS_ERR_INVALID_ARG, "tensor-core precisions need K_i <= 128");
+    s.tc = 1;
+    s.tc_terms = prec == MSS_FP32_TC ? 3 : 1;
+    int kpmax = 0;
+    for (int K : R.cell_K) kpmax = std::max(kpmax, (K + 15) / 16 * 16);
+    int nt = S <= 16 ? 16 : S <= 32 ? 32 : 64;
+    auto smem_of = [&](int ntv) {
+      return (size_t)2 * (2 * 128 * kpmax * 2) + (size_t)s.max_m * (2 * ntv * kpmax * 2) + 128 * 8 + 8 * 8;
+    };
+    auto cols_of = [&](int ntv) {
+      unsigned c = 32;
+      while (c < (unsigned)(s.max_m * ntv)) c <<= 1;
+      return c;
+    };
+    while (nt > 16 && (smem_of(nt) > (size_t)dev_smem || cols_of(nt) > 512)) nt /= 2;
+    MSS_REQUIRE(smem_of(nt) <= (size_t)dev_smem && cols_of(nt) <= 512, MSS_ERR_INVALID_ARG,
+                "cells too large for the tensor-core kernel");
+    s.tc_nt = nt;
+    s.tc_smem = smem_of(nt);
+    std::vector<uint16_t> blob;
+    std::vector<int64_t> off;
+    std::vector<int32_t> kp, kr;
+    build_tc_blob(R, blob, off, kp, kr);
+    upload(s.d.tc_blob, blob);
+    upload(s.d.tc_off, off);
+    upload(s.d.tc_Kp, kp);
+    upload(s.d.tc_Kr, kr);
+    upload(s.d.tc_err, std::vector<int>(1, 0));
+    s.tca.blob = s.d.tc_blob.as<unsigned char>();
+    s.tca.blob_off = s.d.tc_off.as<int64_t>();
+    s.tca.Kp = s.d.tc_Kp.as<int32_t>();
+    s.tca.Kr = s.d.tc_Kr.as<int32_t>();
+    s.tca.err = s.d.tc_err.as<int>();
+    s.tca.slot_bytes = 2 * 128 * kpmax * 2;
+    s.tca.bbuf_bytes = 2 * nt * kpmax * 2;
+    s.tca.max_m = s.max_m;
+    s.tca.terms = s.tc_terms;
+    s.tca.tmem_cols = cols_of(nt);
+  }
   // topology
   std::vector<int64_t> face_row(R.n_faces + 1, 0), face_minv(R.n_faces, 0);
   std::vector<int32_t> face_two(R.n_faces, 0);
@@ -718,7 +843,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
     if (prec == MSS_FP64) upload_as<double>(m, v);
     else upload_as<float>(m, v);
   };
-  up(d.coef, coef);
+  up(d.coef, s.tc ? std::vector<double>() : coef);
   up(d.minv, minv);
   up(d.src_val, R.src_vals);
   up(d.rcv_val, R.rcv_vals);
@@ -930,6 +1055,11 @@ mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32
 mss_status mss_sim_info(const mss_sim *s, int64_t info[8]) {
   return guard([&] {
     MSS_REQUIRE(s && info, MSS_ERR_INVALID_ARG, "null argument");
+    if (s->tc) {
+      int e = 0;
+      MSS_CUDA(cudaMemcpy(&e, s->d.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+      MSS_REQUIRE(e == 0, MSS_ERR_TIMEOUT, "a tensor-core cell kernel's bounded wait gave up");
+    }
     info[0] = s->n_src;
     info[1] = s->n_rcv;
     info[2] = s->prec;
@@ -983,6 +1113,11 @@ mss_status mss_run_host(mss_sim *s, int64_t n_steps, const double *waveform_host
     else step_dispatch<float>(*s, n_steps, s->d.wbuf.as<double>(), s->d.tbuf.p, 1, st);
     MSS_CUDA(cudaMemcpyAsync(traces_host, s->d.tbuf.p, tb, cudaMemcpyDeviceToHost, st));
     MSS_CUDA(cudaStreamSynchronize(st));
+    if (s->tc) {
+      int e = 0;
+      MSS_CUDA(cudaMemcpy(&e, s->d.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+      MSS_REQUIRE(e == 0, MSS_ERR_TIMEOUT, "a tensor-core cell kernel's bounded wait gave up");
+    }
   });
 }
 

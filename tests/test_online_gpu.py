@@ -49,6 +49,7 @@ def _lib_run(P, topo, co, src, rcv, n_src, n_rcv, w, tau, nst, prec, corners=Non
     tr = torch.zeros((nst, n_rcv, n_src), device="cuda", dtype=dt)
     sim.step(nst, wd, tr, use_graph=use_graph)
     torch.cuda.synchronize()
+    sim.info()                    # raises if a bounded device wait gave up
     return tr.cpu().numpy().astype(np.float64), sim
 
 
@@ -226,3 +227,42 @@ def test_fine_grid_gpu_parity(P, prec_tol):
     fs.step(nst, wd, tr)
     torch.cuda.synchronize()
     assert _rel(tr.cpu().numpy().astype(np.float64), ref) <= tol
+
+
+# ---------------------------------------------------------------- tensor-core cell products
+TC_TOL = {2: 1e-3, 3: 5e-2}   # FP32_TC (split BF16, three products) / BF16_TC (one product)
+
+
+@pytest.mark.parametrize("n_src", [1, 16, 37, 64])
+def test_tensor_core_parity_ragged(P, n_src):
+    topo, co, src, rcv = _random_case(n_src=n_src, seed=40 + n_src)
+    tau, nst = 0.08, 150
+    w = synth.ricker(np.arange(nst) * tau, 0.6)
+    ref = _oracle(topo, co, src, rcv, n_src, 4, w, tau, nst)
+    errs = {}
+    for prec in (P.FP32_TC, P.BF16_TC):
+        out, _ = _lib_run(P, topo, co, src, rcv, n_src, 4, w, tau, nst, prec)
+        errs[prec] = _rel(out, ref)
+        assert errs[prec] <= TC_TOL[prec], (prec, errs[prec])
+    assert errs[P.FP32_TC] < errs[P.BF16_TC]
+
+
+def test_tensor_core_uneven_cells_256_sources(P):
+    """512 cells with 3..6 S-fraction layers and 8..16 modes per face, 256 sources (the
+    many-source launch shape); the oracle steps sources 0, 77 and 255."""
+    rng = np.random.default_rng(5)
+    ms = rng.integers(3, 7, 512)
+    io = [(c, 2) for c in range(448, 512)]
+    topo = synth.box_topology((8, 8, 8), modes=16, m=ms, io_cells=io, seed=23, ragged_modes=True)
+    co = synth.random_coefficients(topo, seed=23, spread=2.0)
+    src, rcv = synth.random_io(topo, 256, 6, seed=23, density=0.01)
+    tau, nst = 0.05, 30
+    w = synth.ricker(np.arange(nst) * tau, 1.0)
+    pick = [0, 77, 255]
+    sub = [(f, pick.index(j), v) for (f, j, v) in src if j in pick]
+    ref = _oracle(topo, co, sub, rcv, 3, 6, w, tau, nst)
+    out, sim = _lib_run(P, topo, co, src, rcv, 256, 6, w, tau, nst, P.FP32_TC)
+    assert sim.info()[3] == nst
+    assert _rel(out[:, :, pick], ref) <= TC_TOL[2]
+    out32, _ = _lib_run(P, topo, co, src, rcv, 256, 6, w, tau, nst, P.FP32)
+    assert _rel(out32[:, :, pick], ref) <= FP32_TOL
