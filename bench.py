@@ -214,14 +214,17 @@ def run_native(args):
     w = synth.ricker(np.arange(nst) * tau, wl.f_peak)
     wd = torch.tensor(w, device=dev)
     stream = torch.cuda.current_stream(dev)
+    if args.profile:
+        sim = P.Sim(LR, P.FP32_TC if args.prec == "fp32_tc" else P.FP32, tau, corner_correction=True)
+        tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+        sim.step(args.profile, wd, tr, use_graph=False)
+        torch.cuda.synchronize()
+        sim.info()
+        print(json.dumps({"profile_steps": args.profile, "precision": args.prec}))
+        return
     sim = P.Sim(LR, P.FP32, tau, corner_correction=True)
     kper = int(sim.info()[6])
     tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
-    if args.profile:
-        sim.step(args.profile, wd, tr, use_graph=False)
-        torch.cuda.synchronize()
-        print(json.dumps({"profile_steps": args.profile, "kernels_per_step": kper}))
-        return
     flush = torch.empty(int(512e6) // 4, device=dev, dtype=torch.float32)
     # ---- warm-up (captures the CUDA graph)
     for _ in range(args.warmup):
@@ -286,6 +289,32 @@ def run_native(args):
                  "ms_per_launch": ms[0], "fp32_alu_frac": achieved_tf / alu_peak,
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
                  "other_kernels_ms": {"k_face": ms[1], "k_corner": ms[2]}})
+    # ---- tensor-core cell products (split BF16, FP32 accumulation), same coefficients
+    simtc = P.Sim(LR, P.FP32_TC, tau, corner_correction=True)
+    trtc = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+    for _ in range(2):
+        simtc.reset()
+        simtc.step(nst, wd, trtc, use_graph=True)
+    torch.cuda.synchronize()
+    tc_times = []
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        simtc.reset()
+        simtc.step(nst, wd, trtc, use_graph=True)
+        e1.record(stream)
+        e1.synchronize()
+        tc_times.append(e0.elapsed_time(e1) / 1e3)
+    simtc.info()
+    ttc = statistics.mean(tc_times)
+    simtc.reset()
+    ms_tc = simtc.step_profile(200, wd, trtc)
+    simtc.reset()
+    simtc.step(nst, wd, trtc, use_graph=True)
+    torch.cuda.synchronize()
+    trtc_np = trtc.double().cpu().numpy()
     # ---- FP64 stepping (same coefficients), one run
     sim64 = P.Sim(LR, P.FP64, tau, corner_correction=True)
     tr64 = torch.zeros((nst, R, S), device=dev, dtype=torch.float64)
@@ -348,6 +377,10 @@ def run_native(args):
             "clocks": ck, "gpu_launches": int(args.steps * nst * kper),
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "fp64": {"value": units / t64, "unit": UNIT, "ms": 1e3 * t64},
+            "fp32_tc": {"value": units / ttc, "unit": UNIT, "ms": 1e3 * ttc,
+                        "kernel_ms": {"k_cell_tc": ms_tc[0], "k_face": ms_tc[1], "k_corner": ms_tc[2]},
+                        "rel_l2_vs_fp64": rel(trtc_np, ref64),
+                        "note": "tcgen05 cell products, BF16 hi/lo split operands (3 products), FP32 accumulation"},
             "fine_grid": {"value": units / tfine, "unit": UNIT, "ms": 1e3 * tfine,
                           "note": "FP32 5/7-point leapfrog on the same grid, same tau and steps; cells counted on "
                                   "the same partition"},
@@ -367,6 +400,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--profile", type=int, default=0, help="run N eager time steps after setup and exit")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32_tc"], help="precision of the --profile run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
