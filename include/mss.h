@@ -276,6 +276,37 @@ mss_status mss_fine_step(mss_fine *f, int64_t n_steps, const double *waveform, v
 void mss_fine_destroy(mss_fine *f);
 
 /* ------------------------------------------------------------------------- */
+/* Learned surrogate of the off-line stage (no counterpart in the paper: it    */
+/* replaces the Krylov/Lanczos construction for repeated media; the exact      */
+/* construction stays the fallback and the judge).                            */
+/* ------------------------------------------------------------------------- */
+typedef struct mss_surrogate mss_surrogate;
+
+/* 3D CNN: 3x3x3 convolutions (pad 1) 2 -> C stride 2, stride-2 C -> C convs down to edge 2, one
+ * stride-1 C -> C conv, ReLU after each; flattened output ++ n_feat features -> dense H (ReLU) ->
+ * dense n_out.  Input x: [batch][2][cell][cell][cell] FP32, features [batch][n_feat], outputs
+ * [batch][n_out].  Weights: FP32 masters, BF16 in the forward/backward products, FP32
+ * accumulation; seeded normal initialisation.  cell: a power of two in 4..64. */
+mss_status mss_surrogate_create(int32_t cell, int32_t n_feat, int32_t n_out, int32_t channels, int32_t hidden,
+                                uint64_t seed, mss_surrogate **out);
+/* info: [0] parameters, [1] input values per sample, [2] features, [3] outputs. */
+mss_status mss_surrogate_info(const mss_surrogate *s, int64_t info[4]);
+/* FP32 parameter vector (host): per layer weights then bias, layers in order. set also resets Adam. */
+mss_status mss_surrogate_get_params(const mss_surrogate *s, float *host);
+mss_status mss_surrogate_set_params(mss_surrogate *s, const float *host);
+/* Device buffers; y: [batch][n_out]. */
+mss_status mss_surrogate_forward(mss_surrogate *s, int32_t batch, const float *x, const float *feat, float *y,
+                                 void *stream);
+/* grad (device, n_params) = d sum(dy * forward(x)) / d params (with the BF16-rounded weights). */
+mss_status mss_surrogate_backward(mss_surrogate *s, int32_t batch, const float *x, const float *feat, const float *dy,
+                                  float *grad, void *stream);
+/* One Adam step (beta 0.9 / 0.999) on the mean squared error to target [batch][n_out] (mask of 0/1
+ * weights, may be NULL); loss (device float, may be NULL) receives the batch loss. */
+mss_status mss_surrogate_train_step(mss_surrogate *s, int32_t batch, const float *x, const float *feat,
+                                    const float *target, const float *mask, float lr, float *loss, void *stream);
+void mss_surrogate_destroy(mss_surrogate *s);
+
+/* ------------------------------------------------------------------------- */
 /* Stepping without allocation.  The paper has no counterpart: this entry     */
 /* point exists for callers that cannot let a library allocate device memory  */
 /* -- e.g. a solver embedded in a host application that owns every device     */

@@ -104,6 +104,14 @@ _SIGS = [
     ("mss_fine_step", C.c_int32, [_P, C.c_int64, _P, _P, C.c_int32, _P]),
     ("mss_fine_destroy", None, [_P]),
     ("mss_step_noalloc", C.c_int32, [_P, C.c_int64, _P, _P, _P]),
+    ("mss_surrogate_create", C.c_int32, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _P]),
+    ("mss_surrogate_info", C.c_int32, [_P, _P]),
+    ("mss_surrogate_get_params", C.c_int32, [_P, _P]),
+    ("mss_surrogate_set_params", C.c_int32, [_P, _P]),
+    ("mss_surrogate_forward", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P]),
+    ("mss_surrogate_backward", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P, _P]),
+    ("mss_surrogate_train_step", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P, C.c_float, _P, _P]),
+    ("mss_surrogate_destroy", None, [_P]),
 ]
 
 EXPORTED = [s[0] for s in _SIGS]
@@ -403,6 +411,45 @@ class Sim(_Handle):
     def load_state(self, now, old, steps: int):
         a, b = _arr(now, np.float64), _arr(old, np.float64)
         _check(lib().mss_sim_load_state(self._h, _ptr(a), _ptr(b), int(steps)))
+
+
+class Surrogate(_Handle):
+    """Learned surrogate network (mss_surrogate): hand-written CUDA forward, backward, Adam."""
+
+    _destroy = "mss_surrogate_destroy"
+
+    def __init__(self, cell: int, n_feat: int, n_out: int, channels: int = 32, hidden: int = 256, seed: int = 0):
+        super().__init__()
+        _check(lib().mss_surrogate_create(int(cell), int(n_feat), int(n_out), int(channels), int(hidden),
+                                          C.c_uint64(seed), C.byref(self._h)))
+        info = np.zeros(4, np.int64)
+        _check(lib().mss_surrogate_info(self._h, _ptr(info)))
+        self.n_params, self.n_in, self.n_feat, self.n_out = (int(v) for v in info)
+        self.cell, self.channels, self.hidden = cell, channels, hidden
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        _check(lib().mss_surrogate_get_params(self._h, _ptr(out)))
+        return out
+
+    def set_params(self, p):
+        a = _arr(p, np.float32)
+        _check(lib().mss_surrogate_set_params(self._h, _ptr(a)))
+
+    def forward(self, x, feat, y, stream=None):
+        _check(lib().mss_surrogate_forward(self._h, int(x.shape[0]), _devptr(x), None if feat is None else _devptr(feat),
+                                           _devptr(y), _stream(stream)))
+
+    def backward(self, x, feat, dy, grad, stream=None):
+        _check(lib().mss_surrogate_backward(self._h, int(x.shape[0]), _devptr(x),
+                                            None if feat is None else _devptr(feat), _devptr(dy), _devptr(grad),
+                                            _stream(stream)))
+
+    def train_step(self, x, feat, target, lr: float, loss=None, mask=None, stream=None):
+        _check(lib().mss_surrogate_train_step(self._h, int(x.shape[0]), _devptr(x),
+                                              None if feat is None else _devptr(feat), _devptr(target),
+                                              None if mask is None else _devptr(mask), C.c_float(lr),
+                                              None if loss is None else _devptr(loss), _stream(stream)))
 
 
 def step_noalloc(buffers: StepBuffers, n_steps: int, waveform, traces, stream=None):
