@@ -278,7 +278,7 @@ void mss_fine_destroy(mss_fine *f);
 /* ------------------------------------------------------------------------- */
 /* Learned surrogate of the off-line stage (no counterpart in the paper: it    */
 /* replaces the Krylov/Lanczos construction for repeated media; the exact      */
-/* construction stays the fallback and the judge).                            */
+/* construction stays the fallback and decides which cells need it).          */
 /* ------------------------------------------------------------------------- */
 typedef struct mss_surrogate mss_surrogate;
 
@@ -305,6 +305,62 @@ mss_status mss_surrogate_backward(mss_surrogate *s, int32_t batch, const float *
 mss_status mss_surrogate_train_step(mss_surrogate *s, int32_t batch, const float *x, const float *feat,
                                     const float *target, const float *mask, float lr, float *loss, void *stream);
 void mss_surrogate_destroy(mss_surrogate *s);
+
+/* Output transform: predict() returns mean + scale * network, and train_step fits the network
+ * to (target - mean) / scale.  set: host arrays [n_out] (both NULL: identity); fit: per-output
+ * masked mean and standard deviation (floored at 1e-3 max(1, |mean|)) of targets [n][n_out]. */
+mss_status mss_surrogate_set_output_transform(mss_surrogate *s, const float *mean, const float *scale);
+mss_status mss_surrogate_fit_output_transform(mss_surrogate *s, int32_t n, const double *targets, const float *mask);
+/* Device buffers; y [batch][n_out] = mean + scale * forward. */
+mss_status mss_surrogate_predict(mss_surrogate *s, int32_t batch, const float *x, const float *feat, float *y,
+                                 void *stream);
+
+/* Surrogate data layout.  A cell's boundary rows go to fixed slots of a padded dimension
+ * Kp = 6 slot_modes + io_slots: the face on the low / high side of array axis a fills slot
+ * 2a / 2a+1 (its M_f <= slot_modes modes in face order), an I/O face fills the last io_slots
+ * rows; absent faces leave their rows empty.  A cell's target vector holds, for Gamma^1..Gamma^m
+ * then Gamma-hat^2..Gamma-hat^m (Eq. GammaTrans), the row-major lower triangle (Kp (Kp+1)/2
+ * values) of the lower Cholesky factor L (M = L L^T) with log L_ii on the diagonal, so that any
+ * prediction unpacks to SPD coefficients; (2m-1) Kp (Kp+1)/2 values per cell.  Slots ascend with
+ * the cell's face order, so a cell's rows keep their order and the restriction of a padded
+ * factor to them stays lower triangular.  Gamma-hat^1 is not predicted: it is the exact
+ * projected inverse mass S^T B^-1 S of the boundary (first Markov parameter, Eq. GammaTrans with
+ * G_1 = beta_1^T), which also fixes the face masses (Eq. NtDtri).  Cubic 3D cells only. */
+
+/* Inputs of cells[n] (host): x [n][2][c][c][c] = (log sigma, log rho) of the cell's voxels in
+ * array order; feat [n][7] = 1 for each of the 6 face slots present, then (I/O rows)/io_slots.
+ * Errors: INVALID_ARG (cells not cubic 3D, a face larger than its slot). */
+mss_status mss_surrogate_cell_inputs(const mss_partition *p, int32_t n, const int32_t *cells, int32_t slot_modes,
+                                     int32_t io_slots, float *x, float *feat);
+/* Targets of cells[n] (all of one m) from a ROM's coefficients: targets [n][(2m-1) Kp(Kp+1)/2]
+ * (host doubles), mask (host floats, may be NULL) 1 where the entry belongs to the cell.
+ * Errors: COEF_NOT_SPD (a block has no Cholesky factor). */
+mss_status mss_surrogate_pack(const mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells,
+                              int32_t slot_modes, int32_t io_slots, double *targets, float *mask);
+/* Inverse of mss_surrogate_pack: write Gamma^k = L L^T, Gamma-hat^(k>=2) of cells[n] into r
+ * (Gamma-hat^1 and the face masses stay). */
+mss_status mss_surrogate_unpack(mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells,
+                                int32_t slot_modes, int32_t io_slots, const double *packed);
+/* Off-line stage without the Krylov/Lanczos part: topology, face bases, exact Gamma-hat^1 of
+ * every cell, face masses and Appendix D corner data as mss_build_roms makes them; Gamma^k and
+ * Gamma-hat^(k>=2) are zero until mss_surrogate_unpack or mss_rom_rebuild_cells fills them. */
+mss_status mss_rom_skeleton(const mss_partition *p, const mss_rom_params *prm, const int32_t *cell_m, mss_rom **out);
+/* Exact off-line construction (as mss_build_roms, same parameters) of cells[n] of a ROM built or
+ * skeletoned from p, replacing their coefficients.  Errors: STATE (other partition), NOT_CONVERGED. */
+mss_status mss_rom_rebuild_cells(mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells, void *stream);
+/* Screen of cells[n]: err[n] (host) = ||U^1(s) - F(s)||_F / ||F(s)||_F at the ROM's shift s,
+ * U^1 the S-fraction transfer function of the ROM's current coefficients (Eqs. GammaU1st,
+ * GammaUrem, tfgamma) and F(s) = C^T (A + sB)^{-1} C of the cell's exact operator (shifted CG
+ * on the GPU, FP64).  A singular recursion gives err = 1e300.  Errors: STATE, NOT_CONVERGED. */
+mss_status mss_surrogate_screen(const mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells, double *err,
+                                void *stream);
+/* Surrogate off-line stage for cells[n] (one m) of a ROM from mss_rom_skeleton or mss_build_roms:
+ * inputs -> predict (GPU) -> unpack into r -> screen (err[n], host) -> exact rebuild of every cell
+ * with err > tol (fallback[n] = 1 for those, host).  The surrogate must have 7 features and
+ * (2m-1) Kp(Kp+1)/2 outputs.  Errors: INVALID_ARG, STATE, NOT_CONVERGED, CUDA. */
+mss_status mss_surrogate_infer(mss_surrogate *sur, mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells,
+                               int32_t slot_modes, int32_t io_slots, double tol, double *err, int32_t *fallback,
+                               void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* Stepping without allocation.  The paper has no counterpart: this entry     */

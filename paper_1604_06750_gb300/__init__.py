@@ -112,6 +112,16 @@ _SIGS = [
     ("mss_surrogate_backward", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P, _P]),
     ("mss_surrogate_train_step", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P, C.c_float, _P, _P]),
     ("mss_surrogate_destroy", None, [_P]),
+    ("mss_surrogate_cell_inputs", C.c_int32, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P]),
+    ("mss_surrogate_pack", C.c_int32, [_P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P]),
+    ("mss_surrogate_unpack", C.c_int32, [_P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
+    ("mss_rom_skeleton", C.c_int32, [_P, _P, _P, _P]),
+    ("mss_rom_rebuild_cells", C.c_int32, [_P, _P, C.c_int32, _P, _P]),
+    ("mss_surrogate_screen", C.c_int32, [_P, _P, C.c_int32, _P, _P, _P]),
+    ("mss_surrogate_set_output_transform", C.c_int32, [_P, _P, _P]),
+    ("mss_surrogate_fit_output_transform", C.c_int32, [_P, C.c_int32, _P, _P]),
+    ("mss_surrogate_predict", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P]),
+    ("mss_surrogate_infer", C.c_int32, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
 ]
 
 EXPORTED = [s[0] for s in _SIGS]
@@ -221,6 +231,7 @@ class Partition(_Handle):
         super().__init__()
         self.op = op
         c = _arr(list(cell) + [1] * (3 - len(cell)), np.int32)
+        self.cell_size = c.copy()
         io = _arr(np.asarray(io_nodes).reshape(-1, len(cell)) if len(io_nodes) else np.zeros((0, len(cell))),
                   np.int32)
         _check(lib().mss_partition_create(op._h, _ptr(op._sigma), _ptr(op._rho), _ptr(c), int(io.shape[0]),
@@ -262,6 +273,17 @@ class Partition(_Handle):
         return dict(faces=faces, nodes=nodes, K=K, rowptr=rp, col=col, val=val, B=b)
 
 
+    def cell_inputs(self, cells, slot_modes: int, io_slots: int):
+        """Surrogate inputs of the listed cells: (x [n][2][c][c][c] log sigma/log rho, feat [n][7])."""
+        c = _arr(cells, np.int32)
+        e = int(self.cell_size[0])
+        x = np.zeros((len(c), 2, e, e, e), np.float32)
+        f = np.zeros((len(c), 7), np.float32)
+        _check(lib().mss_surrogate_cell_inputs(self._h, len(c), _ptr(c), int(slot_modes), int(io_slots), _ptr(x),
+                                               _ptr(f)))
+        return x, f
+
+
 class Rom(_Handle):
     """Cell ROMs / S-fraction coefficients, projected I/O, corner data (mss_rom)."""
 
@@ -278,6 +300,49 @@ class Rom(_Handle):
                                     C.byref(self._h)))
         self.part = part
         return self
+
+    @classmethod
+    def skeleton(cls, part: Partition, m: int, n_modes: int, shift: float, cg_tol: float = 1e-12,
+                 cg_maxit: int = 5000, cell_m=None) -> "Rom":
+        """Off-line stage without Krylov/Lanczos: exact Gamma-hat^1, face masses, corner data."""
+        self = cls()
+        p = _RomParams(m=int(m), n_modes=int(n_modes), shift=float(shift), cg_tol=float(cg_tol),
+                       cg_maxit=int(cg_maxit), reserved=0)
+        cm = None if cell_m is None else _arr(cell_m, np.int32)
+        _check(lib().mss_rom_skeleton(part._h, C.byref(p), None if cm is None else _ptr(cm), C.byref(self._h)))
+        self.part = part
+        return self
+
+    def rebuild_cells(self, cells, stream=None) -> None:
+        """Exact off-line construction of the listed cells (same parameters as the ROM's)."""
+        c = _arr(cells, np.int32)
+        _check(lib().mss_rom_rebuild_cells(self._h, self.part._h, len(c), _ptr(c) if len(c) else None,
+                                           _stream(stream)))
+
+    def screen(self, cells, stream=None) -> np.ndarray:
+        """Relative transfer-function error of the listed cells at the ROM's shift."""
+        c = _arr(cells, np.int32)
+        err = np.zeros(len(c))
+        _check(lib().mss_surrogate_screen(self._h, self.part._h, len(c), _ptr(c), _ptr(err), _stream(stream)))
+        return err
+
+    def pack(self, cells, slot_modes: int, io_slots: int, m: int):
+        """(targets [n][(2m-1) Kp(Kp+1)/2] FP64, mask FP32) in the surrogate's fixed slot layout."""
+        c = _arr(cells, np.int32)
+        Kp = 6 * slot_modes + io_slots
+        D = (2 * m - 1) * Kp * (Kp + 1) // 2
+        t = np.zeros((len(c), D))
+        mk = np.zeros((len(c), D), np.float32)
+        _check(lib().mss_surrogate_pack(self._h, self.part._h, len(c), _ptr(c), int(slot_modes), int(io_slots),
+                                        _ptr(t), _ptr(mk)))
+        return t, mk
+
+    def unpack(self, cells, slot_modes: int, io_slots: int, packed) -> None:
+        """Write packed Gamma^k, Gamma-hat^(k>=2) of the listed cells into this ROM."""
+        c = _arr(cells, np.int32)
+        v = _arr(packed, np.float64)
+        _check(lib().mss_surrogate_unpack(self._h, self.part._h, len(c), _ptr(c), int(slot_modes), int(io_slots),
+                                          _ptr(v)))
 
     @classmethod
     def import_(cls, topology, coeffs) -> "Rom":
@@ -450,6 +515,35 @@ class Surrogate(_Handle):
                                               None if feat is None else _devptr(feat), _devptr(target),
                                               None if mask is None else _devptr(mask), C.c_float(lr),
                                               None if loss is None else _devptr(loss), _stream(stream)))
+
+    def set_output_transform(self, mean=None, scale=None):
+        if mean is None:
+            _check(lib().mss_surrogate_set_output_transform(self._h, None, None))
+            return
+        m, s = _arr(mean, np.float32), _arr(scale, np.float32)
+        _check(lib().mss_surrogate_set_output_transform(self._h, _ptr(m), _ptr(s)))
+
+    def fit_output_transform(self, targets, mask=None):
+        t = _arr(targets, np.float64)
+        mk = None if mask is None else _arr(mask, np.float32)
+        _check(lib().mss_surrogate_fit_output_transform(self._h, int(t.shape[0]), _ptr(t),
+                                                        None if mk is None else _ptr(mk)))
+
+    def predict(self, x, feat, y, stream=None):
+        _check(lib().mss_surrogate_predict(self._h, int(x.shape[0]), _devptr(x), None if feat is None else _devptr(feat),
+                                           _devptr(y), _stream(stream)))
+
+    def infer(self, rom: "Rom", cells, slot_modes: int, io_slots: int, tol: float, stream=None):
+        """Predict the listed cells into rom, screen them, rebuild the rejected ones exactly.
+
+        Returns (err, fallback): per-cell transfer-function error before the fallback, and 1 where
+        the cell was rebuilt."""
+        c = _arr(cells, np.int32)
+        err = np.zeros(len(c))
+        fb = np.zeros(len(c), np.int32)
+        _check(lib().mss_surrogate_infer(self._h, rom._h, rom.part._h, len(c), _ptr(c), int(slot_modes), int(io_slots),
+                                         C.c_double(tol), _ptr(err), _ptr(fb), _stream(stream)))
+        return err, fb
 
 
 def step_noalloc(buffers: StepBuffers, n_steps: int, waveform, traces, stream=None):

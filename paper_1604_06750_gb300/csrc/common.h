@@ -133,6 +133,7 @@ struct Rom {
   std::vector<int64_t> basis_off;
   std::vector<double> bases;
   const Partition *source = nullptr;
+  mss_rom_params prm{};            // parameters of the off-line construction (built ROMs)
 
   void finalize_topology();   // validates and fills cell_K, coef_off, fmass_off
 };

@@ -488,6 +488,56 @@ __global__ void k_pack_sm(double *Sm, const int64_t *sm_off, const double *V, co
   }
 }
 
+// Transfer function of the three-point scheme (Eqs. GammaU1st, GammaUrem, tfgamma) at a real
+// Laplace point z, per cell: Z_m = D_m, Z_k = D_k - Gamma^k Z_{k+1}^{-1} Gamma^k, U^1 = Z_1^{-1},
+// D_k = -Gamma^k - Gamma^{k-1} + z (Gamma-hat^k)^{-1}; then the relative Frobenius distance
+// of U^1 to F (the exact cell transfer function at z).  Workspace: 6 K x K per cell.
+__global__ void k_sfrac_err(const double *gam, const double *gh, const int64_t *coef_off, const int32_t *Kt,
+                            const int32_t *mc, double z, const double *F, const int64_t *f_off, double *work,
+                            const int64_t *w_off, double *err) {
+  const int c = blockIdx.x;
+  const int K = Kt[c], m = mc[c];
+  const double *G = gam + coef_off[c], *H = gh + coef_off[c];
+  double *w = work + w_off[c];
+  double *Z = w, *T1 = w + (size_t)K * K, *T2 = T1 + (size_t)K * K, *Hi = T2 + (size_t)K * K,
+         *T3 = Hi + (size_t)K * K;
+  __shared__ double num, den;
+  for (int k = m - 1; k >= 0; --k) {
+    // D_k (0-based layer k): -Gamma^k - Gamma^{k-1} + z (Gamma-hat^k)^{-1}
+    bcopy(T1, K, H + (size_t)k * K * K, K, K, K, 1.0);
+    if (!binverse(T1, K, Hi, K, K)) { if (threadIdx.x == 0) err[c] = 1e300; return; }
+    for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+      double v = -G[(size_t)k * K * K + idx] + z * Hi[idx];
+      if (k > 0) v -= G[(size_t)(k - 1) * K * K + idx];
+      T2[idx] = v;
+    }
+    __syncthreads();
+    if (k < m - 1) {
+      // T2 -= Gamma^k Z^{-1} Gamma^k   (Z holds Z_{k+1})
+      bcopy(T1, K, Z, K, K, K, 1.0);
+      if (!binverse(T1, K, Hi, K, K)) { if (threadIdx.x == 0) err[c] = 1e300; return; }
+      bgemm(T3, K, Hi, K, false, G + (size_t)k * K * K, K, false, K, K, K, 1.0, 0.0);
+      bgemm(T2, K, G + (size_t)k * K * K, K, false, T3, K, false, K, K, K, -1.0, 1.0);
+    }
+    bcopy(Z, K, T2, K, K, K, 1.0);
+  }
+  bcopy(T1, K, Z, K, K, K, 1.0);
+  if (!binverse(T1, K, Hi, K, K)) { if (threadIdx.x == 0) err[c] = 1e300; return; }
+  if (threadIdx.x == 0) { num = 0; den = 0; }
+  __syncthreads();
+  double a = 0, b = 0;
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+    const double f = F[f_off[c] + idx];
+    const double d = Hi[idx] - f;
+    a += d * d;
+    b += f * f;
+  }
+  atomicAdd(&num, a);
+  atomicAdd(&den, b);
+  __syncthreads();
+  if (threadIdx.x == 0) err[c] = sqrt(num / fmax(den, 1e-300));
+}
+
 inline unsigned nblk(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 }  // namespace
@@ -690,12 +740,12 @@ static void invert_spd_host(const double *A, int n, double *out) {
   }
 }
 
-static void build_roms(const Partition &Pc, const mss_rom_params &prm, const int32_t *cell_m, cudaStream_t st, Rom &R) {
-  Partition &P = const_cast<Partition &>(Pc);
+// Topology, face bases and C = P^Gamma S blocks of every cell (host); coefficients left zero.
+static void rom_topology(Partition &P, const mss_rom_params &prm, const int32_t *cell_m, Rom &R,
+                         std::vector<int> &Kt, std::vector<int> &mv, std::vector<std::vector<double>> &Cb) {
   MSS_REQUIRE(prm.n_modes >= 1 && prm.shift < 0 && prm.cg_tol > 0 && prm.cg_maxit > 0, MSS_ERR_INVALID_ARG,
               "bad ROM parameters (n_modes >= 1, shift < 0, cg_tol > 0, cg_maxit > 0)");
   const int nc = P.n_cells, nf = (int)P.faces.size();
-  // face bases and topology
   R.n_cells = nc;
   R.n_faces = nf;
   R.face_M.assign(nf, 0);
@@ -726,10 +776,9 @@ static void build_roms(const Partition &Pc, const mss_rom_params &prm, const int
   R.finalize_topology();
   R.gamma.assign(R.coef_off[nc], 0.0);
   R.gamma_hat.assign(R.coef_off[nc], 0.0);
-  // per cell: split matrices and the boundary block of C = P^Gamma S_c (K_c rows x Kt_c)
-  std::vector<int> Kt(nc), mv(nc);
-  std::vector<std::vector<double>> Cb(nc);
-  int64_t maxbytes = 0;
+  Kt.assign(nc, 0);
+  mv.assign(nc, 0);
+  Cb.assign(nc, std::vector<double>());
   for (int c = 0; c < nc; ++c) {
     P.build_cell(c);
     const Cell &cl = P.cells[c];
@@ -749,17 +798,25 @@ static void build_roms(const Partition &Pc, const mss_rom_params &prm, const int
       rr += Kf;
       oc += M;
     }
-    maxbytes = std::max<int64_t>(maxbytes, (int64_t)cl.nodes.size());
   }
-  // chunks bounded by device memory (~ (mmax + 6) dense N x W arrays)
+}
+
+// Exact off-line construction of the listed cells on the device (chunks bounded by memory).
+static void rom_exact_cells(const Partition &P, const std::vector<int> &cells, const std::vector<int> &Kt,
+                            const std::vector<int> &mv, const std::vector<std::vector<double>> &Cb,
+                            const mss_rom_params &prm, Rom &R, cudaStream_t st) {
+  if (cells.empty()) return;
   size_t free_b = 0, total_b = 0;
   MSS_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const int Wmax = *std::max_element(Kt.begin(), Kt.end());
-  const int mmax = *std::max_element(mv.begin(), mv.end());
+  int Wmax = 0, mmax = 0;
+  for (int c : cells) {
+    Wmax = std::max(Wmax, Kt[c]);
+    mmax = std::max(mmax, mv[c]);
+  }
   const double budget = std::min<double>(0.5 * (double)free_b, 48e9);
   std::vector<int> chunk;
   double used = 0;
-  for (int c = 0; c < nc; ++c) {
+  for (int c : cells) {
     const double need = (double)P.cells[c].nodes.size() * Wmax * 8.0 * (mmax + 7) +
                         8.0 * ((double)mv[c] * Kt[c]) * ((double)mv[c] * Kt[c]) * 3;
     if (!chunk.empty() && used + need > budget) {
@@ -771,7 +828,37 @@ static void build_roms(const Partition &Pc, const mss_rom_params &prm, const int
     used += need;
   }
   if (!chunk.empty()) build_chunk(P, chunk, Kt, mv, Cb, prm.shift, prm.cg_tol, prm.cg_maxit, R, st);
-  // face masses M_f = sum_i (Gamma-hat^1_{i,f})^{-1}
+}
+
+// Exact Markov parameter Gamma-hat^1 = S^T P^T B^{-1} P S (block-diagonal over the faces;
+// Remark Sinsubspace) of the listed cells, written as layer 1 of gamma_hat.
+static void rom_exact_markov(const Partition &P, const std::vector<int> &cells, Rom &R) {
+  for (int c : cells) {
+    const Cell &cl = P.cells[c];
+    const int K = R.cell_K[c];
+    double *H = R.gamma_hat.data() + R.coef_off[c];
+    std::fill(H, H + (size_t)K * K, 0.0);
+    int64_t rr = 0;
+    int oc = 0;
+    for (int f : cl.faces) {
+      const int Kf = R.face_K[f], M = R.face_M[f];
+      const double *S = R.bases.data() + R.basis_off[f];
+      for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+          double acc = 0;
+          for (int r = 0; r < Kf; ++r) acc += S[(size_t)r * M + i] * S[(size_t)r * M + j] / cl.B[rr + r];
+          H[(size_t)(oc + i) * K + oc + j] = acc;
+        }
+      rr += Kf;
+      oc += M;
+    }
+  }
+}
+
+// Face masses from Gamma-hat^1 and the Appendix D groups.
+static void rom_faces(const Partition &Pc, Rom &R) {
+  Partition &P = const_cast<Partition &>(Pc);
+  const int nf = R.n_faces;
   R.face_mass.assign(R.fmass_off[nf], 0.0);
   for (int f = 0; f < nf; ++f) {
     const int M = R.face_M[f];
@@ -826,6 +913,407 @@ static void build_roms(const Partition &Pc, const mss_rom_params &prm, const int
   R.source = &Pc;
 }
 
+static void build_roms(const Partition &Pc, const mss_rom_params &prm, const int32_t *cell_m, cudaStream_t st, Rom &R) {
+  Partition &P = const_cast<Partition &>(Pc);
+  std::vector<int> Kt, mv;
+  std::vector<std::vector<double>> Cb;
+  rom_topology(P, prm, cell_m, R, Kt, mv, Cb);
+  std::vector<int> all(P.n_cells);
+  std::iota(all.begin(), all.end(), 0);
+  rom_exact_cells(P, all, Kt, mv, Cb, prm, R, st);
+  rom_faces(Pc, R);
+  R.prm = prm;
+}
+
+
+// Exact cell transfer functions F(s) = C^T (A + sB)^{-1} C of the listed cells (batched CG on
+// -(A + sB)), compared with the S-fraction transfer functions of the ROM's current coefficients.
+static void screen_cells(const Partition &P, const std::vector<int> &cells, const std::vector<int> &Kt,
+                         const std::vector<std::vector<double>> &Cb, const Rom &R, double shift, double cg_tol,
+                         int cg_maxit, double *err_out, cudaStream_t st) {
+  const int nc = (int)cells.size();
+  if (nc == 0) return;
+  int W = 0;
+  for (int c : cells) W = std::max(W, Kt[c]);
+  std::vector<int64_t> row0(nc + 1, 0), ptr(1, 0), col, cb_off(nc, 0);
+  std::vector<double> val, Bv, Cbv, dinv;
+  std::vector<int32_t> Kb(nc), K(nc), mc(nc);
+  for (int i = 0; i < nc; ++i) {
+    const Cell &cl = P.cells[cells[i]];
+    row0[i + 1] = row0[i] + (int64_t)cl.nodes.size();
+    for (int64_t r = 0; r < cl.A.n; ++r) {
+      double diag = 0;
+      for (int64_t k = cl.A.ptr[r]; k < cl.A.ptr[r + 1]; ++k) {
+        col.push_back(row0[i] + cl.A.col[k]);
+        val.push_back(cl.A.val[k]);
+        if (cl.A.col[k] == r) diag = cl.A.val[k];
+      }
+      ptr.push_back((int64_t)col.size());
+      dinv.push_back(1.0 / (-diag - shift * cl.B[r]));
+    }
+    Bv.insert(Bv.end(), cl.B.begin(), cl.B.end());
+    cb_off[i] = (int64_t)Cbv.size();
+    Cbv.insert(Cbv.end(), Cb[cells[i]].begin(), Cb[cells[i]].end());
+    Kb[i] = (int32_t)cl.K;
+    K[i] = Kt[cells[i]];
+    mc[i] = R.cell_m[cells[i]];
+  }
+  const int64_t rows = row0[nc], NW = rows * W;
+  DevMem d_row0, d_ptr, d_col, d_val, d_B, d_dinv, d_Cb, d_cboff, d_Kb, d_Kt, d_mc;
+  upload(d_row0, row0);
+  upload(d_ptr, ptr);
+  upload(d_col, col);
+  upload(d_val, val);
+  upload(d_B, Bv);
+  upload(d_dinv, dinv);
+  upload(d_Cb, Cbv);
+  upload(d_cboff, cb_off);
+  upload(d_Kb, Kb);
+  upload(d_Kt, K);
+  upload(d_mc, mc);
+  DevMem X, Y, cr, cz, cp, cq, G, sb1, sb2, sb3, sb4, sb5, mx;
+  for (DevMem *b : {&X, &Y, &cr, &cz, &cp, &cq}) b->alloc(NW * 8);
+  G.alloc((size_t)nc * W * W * 8);
+  for (DevMem *b : {&sb1, &sb2, &sb3, &sb4, &sb5}) b->alloc((size_t)nc * W * 8);
+  mx.alloc(8);
+  double *s1 = sb1.as<double>(), *s2 = sb2.as<double>(), *s3 = sb3.as<double>(), *s4 = sb4.as<double>(),
+         *s5 = sb5.as<double>();
+  const int64_t *r0 = d_row0.as<int64_t>();
+  const int32_t *kt = d_Kt.as<int32_t>();
+  // X = C; solve -(A + sB) Y = C
+  k_expand_c<<<nblk(NW), kThreads, 0, st>>>(X.as<double>(), d_Cb.as<double>(), d_cboff.as<int64_t>(), r0,
+                                           d_Kb.as<int32_t>(), kt, d_B.as<double>(), nc, rows, W, 0);
+  k_coldot<<<nc, 128, 0, st>>>(s5, nullptr, X.as<double>(), X.as<double>(), nullptr, r0, kt, W);
+  k_cg_init<<<nblk(NW), kThreads, 0, st>>>(Y.as<double>(), cr.as<double>(), cz.as<double>(), cp.as<double>(), X.as<double>(),
+                                          d_dinv.as<double>(), r0, kt, nc, rows, W);
+  k_coldot<<<nc, 128, 0, st>>>(s1, nullptr, cr.as<double>(), cz.as<double>(), nullptr, r0, kt, W);
+  bool conv = false;
+  for (int it = 0; it < cg_maxit; ++it) {
+    k_spmm<<<nblk(NW), kThreads, 0, st>>>(cq.as<double>(), cp.as<double>(), d_ptr.as<int64_t>(), d_col.as<int64_t>(),
+                                         d_val.as<double>(), d_B.as<double>(), shift, r0, kt, nc, rows, W, 1);
+    k_coldot<<<nc, 128, 0, st>>>(s2, nullptr, cp.as<double>(), cq.as<double>(), nullptr, r0, kt, W);
+    k_cg_xr<<<nblk(NW), kThreads, 0, st>>>(Y.as<double>(), cr.as<double>(), cz.as<double>(), cp.as<double>(), cq.as<double>(),
+                                          d_dinv.as<double>(), s1, s2, r0, nc, rows, W);
+    k_coldot<<<nc, 128, 0, st>>>(s3, s4, cr.as<double>(), cz.as<double>(), nullptr, r0, kt, W);
+    k_cg_p<<<nblk(NW), kThreads, 0, st>>>(cp.as<double>(), cz.as<double>(), s3, s1, r0, nc, rows, W);
+    std::swap(s1, s3);
+    if (it % 10 == 9 || it + 1 == cg_maxit) {
+      k_maxratio<<<1, kThreads, 0, st>>>(mx.as<double>(), s4, s5, kt, nc, W);
+      double h = 0;
+      MSS_CUDA(cudaMemcpyAsync(&h, mx.p, 8, cudaMemcpyDeviceToHost, st));
+      MSS_CUDA(cudaStreamSynchronize(st));
+      if (h <= cg_tol * cg_tol) { conv = true; break; }
+    }
+  }
+  MSS_REQUIRE(conv, MSS_ERR_NOT_CONVERGED, "shifted CG of the screen did not reach the tolerance");
+  // F = -C^T Y, packed K x K per cell
+  const dim3 ggram(nc, (W + 15) / 16, (W + 15) / 16);
+  k_gram<<<ggram, kThreads, 0, st>>>(G.as<double>(), X.as<double>(), Y.as<double>(), nullptr, r0, kt, W);
+  std::vector<double> Gh((size_t)nc * W * W);
+  MSS_CUDA(cudaMemcpyAsync(Gh.data(), G.p, Gh.size() * 8, cudaMemcpyDeviceToHost, st));
+  MSS_CUDA(cudaStreamSynchronize(st));
+  std::vector<int64_t> f_off(nc + 1, 0), c_off(nc + 1, 0), w_off(nc + 1, 0);
+  std::vector<double> Fv, gam, gh;
+  for (int i = 0; i < nc; ++i) {
+    const int k = K[i], c = cells[i];
+    f_off[i + 1] = f_off[i] + (int64_t)k * k;
+    for (int a = 0; a < k; ++a)
+      for (int bb = 0; bb < k; ++bb) Fv.push_back(-Gh[(size_t)i * W * W + (size_t)a * W + bb]);
+    const int64_t n = (int64_t)mc[i] * k * k;
+    c_off[i + 1] = c_off[i] + n;
+    gam.insert(gam.end(), R.gamma.begin() + R.coef_off[c], R.gamma.begin() + R.coef_off[c] + n);
+    gh.insert(gh.end(), R.gamma_hat.begin() + R.coef_off[c], R.gamma_hat.begin() + R.coef_off[c] + n);
+    w_off[i + 1] = w_off[i] + 6LL * k * k;
+  }
+  DevMem d_F, d_foff, d_gam, d_gh, d_coff, d_work, d_woff, d_err;
+  upload(d_F, Fv);
+  upload(d_foff, f_off);
+  upload(d_gam, gam);
+  upload(d_gh, gh);
+  upload(d_coff, c_off);
+  d_work.alloc(w_off[nc] * 8);
+  upload(d_woff, w_off);
+  d_err.alloc(nc * 8);
+  k_sfrac_err<<<nc, kThreads, 0, st>>>(d_gam.as<double>(), d_gh.as<double>(), d_coff.as<int64_t>(), kt, d_mc.as<int32_t>(),
+                                       shift, d_F.as<double>(), d_foff.as<int64_t>(), d_work.as<double>(),
+                                       d_woff.as<int64_t>(), d_err.as<double>());
+  MSS_CUDA(cudaGetLastError());
+  MSS_CUDA(cudaMemcpyAsync(err_out, d_err.p, nc * 8, cudaMemcpyDeviceToHost, st));
+  MSS_CUDA(cudaStreamSynchronize(st));
+}
+
+// Slot of each boundary row of cell c in the fixed surrogate layout: face on the low / high side
+// of axis a -> slot 2a / 2a+1 (slot_modes rows each), I/O face -> rows after the 6 slots.
+static void cell_slots(const Partition &P, const Rom &R, int c, int slot_modes, int io_slots, std::vector<int> &row_of,
+                       float *feat) {
+  row_of.clear();
+  const Cell &cl = P.cells[c];
+  if (feat)
+    for (int j = 0; j < 7; ++j) feat[j] = 0.f;
+  for (int f : cl.faces) {
+    const Face &F = P.faces[f];
+    const int M = R.face_M[f];
+    int base;
+    if (F.kind == 1) {
+      MSS_REQUIRE(M <= io_slots, MSS_ERR_INVALID_ARG, "I/O face larger than the surrogate's I/O slots");
+      base = 6 * slot_modes;
+      if (feat) feat[6] = (float)M / (float)io_slots;
+    } else {
+      MSS_REQUIRE(M <= slot_modes, MSS_ERR_INVALID_ARG, "face has more modes than the surrogate's slots");
+      const int slot = 2 * F.axis + (F.cells[0] == c ? 1 : 0);
+      base = slot * slot_modes;
+      if (feat) feat[slot] = 1.f;
+    }
+    for (int j = 0; j < M; ++j) row_of.push_back(base + j);
+  }
+}
+
+// In-place lower Cholesky factor of an SPD n x n row-major matrix (upper part zeroed); false if
+// a pivot is not positive.
+static bool cholesky_lower(double *A, int n) {
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+    if (!(d > 0)) return false;
+    d = std::sqrt(d);
+    A[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double v = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) v -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+      A[(size_t)i * n + j] = v / d;
+    }
+    for (int k = j + 1; k < n; ++k) A[(size_t)j * n + k] = 0.0;
+  }
+  return true;
+}
+
+// Row-major lower-triangle position of (a, b), a >= b.
+static inline int64_t tri_index(int a, int b) { return (int64_t)a * (a + 1) / 2 + b; }
+
+// Packed factors -> Gamma^k (k = 1..m) and Gamma-hat^k (k = 2..m) = L L^T of the listed cells.
+static void unpack_cells(Rom &R, const Partition &P, const std::vector<int> &cells, int slot_modes, int io_slots,
+                         const double *packed) {
+  const int Kp = 6 * slot_modes + io_slots;
+  const int64_t tri = (int64_t)Kp * (Kp + 1) / 2;
+  std::vector<int> row_of;
+  std::vector<double> L;
+  for (size_t i = 0; i < cells.size(); ++i) {
+    const int c = cells[i];
+    MSS_REQUIRE(c >= 0 && c < R.n_cells, MSS_ERR_INVALID_ARG, "cell out of range");
+    const int m = R.cell_m[c], K = R.cell_K[c];
+    const int64_t D = (int64_t)(2 * m - 1) * tri;
+    cell_slots(P, R, c, slot_modes, io_slots, row_of, nullptr);
+    const double *t = packed + (int64_t)i * D;
+    L.assign((size_t)K * K, 0.0);
+    for (int q = 0; q < 2 * m - 1; ++q) {
+      for (int a = 0; a < K; ++a)
+        for (int b2 = 0; b2 <= a; ++b2) {
+          const double v = t[(int64_t)q * tri + tri_index(row_of[a], row_of[b2])];
+          L[(size_t)a * K + b2] = a == b2 ? std::exp(v) : v;
+        }
+      double *Mq = q < m ? R.gamma.data() + R.coef_off[c] + (size_t)q * K * K
+                         : R.gamma_hat.data() + R.coef_off[c] + (size_t)(q - m + 1) * K * K;
+      for (int a = 0; a < K; ++a)
+        for (int b2 = 0; b2 <= a; ++b2) {
+          double acc = 0;
+          for (int k = 0; k <= b2; ++k) acc += L[(size_t)a * K + k] * L[(size_t)b2 * K + k];
+          Mq[(size_t)a * K + b2] = acc;
+          Mq[(size_t)b2 * K + a] = acc;
+        }
+    }
+  }
+}
+
+}  // namespace mss
+
+using namespace mss;
+
+extern "C" {
+
+mss_status mss_rom_skeleton(const mss_partition *p, const mss_rom_params *prm, const int32_t *cell_m, mss_rom **out) {
+  return guard([&] {
+    MSS_REQUIRE(p && prm && out, MSS_ERR_INVALID_ARG, "null argument");
+    auto h = std::make_unique<mss_rom>();
+    Partition &P = const_cast<Partition &>(p->p);
+    std::vector<int> Kt, mv;
+    std::vector<std::vector<double>> Cb;
+    rom_topology(P, *prm, cell_m, h->r, Kt, mv, Cb);
+    std::vector<int> all(P.n_cells);
+    std::iota(all.begin(), all.end(), 0);
+    rom_exact_markov(P, all, h->r);
+    rom_faces(p->p, h->r);
+    h->r.prm = *prm;
+    *out = h.release();
+  });
+}
+
+mss_status mss_rom_rebuild_cells(mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells, void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(r && p && n >= 0 && (n == 0 || cells), MSS_ERR_INVALID_ARG, "bad argument");
+    Rom &R = r->r;
+    MSS_REQUIRE(R.source == &p->p, MSS_ERR_STATE, "ROM was not built from this partition");
+    Partition &P = const_cast<Partition &>(p->p);
+    std::vector<int> list(cells, cells + n);
+    for (int c : list) MSS_REQUIRE(c >= 0 && c < R.n_cells, MSS_ERR_INVALID_ARG, "cell out of range");
+    Rom tmp = R;   // topology recomputation below must not disturb the ROM's face bases
+    std::vector<int> Kt, mv;
+    std::vector<std::vector<double>> Cb;
+    rom_topology(P, R.prm, R.cell_m.data(), tmp, Kt, mv, Cb);
+    tmp.gamma = R.gamma;
+    tmp.gamma_hat = R.gamma_hat;
+    rom_exact_cells(P, list, Kt, mv, Cb, R.prm, tmp, (cudaStream_t)stream);
+    rom_exact_markov(P, list, tmp);   // keep Gamma-hat^1 (and so the face masses) exact
+    R.gamma.swap(tmp.gamma);
+    R.gamma_hat.swap(tmp.gamma_hat);
+  });
+}
+
+mss_status mss_surrogate_cell_inputs(const mss_partition *p, int32_t n, const int32_t *cells, int32_t slot_modes,
+                                     int32_t io_slots, float *x, float *feat) {
+  return guard([&] {
+    MSS_REQUIRE(p && n >= 1 && cells && x && feat && slot_modes >= 1 && io_slots >= 0, MSS_ERR_INVALID_ARG,
+                "bad argument");
+    const Partition &P = p->p;
+    const mss_grid &g = P.op->g;
+    MSS_REQUIRE(P.d == 3 && P.cs[0] == P.cs[1] && P.cs[1] == P.cs[2], MSS_ERR_INVALID_ARG, "cubic 3D cells required");
+    const int c3 = P.cs[0];
+    Rom dummy;
+    dummy.face_M.assign(P.faces.size(), 0);
+    for (size_t f = 0; f < P.faces.size(); ++f)
+      dummy.face_M[f] = P.faces[f].kind == 1 ? (int)P.faces[f].nodes.size()
+                                               : std::min<int>(slot_modes, (int)P.faces[f].nodes.size());
+    std::vector<int> row_of;
+    for (int i = 0; i < n; ++i) {
+      const int c = cells[i];
+      MSS_REQUIRE(c >= 0 && c < P.n_cells, MSS_ERR_INVALID_ARG, "cell out of range");
+      const int *C = P.cells[c].coords;
+      float *xs = x + (int64_t)i * 2 * c3 * c3 * c3, *xr = xs + (int64_t)c3 * c3 * c3;
+      for (int a = 0; a < c3; ++a)
+        for (int b2 = 0; b2 < c3; ++b2)
+          for (int d2 = 0; d2 < c3; ++d2) {
+            const int64_t v = (((int64_t)(C[0] * c3 + a) * g.n[1]) + C[1] * c3 + b2) * g.n[2] + C[2] * c3 + d2;
+            const int64_t o = ((int64_t)a * c3 + b2) * c3 + d2;
+            xs[o] = (float)std::log(P.sigma[v]);
+            xr[o] = (float)std::log(P.rho[v]);
+          }
+      cell_slots(P, dummy, c, slot_modes, io_slots, row_of, feat + (int64_t)i * 7);
+    }
+  });
+}
+
+mss_status mss_surrogate_pack(const mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells, int32_t slot_modes,
+                              int32_t io_slots, double *targets, float *mask) {
+  return guard([&] {
+    MSS_REQUIRE(r && p && n >= 1 && cells && targets && slot_modes >= 1, MSS_ERR_INVALID_ARG, "bad argument");
+    const Rom &R = r->r;
+    const int Kp = 6 * slot_modes + io_slots;
+    const int64_t tri = (int64_t)Kp * (Kp + 1) / 2;
+    const int m = R.cell_m[cells[0]];
+    const int64_t D = (int64_t)(2 * m - 1) * tri;
+    std::vector<int> row_of;
+    std::vector<double> L;
+    for (int i = 0; i < n; ++i) {
+      const int c = cells[i];
+      MSS_REQUIRE(c >= 0 && c < R.n_cells && R.cell_m[c] == m, MSS_ERR_INVALID_ARG, "cells must share m");
+      cell_slots(p->p, R, c, slot_modes, io_slots, row_of, nullptr);
+      const int K = R.cell_K[c];
+      double *t = targets + (int64_t)i * D;
+      std::fill(t, t + D, 0.0);
+      if (mask) std::fill(mask + (int64_t)i * D, mask + (int64_t)(i + 1) * D, 0.f);
+      for (int q = 0; q < 2 * m - 1; ++q) {
+        const double *Mq = q < m ? R.gamma.data() + R.coef_off[c] + (size_t)q * K * K
+                                 : R.gamma_hat.data() + R.coef_off[c] + (size_t)(q - m + 1) * K * K;
+        L.assign(Mq, Mq + (size_t)K * K);
+        MSS_REQUIRE(cholesky_lower(L.data(), K), MSS_ERR_COEF_NOT_SPD, "a coefficient block is not SPD");
+        for (int a = 0; a < K; ++a)
+          for (int b2 = 0; b2 <= a; ++b2) {
+            const int64_t o = (int64_t)q * tri + tri_index(row_of[a], row_of[b2]);
+            t[o] = a == b2 ? std::log(L[(size_t)a * K + a]) : L[(size_t)a * K + b2];
+            if (mask) mask[(int64_t)i * D + o] = 1.f;
+          }
+      }
+    }
+  });
+}
+
+mss_status mss_surrogate_unpack(mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells, int32_t slot_modes,
+                                int32_t io_slots, const double *packed) {
+  return guard([&] {
+    MSS_REQUIRE(r && p && n >= 1 && cells && packed, MSS_ERR_INVALID_ARG, "bad argument");
+    unpack_cells(r->r, p->p, std::vector<int>(cells, cells + n), slot_modes, io_slots, packed);
+  });
+}
+
+mss_status mss_surrogate_screen(const mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells, double *err,
+                                void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(r && p && n >= 1 && cells && err, MSS_ERR_INVALID_ARG, "bad argument");
+    const Rom &R = r->r;
+    MSS_REQUIRE(R.source == &p->p, MSS_ERR_STATE, "ROM was not built from this partition");
+    Partition &P = const_cast<Partition &>(p->p);
+    Rom tmp;
+    std::vector<int> Kt, mv;
+    std::vector<std::vector<double>> Cb;
+    rom_topology(P, R.prm, R.cell_m.data(), tmp, Kt, mv, Cb);
+    std::vector<int> list(cells, cells + n);
+    screen_cells(P, list, Kt, Cb, R, R.prm.shift, R.prm.cg_tol, R.prm.cg_maxit, err, (cudaStream_t)stream);
+  });
+}
+
+mss_status mss_surrogate_infer(mss_surrogate *sur, mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells,
+                               int32_t slot_modes, int32_t io_slots, double tol, double *err, int32_t *fallback,
+                               void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(sur && r && p && n >= 1 && cells && err && fallback && tol > 0, MSS_ERR_INVALID_ARG, "bad argument");
+    Rom &R = r->r;
+    MSS_REQUIRE(R.source == &p->p, MSS_ERR_STATE, "ROM was not built from this partition");
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t info[4];
+    mss_status e = mss_surrogate_info(sur, info);
+    MSS_REQUIRE(e == MSS_OK, e, "surrogate info");
+    const int Kp = 6 * slot_modes + io_slots;
+    const int64_t tri = (int64_t)Kp * (Kp + 1) / 2;
+    const int m = R.cell_m[cells[0]];
+    for (int i = 0; i < n; ++i)
+      MSS_REQUIRE(cells[i] >= 0 && cells[i] < R.n_cells && R.cell_m[cells[i]] == m, MSS_ERR_INVALID_ARG,
+                  "cells must exist and share m");
+    MSS_REQUIRE(info[2] == 7 && info[3] == (2 * m - 1) * tri, MSS_ERR_INVALID_ARG,
+                "surrogate outputs do not match the slot layout");
+    const int64_t nx = info[1];
+    std::vector<float> x((size_t)n * nx), f((size_t)n * 7);
+    e = mss_surrogate_cell_inputs(p, n, cells, slot_modes, io_slots, x.data(), f.data());
+    MSS_REQUIRE(e == MSS_OK, e, "surrogate inputs");
+    DevMem dx, df, dy;
+    upload(dx, x);
+    upload(df, f);
+    dy.alloc((size_t)n * info[3] * 4);
+    e = mss_surrogate_predict(sur, n, dx.as<float>(), df.as<float>(), dy.as<float>(), stream);
+    MSS_REQUIRE(e == MSS_OK, e, "surrogate forward");
+    std::vector<float> yh((size_t)n * info[3]);
+    MSS_CUDA(cudaMemcpyAsync(yh.data(), dy.p, yh.size() * 4, cudaMemcpyDeviceToHost, st));
+    MSS_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> yd(yh.begin(), yh.end());
+    std::vector<int> list(cells, cells + n);
+    unpack_cells(R, p->p, list, slot_modes, io_slots, yd.data());
+    Partition &P = const_cast<Partition &>(p->p);
+    Rom tmp;
+    std::vector<int> Kt, mv;
+    std::vector<std::vector<double>> Cb;
+    rom_topology(P, R.prm, R.cell_m.data(), tmp, Kt, mv, Cb);
+    screen_cells(P, list, Kt, Cb, R, R.prm.shift, R.prm.cg_tol, R.prm.cg_maxit, err, st);
+    std::vector<int> bad;
+    for (int i = 0; i < n; ++i) {
+      fallback[i] = !(err[i] <= tol);
+      if (fallback[i]) bad.push_back(cells[i]);
+    }
+    rom_exact_cells(P, bad, Kt, mv, Cb, R.prm, R, st);
+    rom_exact_markov(P, bad, R);
+  });
+}
+
+}  // extern "C"
+
+namespace mss {
 }  // namespace mss
 
 using namespace mss;

@@ -2,7 +2,7 @@
 // patch (plus features describing which faces the cell has) to its S-fraction coefficients,
 // trained on cells whose coefficients the exact off-line stage produced.  The paper has no such
 // component; it replaces the Krylov/Lanczos construction for repeated media, with the exact
-// construction kept as the fallback and judge.
+// construction kept as the fallback for every cell its screen rejects.
 //
 // Network (channels C, hidden H, cell of c^3 voxels, c a power of two >= 4):
 //   conv3d 3x3x3 pad 1: 2 -> C stride 2, then (log2 c - 2) more stride-2 convs C -> C, then one
@@ -200,16 +200,18 @@ __global__ void k_relu_bwd(float *g, const float *a, int B, int64_t n, int64_t s
   if (a[j] <= 0.f) g[j] = 0.f;
 }
 
-// MSE loss and its gradient: dy = 2 (y - t) / (B D) over masked entries (mask may be null)
-__global__ void k_mse(const float *y, const float *t, const float *mask, float *dy, float *part, int B, int D,
-                      int64_t y_stride) {
+// MSE loss and its gradient: dy = 2 (y - t') / (B D) over masked entries (mask may be null),
+// t' = (t - mean) / scale per output when an output transform is set (mean null otherwise)
+__global__ void k_mse(const float *y, const float *t, const float *mask, const float *mean, const float *scale, float *dy,
+                      float *part, int B, int D, int64_t y_stride) {
   __shared__ float sm[kT];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float l = 0.f;
   if (i < (int64_t)B * D) {
     const int b = (int)(i / D), o = (int)(i % D);
     const float mk = mask ? mask[i] : 1.f;
-    const float d = (y[(int64_t)b * y_stride + o] - t[i]) * mk;
+    const float tt = mean ? (t[i] - mean[o]) / scale[o] : t[i];
+    const float d = (y[(int64_t)b * y_stride + o] - tt) * mk;
     dy[(int64_t)b * y_stride + o] = 2.f * d / ((float)B * D);
     l = d * d;
   }
@@ -220,6 +222,14 @@ __global__ void k_mse(const float *y, const float *t, const float *mask, float *
     __syncthreads();
   }
   if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// y = mean + scale * y per output
+__global__ void k_affine(float *y, const float *mean, const float *scale, int B, int D) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)B * D) return;
+  const int o = (int)(i % D);
+  y[i] = mean[o] + scale[o] * y[i];
 }
 
 __global__ void k_sum_parts(const float *part, int n, float *out, float scale) {
@@ -282,6 +292,7 @@ struct mss_surrogate {
   int64_t nparam = 0, act_per = 0;   // activation arena elements per sample
   int64_t step = 0;
   mss::DevMem p, g, m1, m2, wbf, isw, act, dact, part, loss;
+  mss::DevMem out_mean, out_scale;   // output transform (empty: identity)
 };
 
 namespace mss {
@@ -539,7 +550,9 @@ mss_status mss_surrogate_train_step(mss_surrogate *s, int32_t batch, const float
     const auto &lo = s->L.back();
     MSS_CUDA(cudaMemsetAsync(s->dact.p, 0, (size_t)batch * s->act_per * 4, st));
     const int64_t n = (int64_t)batch * s->nout;
-    k_mse<<<nb(n), kT, 0, st>>>(s->act.as<float>() + lo.out_off, target, mask, s->dact.as<float>() + lo.out_off,
+    const bool aff = s->out_mean.p != nullptr;
+    k_mse<<<nb(n), kT, 0, st>>>(s->act.as<float>() + lo.out_off, target, mask, aff ? s->out_mean.as<float>() : nullptr,
+                                aff ? s->out_scale.as<float>() : nullptr, s->dact.as<float>() + lo.out_off,
                                 s->part.as<float>(), batch, s->nout, s->act_per);
     k_sum_parts<<<1, kT, 0, st>>>(s->part.as<float>(), (int)nb(n), s->loss.as<float>(), 1.f / (float)n);
     sur_backward(*s, batch, st);
@@ -549,6 +562,65 @@ mss_status mss_surrogate_train_step(mss_surrogate *s, int32_t batch, const float
                                          s->wbf.as<__nv_bfloat16>(), s->isw.as<unsigned char>(), s->nparam, lr, b1, b2,
                                          1e-8f, 1.f - std::pow(b1, (float)s->step), 1.f - std::pow(b2, (float)s->step));
     if (loss) MSS_CUDA(cudaMemcpyAsync(loss, s->loss.p, 4, cudaMemcpyDeviceToDevice, st));
+    MSS_CUDA(cudaGetLastError());
+  });
+}
+
+mss_status mss_surrogate_set_output_transform(mss_surrogate *s, const float *mean, const float *scale) {
+  return guard([&] {
+    MSS_REQUIRE(s && ((mean == nullptr) == (scale == nullptr)), MSS_ERR_INVALID_ARG, "bad argument");
+    if (!mean) {
+      s->out_mean.release();
+      s->out_scale.release();
+      return;
+    }
+    for (int o = 0; o < s->nout; ++o)
+      MSS_REQUIRE(scale[o] > 0 && std::isfinite(scale[o]) && std::isfinite(mean[o]), MSS_ERR_INVALID_ARG,
+                  "output scales must be positive and finite");
+    upload(s->out_mean, std::vector<float>(mean, mean + s->nout));
+    upload(s->out_scale, std::vector<float>(scale, scale + s->nout));
+  });
+}
+
+mss_status mss_surrogate_fit_output_transform(mss_surrogate *s, int32_t n, const double *targets, const float *mask) {
+  return guard([&] {
+    MSS_REQUIRE(s && n >= 1 && targets, MSS_ERR_INVALID_ARG, "bad argument");
+    const int D = s->nout;
+    std::vector<double> sum(D, 0.0), sq(D, 0.0), cnt(D, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int o = 0; o < D; ++o) {
+        const double w = mask ? (double)mask[(int64_t)i * D + o] : 1.0;
+        const double v = targets[(int64_t)i * D + o];
+        sum[o] += w * v;
+        sq[o] += w * v * v;
+        cnt[o] += w;
+      }
+    std::vector<float> mean(D, 0.f), scale(D, 1.f);
+    for (int o = 0; o < D; ++o) {
+      if (cnt[o] <= 0) continue;
+      const double mu = sum[o] / cnt[o];
+      const double var = std::max(0.0, sq[o] / cnt[o] - mu * mu);
+      mean[o] = (float)mu;
+      scale[o] = (float)std::max(std::sqrt(var), 1e-3 * std::max(1.0, std::fabs(mu)));
+    }
+    upload(s->out_mean, mean);
+    upload(s->out_scale, scale);
+  });
+}
+
+mss_status mss_surrogate_predict(mss_surrogate *s, int32_t batch, const float *x, const float *feat, float *y,
+                                 void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(s && batch >= 1 && x && y && (s->nfeat == 0 || feat), MSS_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    sur_alloc_batch(*s, batch);
+    sur_forward(*s, batch, x, feat, st);
+    const auto &lo = s->L.back();
+    MSS_CUDA(cudaMemcpy2DAsync(y, (size_t)s->nout * 4, s->act.as<float>() + lo.out_off, (size_t)s->act_per * 4,
+                               (size_t)s->nout * 4, batch, cudaMemcpyDeviceToDevice, st));
+    if (s->out_mean.p)
+      k_affine<<<nb((int64_t)batch * s->nout), kT, 0, st>>>(y, s->out_mean.as<float>(), s->out_scale.as<float>(), batch,
+                                                             s->nout);
     MSS_CUDA(cudaGetLastError());
   });
 }

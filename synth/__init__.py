@@ -180,6 +180,42 @@ def workload_3d_layers(n: int = 128, cell: int = 16, m: int = 4, n_modes: int = 
                     n_steps, 0.5, fp, ricker_band_limit(fp))
 
 
+def medium_family(n: int = 32, cell: int = 8, n_media: int = 16, m: int = 2, n_modes: int = 3,
+                  seed_index: int = 11) -> List[Workload]:
+    """Media for training and testing a learned surrogate of the off-line stage.
+
+    The 3D layered recipe of ``workload_3d_layers`` (Neumann top, Dirichlet elsewhere, 4 layers,
+    Gaussian-random-field log-perturbation of sigma with correlation length 4 voxels), with the
+    layer values drawn per medium: sigma = 2^U(0, 3), rho = U(1, 2.5), field amplitude U(0, 0.2),
+    and the layer boundaries shifted by up to a quarter cell.  Sources on a surface line and one
+    receiver lattice, off the cell skeleton, identical for all media.  f_peak / f_max are those of
+    the slowest medium the recipe can draw (c_min = sqrt(1 / 2.5) exp(-0.6)), so one shift serves
+    the whole family.
+    """
+    rng = np.random.default_rng(SEED_BASE + seed_index)
+    grid = Grid(n=(n, n, n), h=1.0 / n, bc=(("D", "N"), ("D", "D"), ("D", "D")))
+    q = cell // 4
+    xs = [q + 2 * q * j for j in range(n // (2 * q))][:2]
+    src = np.array([[n, n // 2 + cell // 2, x] for x in xs])
+    rcv = np.array([[n, cell // 2 + cell * l, x] for l in range(n // cell) for x in xs])
+    c_min = math.sqrt(1.0 / 2.5) * math.exp(-0.6)
+    fp = c_min / (20.0 * grid.h)
+    out = []
+    for k in range(n_media):
+        sig_l = 2.0 ** rng.uniform(0.0, 3.0, 4)
+        rho_l = rng.uniform(1.0, 2.5, 4)
+        amp = rng.uniform(0.0, 0.2)
+        shift = int(rng.integers(-(cell // 4), cell // 4 + 1))
+        j = np.clip(np.arange(n) + shift, 0, n - 1)
+        li = _layer_index(n, 4)[j]
+        g = gaussian_random_field((n, n, n), 4.0, rng)
+        sigma = sig_l[li][:, None, None] * np.exp(amp * g)
+        rho = rho_l[li][:, None, None] * np.ones((n, n, n))
+        out.append(Workload("family_%d_%d" % (n, k), grid, sigma, rho, (cell, cell, cell), m, n_modes, src, rcv,
+                            400, 0.5, fp, ricker_band_limit(fp)))
+    return out
+
+
 def workload_3d_dipping(n: int = 256, cell: int = 16, m: int = 4, n_modes: int = 15,
                         n_steps: int = 6000, seed_index: int = 2) -> Workload:
     """3D acoustic, n^3 voxels, Dirichlet walls, lognormal GRF background + 2 dipping interfaces.
