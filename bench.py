@@ -12,7 +12,10 @@ FP64 stepping, the same GPU's fine-grid leapfrog (FP32), receiver-trace differen
 off-line build time, per-kernel roofline, the oracle timed on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-    python bench.py --profile N      # same workload, N eager time steps, for ncu captures
+    python bench.py --profile N [--sched K]   # same workload, N eager time steps, for ncu captures
+
+The step schedule (graph-captured kernels with the plain or TMA-streamed cell kernel, or the
+persistent time-block kernel) is picked by the library's autotuner before the timed region.
 """
 from __future__ import annotations
 
@@ -163,14 +166,22 @@ def _kernel_model(rom_info, topo_K, topo_m, n_src, es):
     return byts, flops
 
 
-def _traffic_record(kernel_src: str):
-    """ncu DRAM bytes per launch of the cell kernel, if recorded for this exact kernel source."""
+SCHED_NAMES = ["graph", "graph_stream", "persistent", "persistent_stream"]
+CELL_KERNEL = {0: ("k_cell<float,16>", ["online.cu"]), 1: ("k_cell_s", ["cell_stream.cuh", "online.cu"])}
+
+
+def _traffic_record(kernel: str, sources):
+    """ncu DRAM bytes per launch of a cell kernel, if recorded for these exact kernel sources."""
     path = os.path.join(ROOT, "profiles", "cell_kernel_traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return rec.get("bytes_per_launch") if rec.get("source_sha256") == sha else None
+    rec = json.load(open(path)).get("kernels", {}).get(kernel)
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for f in sources:
+        h.update(open(os.path.join(ROOT, "paper_1604_06750_gb300", "csrc", f), "rb").read())
+    return rec.get("bytes_per_launch") if rec.get("source_sha256") == h.hexdigest() else None
 
 
 def run_native(args):
@@ -216,14 +227,17 @@ def run_native(args):
     stream = torch.cuda.current_stream(dev)
     if args.profile:
         sim = P.Sim(LR, P.FP32_TC if args.prec == "fp32_tc" else P.FP32, tau, corner_correction=True)
+        sim.set_schedule(args.sched)
         tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
         sim.step(args.profile, wd, tr, use_graph=False)
         torch.cuda.synchronize()
         sim.info()
-        print(json.dumps({"profile_steps": args.profile, "precision": args.prec}))
+        print(json.dumps({"profile_steps": args.profile, "precision": args.prec, "schedule": SCHED_NAMES[args.sched]}))
         return
     sim = P.Sim(LR, P.FP32, tau, corner_correction=True)
     kper = int(sim.info()[6])
+    # ---- schedule: the library times every available one and keeps the fastest
+    sched, sched_ms = sim.autotune(200)
     tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
     flush = torch.empty(int(512e6) // 4, device=dev, dtype=torch.float32)
     # ---- warm-up (captures the CUDA graph)
@@ -260,9 +274,14 @@ def run_native(args):
     value = world * units / t_step
     tr32 = tr.double().cpu().numpy()
     # ---- per-kernel timing (eager, CUDA events on the launching stream)
+    # per-kernel events need separate launches: profile the graph schedule with the same cell body
+    prof_sched = 1 if sched in (1, 3) else 0
+    kname, ksrc = CELL_KERNEL[prof_sched]
+    sim.set_schedule(prof_sched)
     sim.reset()
     prof_steps = 400
     ms = sim.step_profile(prof_steps, wd, tr)
+    sim.set_schedule(sched)
     _, algo_flops = _kernel_model(None, Ks, cm, S, 4)
     algo_bytes, _ = _kernel_model(None, Ks, cm, S, 4)
     peaks = {}
@@ -277,14 +296,14 @@ def run_native(args):
     achieved_tf = algo_flops / cell_s / 1e12
     ridge = alu_peak * 1e12 / (hbm * 1e9)
     intensity = algo_flops / algo_bytes
-    traffic = _traffic_record(os.path.join(ROOT, "paper_1604_06750_gb300", "csrc", "online.cu"))
+    traffic = _traffic_record(kname, ksrc)
     if intensity < ridge:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
                 "traffic": traffic}
     else:
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved_tf / alu_peak, "traffic": traffic}
-    roof.update({"kernel": "k_cell<float,16>", "algorithmic_bytes_per_launch": algo_bytes,
+    roof.update({"kernel": kname, "algorithmic_bytes_per_launch": algo_bytes,
                  "algorithmic_flops_per_launch": algo_flops, "intensity_flop_per_byte": intensity,
                  "ms_per_launch": ms[0], "fp32_alu_frac": achieved_tf / alu_peak,
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
@@ -374,7 +393,11 @@ def run_native(args):
             "config": _config(wl, {"precision": "fp32 state and coefficients", "corner_correction": True,
                                    "l2": "flushed between steps (512 MB write)",
                                    "parallelism": "independent source batches per GPU" if world > 1 else "single GPU"}),
-            "clocks": ck, "gpu_launches": int(args.steps * nst * kper),
+            "clocks": ck,
+            "gpu_launches": int(args.steps * (nst * kper if sched in (0, 1) else -(-nst // 512))),
+            "schedule": {"chosen": SCHED_NAMES[sched],
+                         "autotune_ms_per_time_step": {SCHED_NAMES[k]: (float(sched_ms[k]) if sched_ms[k] >= 0 else None)
+                                                       for k in range(len(SCHED_NAMES))}},
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "fp64": {"value": units / t64, "unit": UNIT, "ms": 1e3 * t64},
             "fp32_tc": {"value": units / ttc, "unit": UNIT, "ms": 1e3 * ttc,
@@ -401,6 +424,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--profile", type=int, default=0, help="run N eager time steps after setup and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32_tc"], help="precision of the --profile run")
+    ap.add_argument("--sched", type=int, default=0, choices=[0, 1, 2, 3], help="schedule of the --profile run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

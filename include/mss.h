@@ -257,6 +257,32 @@ mss_status mss_step_profile(mss_sim *s, int64_t n_steps, const double *waveform,
  * save: now[], old[] <- state; load: state <- now[], old[] (and the step counter).
  * Resuming from a saved state continues bit-identically on the same precision. */
 mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_t *steps_taken);
+
+/* Schedules of one step (Algorithm alg1red step 2; all give the same arithmetic, element by
+ * element, for the same precision and tile):
+ *   GRAPH            cell, face(+receivers) and corner kernels per step, the loop captured as a
+ *                    CUDA graph when use_graph is set;
+ *   GRAPH_STREAM     as GRAPH with the streamed FP32 cell kernel: each cell's coefficient stream
+ *                    staged into shared memory by 1-D TMA bulk copies through a 4-slot ring
+ *                    (FP32, 16-source tiles, K_i <= 128);
+ *   PERSIST          one cooperative persistent kernel per block of up to 512 steps, phases
+ *                    separated by a grid barrier with a 1 s time limit (CUDA-core precisions);
+ *   PERSIST_STREAM   PERSIST with the streamed cell body.
+ * The default is GRAPH; mss_sim_autotune times every available schedule and keeps the fastest. */
+#define MSS_SCHED_GRAPH 0
+#define MSS_SCHED_GRAPH_STREAM 1
+#define MSS_SCHED_PERSIST 2
+#define MSS_SCHED_PERSIST_STREAM 3
+#define MSS_SCHED_COUNT 4
+/* Errors: INVALID_ARG (schedule not available for this sim's precision, tile or cell sizes). */
+mss_status mss_sim_set_schedule(mss_sim *s, int32_t sched);
+/* sched: current schedule; available (may be NULL): [MSS_SCHED_COUNT] 1 where usable. */
+mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *available);
+/* Time n_steps (rounded up to even) of every available schedule on zero input, after one
+ * untimed pass each, restoring the state after each; keep the fastest.  ms (host, may be NULL):
+ * [MSS_SCHED_COUNT] ms per step, -1 where unavailable; chosen (may be NULL) receives the pick.
+ * Synchronises the stream.  Errors: INVALID_ARG, TIMEOUT, CUDA. */
+mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *ms, int32_t *chosen);
 mss_status mss_sim_load_state(mss_sim *s, const double *now, const double *old, int64_t steps_taken);
 void mss_sim_destroy(mss_sim *s);
 

@@ -19,6 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmss.so")
 
 FP64, FP32, FP32_TC, BF16_TC = 0, 1, 2, 3
+SCHED_GRAPH, SCHED_GRAPH_STREAM, SCHED_PERSIST, SCHED_PERSIST_STREAM = 0, 1, 2, 3
+SCHED_COUNT = 4
 DIRICHLET, NEUMANN = 0, 1
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "KRYLOV_DEFLATION", 4: "LANCZOS_BREAKDOWN",
@@ -121,6 +123,9 @@ _SIGS = [
     ("mss_surrogate_set_output_transform", C.c_int32, [_P, _P, _P]),
     ("mss_surrogate_fit_output_transform", C.c_int32, [_P, C.c_int32, _P, _P]),
     ("mss_surrogate_predict", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P]),
+    ("mss_sim_set_schedule", C.c_int32, [_P, C.c_int32]),
+    ("mss_sim_get_schedule", C.c_int32, [_P, _P, _P]),
+    ("mss_sim_autotune", C.c_int32, [_P, C.c_int32, _P, _P, _P]),
     ("mss_surrogate_infer", C.c_int32, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
 ]
 
@@ -476,6 +481,23 @@ class Sim(_Handle):
     def load_state(self, now, old, steps: int):
         a, b = _arr(now, np.float64), _arr(old, np.float64)
         _check(lib().mss_sim_load_state(self._h, _ptr(a), _ptr(b), int(steps)))
+
+    def set_schedule(self, sched: int):
+        _check(lib().mss_sim_set_schedule(self._h, int(sched)))
+
+    def schedule(self):
+        """(current schedule, availability mask [SCHED_COUNT])."""
+        cur = np.zeros(1, np.int32)
+        av = np.zeros(SCHED_COUNT, np.int32)
+        _check(lib().mss_sim_get_schedule(self._h, _ptr(cur), _ptr(av)))
+        return int(cur[0]), av
+
+    def autotune(self, n_steps: int = 32, stream=None):
+        """Time every available schedule, keep the fastest; returns (chosen, ms per step)."""
+        ms = np.zeros(SCHED_COUNT)
+        ch = np.zeros(1, np.int32)
+        _check(lib().mss_sim_autotune(self._h, int(n_steps), _stream(stream), _ptr(ms), _ptr(ch)))
+        return int(ch[0]), ms
 
 
 class Surrogate(_Handle):

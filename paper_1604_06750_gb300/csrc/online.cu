@@ -52,7 +52,7 @@ struct StepArgs {
   // values
   const T *coef, *minv, *src_val, *rcv_val, *cg_rows, *cg_w;
   T *fstate0, *fstate1, *cstate0, *cstate1, *flux, *uhat;
-  int S, n_cells, n_faces, n_rcv, corners;
+  int S, n_cells, n_faces, n_rcv, corners, n_cfaces;
   T tau2;
 };
 
@@ -93,13 +93,13 @@ template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
 
+// One (cell, source tile) of the cell phase with the CUDA cores; any block size.
 template <typename T, int ST>
-__global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 4 : 2) k_cell(const StepArgs<T> a, const int cur) {
-  const int cell = blockIdx.x;
-  const int s0 = blockIdx.y * ST;
+__device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, const int cell, const int tile,
+                                          unsigned char *smem_raw) {
+  const int s0 = tile * ST;
   const int K = a.cell_K[cell], m = a.cell_m[cell];
   const int ns = min(ST, a.S - s0);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T *X = reinterpret_cast<T *>(smem_raw);        // U (layers 1..m, [k][r][s]), then F^k
   T *D = X + (size_t)m * K * ST;                 // U^{k+1} - U^k, then F^k - F^{k-1}
   int64_t *rows = reinterpret_cast<int64_t *>(D + (size_t)m * K * ST);   // K boundary rows: face row*2+side
@@ -196,15 +196,21 @@ __global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 4 : 2) k_cell(c
 }
 
 template <typename T, int ST>
-__global__ void __launch_bounds__(kFaceThreads) k_face(const StepArgs<T> a, const int cur, const double *w,
-                                                       T *traces) {
-  const int b = blockIdx.x;
-  const int s0 = blockIdx.y * ST;
+__global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 4 : 2) k_cell(const StepArgs<T> a, const int cur) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cell_item<T, ST>(a, cur, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// Item b of the face phase: b < n_faces is a face update, the rest are receiver blocks of
+// blockDim.x / ST receivers each (sampled before the state advances).
+template <typename T, int ST>
+__device__ __forceinline__ void face_item(const StepArgs<T> &a, const int cur, const int b, const int tile,
+                                          const double *w, T *traces, unsigned char *smem_raw) {
+  const int s0 = tile * ST;
   const int ns = min(ST, a.S - s0);
   const int S = a.S;
   const T *fs = cur ? a.fstate1 : a.fstate0;
   if (b < a.n_faces) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int f = b, M = a.face_M[f];
     T *sum = reinterpret_cast<T *>(smem_raw);    // M x ST flux sums
     T *nv = sum + (size_t)M * ST;                // M x ST new face values (corner correction only)
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_face(const StepArgs<T> a, cons
     }
   } else {
     // receivers: sample the state at this step, before it is advanced
-    const int per = kFaceThreads / ST;
+    const int per = (int)blockDim.x / ST;
     const int r = (b - a.n_faces) * per + (int)threadIdx.x / ST;
     const int s = (int)threadIdx.x % ST;
     if (r >= a.n_rcv || s >= ns) return;
@@ -275,16 +281,23 @@ __global__ void __launch_bounds__(kFaceThreads) k_face(const StepArgs<T> a, cons
 // - u^_l from the pre-correction values u^ (computed by k_face), then u~_f += sum_l s_l delta_l,
 // in place on the new level (each block touches only its own face's rows).
 template <typename T, int ST>
-__global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, const int cur) {
-  const int f = a.cfaces[blockIdx.x];
-  const int s0 = blockIdx.y * ST;
+__global__ void __launch_bounds__(kFaceThreads) k_face(const StepArgs<T> a, const int cur, const double *w,
+                                                       T *traces) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  face_item<T, ST>(a, cur, blockIdx.x, blockIdx.y, w, traces, smem_raw);
+}
+
+template <typename T, int ST>
+__device__ __forceinline__ void corner_item(const StepArgs<T> &a, const int cur, const int ci, const int tile,
+                                            unsigned char *smem_raw) {
+  const int f = a.cfaces[ci];
+  const int s0 = tile * ST;
   const int ns = min(ST, a.S - s0);
   const int S = a.S;
   const int M = a.face_M[f];
   const int64_t row0 = a.face_row[f];
   T *dst = cur ? a.fstate0 : a.fstate1;
   const int j0 = a.fm_ptr[f], nm = a.fm_ptr[f + 1] - j0;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T *delta = reinterpret_cast<T *>(smem_raw);   // nm x ST
   T *rowsm = delta + (size_t)nm * ST;           // nm x M member rows of S_f
   for (int i = threadIdx.x; i < nm * M; i += blockDim.x) {
@@ -313,9 +326,16 @@ __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, co
   }
 }
 
+template <typename T, int ST>
+__global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, const int cur) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  corner_item<T, ST>(a, cur, blockIdx.x, blockIdx.y, smem_raw);
+}
+
 }  // namespace mss
 
 #include "cell_tc.cuh"
+#include "cell_stream.cuh"
 
 namespace mss {
 
@@ -328,14 +348,15 @@ struct SimDev {
   DevMem coef, minv, src_val, rcv_val, cg_rows, cg_w;
   DevMem fstate[2], cstate[2], flux, uhat, cfaces, wbuf, tbuf;
   DevMem tc_blob, tc_off, tc_Kp, tc_Kr, tc_err;
+  DevMem sc_coef, sc_off, sc_Kq, bar;   // streamed cell kernel blob, grid barrier words
 };
 
 struct GraphKey {
   int64_t n;
   const void *w, *t;
-  int cur;
+  int cur, sched;
   bool operator<(const GraphKey &o) const {
-    return std::tie(n, w, t, cur) < std::tie(o.n, o.w, o.t, o.cur);
+    return std::tie(n, w, t, cur, sched) < std::tie(o.n, o.w, o.t, o.cur, o.sched);
   }
 };
 
@@ -353,6 +374,13 @@ struct mss_sim {
   int cur = 0;
   double tau = 0;
   size_t cell_smem = 0, face_smem = 0, corner_smem = 0;
+  // schedule of the step: MSS_SCHED_* (graph-captured kernels, plain or streamed cell kernel,
+  // or the persistent time-block kernel with either cell body)
+  int sched = MSS_SCHED_GRAPH;
+  bool stream_ok = false;
+  size_t stream_smem = 0;
+  mss::StreamArgs sca{};
+  int persist_block = 512;           // steps per persistent launch
   int64_t dev_bytes = 0;
   mss::SimDev d;
   std::map<mss::GraphKey, cudaGraphExec_t> graphs;
@@ -415,6 +443,7 @@ static StepArgs<T> make_args(const mss_sim &s) {
   a.n_faces = s.n_faces;
   a.n_rcv = s.n_rcv;
   a.corners = s.corners;
+  a.n_cfaces = s.n_cfaces;
   a.tau2 = (T)(s.tau * s.tau);
   return a;
 }
@@ -427,6 +456,8 @@ static void set_smem_attrs(const mss_sim &s) {
     MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
   }
   MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
+  if (s.stream_ok)
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.stream_smem));
   MSS_CUDA(cudaFuncSetAttribute(k_face<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.face_smem));
   MSS_CUDA(cudaFuncSetAttribute(k_corner<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.corner_smem));
 }
@@ -449,7 +480,58 @@ static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStr
     }
   }
   const dim3 gc(s.n_cells, s.tiles);
+  if constexpr (std::is_same<T, float>::value && ST == kStreamST) {
+    if (s.sched == MSS_SCHED_GRAPH_STREAM) {
+      k_cell_s<<<gc, kCellThreads, s.stream_smem, st>>>(a, s.sca, cur);
+      return;
+    }
+  }
   k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
+}
+
+// Shared memory of the persistent kernel: the largest of its phases.
+template <typename T, int ST>
+static size_t persist_smem(const mss_sim &s, bool stream) {
+  const size_t aux = stream ? (size_t)kStreamSlots * kStreamChunk + 64 : 0;
+  return std::max({stream ? s.stream_smem : s.cell_smem, aux + s.face_smem, aux + s.corner_smem});
+}
+
+// n steps as persistent launches of at most persist_block steps each (cooperative: the driver
+// refuses a grid that cannot be resident at once).
+template <typename T, int ST>
+static void launch_persist(mss_sim &s, int64_t n, const double *w, T *traces, cudaStream_t st) {
+  const bool stream = s.sched == MSS_SCHED_PERSIST_STREAM;
+  StepArgs<T> a = make_args<T>(s);
+  const size_t smem = persist_smem<T, ST>(s, stream);
+  void (*kern)(const StepArgs<T>, const StreamArgs, const int, const int, const double *, T *, unsigned *, const int);
+  if constexpr (std::is_same<T, float>::value && ST == kStreamST) {
+    kern = stream ? k_persist<T, ST, true> : k_persist<T, ST, false>;
+  } else {
+    MSS_REQUIRE(!stream, MSS_ERR_INVALID_ARG, "the streamed cell body needs FP32 and 16-source tiles");
+    kern = k_persist<T, ST, false>;
+  }
+  MSS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, sms = 0;
+  MSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCellThreads, smem));
+  MSS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device));
+  MSS_REQUIRE(per_sm >= 1, MSS_ERR_INVALID_ARG, "persistent kernel does not fit on an SM");
+  const int per = kCellThreads / ST;
+  int n_rcv_items = (s.n_rcv + per - 1) / per;
+  const int64_t items = (int64_t)std::max(s.n_cells, s.n_faces + n_rcv_items) * s.tiles;
+  int grid = (int)std::min<int64_t>((int64_t)per_sm * sms, std::max<int64_t>(1, items));
+  StreamArgs t = s.sca;
+  t.err = s.d.tc_err.as<int>();
+  unsigned *bar = s.d.bar.as<unsigned>();
+  int cur = s.cur;
+  for (int64_t j0 = 0; j0 < n; j0 += s.persist_block) {
+    int nb = (int)std::min<int64_t>(s.persist_block, n - j0);
+    const double *wj = w + j0;
+    T *tj = traces + j0 * (int64_t)s.n_rcv * s.n_src;
+    MSS_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+    void *args[] = {&a, &t, &cur, &nb, &wj, &tj, &bar, &n_rcv_items};
+    MSS_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kCellThreads), args, smem, st));
+    cur ^= (nb & 1);
+  }
 }
 
 template <typename T, int ST>
@@ -471,13 +553,15 @@ static void launch_steps(mss_sim &s, int64_t n, const double *w, T *traces, cuda
 template <typename T, int ST>
 static void step_impl(mss_sim &s, int64_t n, const double *w, void *traces, int use_graph, cudaStream_t st) {
   set_smem_attrs<T, ST>(s);
-  if (!use_graph) {
+  if (s.sched == MSS_SCHED_PERSIST || s.sched == MSS_SCHED_PERSIST_STREAM) {
+    launch_persist<T, ST>(s, n, w, (T *)traces, st);
+  } else if (!use_graph) {
     launch_steps<T, ST>(s, n, w, (T *)traces, st);
   } else {
     // capture and replay on the sim's own stream (the legacy stream cannot be captured)
     MSS_CUDA(cudaEventRecord(s.ev_in, st));
     MSS_CUDA(cudaStreamWaitEvent(s.cap, s.ev_in, 0));
-    GraphKey key{n, w, traces, s.cur};
+    GraphKey key{n, w, traces, s.cur, s.sched};
     auto it = s.graphs.find(key);
     if (it == s.graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -757,6 +841,39 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
     }
   }
   s.cell_rows = srows;
+  // streamed cell kernel: FP32 CUDA-core path with 16-source tiles and K_i <= 128; the same
+  // matrices as coef, each row padded to Kq = K rounded up to 4 floats (16-byte rows)
+  if (prec == MSS_FP32 && !s.tc && s.ST == kStreamST && s.max_K <= 128) {
+    const size_t need = (size_t)kStreamSlots * kStreamChunk + 64 + 2 * (size_t)s.max_m * s.max_K * kStreamST * 4 +
+                        8 * (size_t)s.max_K;
+    if (need <= (size_t)dev_smem) {
+      std::vector<float> blob;
+      std::vector<int64_t> soff(R.n_cells);
+      std::vector<int32_t> kq(R.n_cells);
+      for (int c = 0; c < R.n_cells; ++c) {
+        const int K = R.cell_K[c], m = R.cell_m[c], Kq = (K + 3) / 4 * 4;
+        kq[c] = Kq;
+        soff[c] = (int64_t)blob.size();
+        const double *src = coef.data() + cell_coef[c];
+        for (int q = 0; q < 2 * m - 1; ++q)
+          for (int j = 0; j < K; ++j) {
+            for (int r = 0; r < K; ++r) blob.push_back((float)src[(size_t)q * K * K + (size_t)j * K + r]);
+            for (int r = K; r < Kq; ++r) blob.push_back(0.f);
+          }
+      }
+      upload(s.d.sc_coef, blob);
+      upload(s.d.sc_off, soff);
+      upload(s.d.sc_Kq, kq);
+      s.sca.coef = s.d.sc_coef.as<float>();
+      s.sca.coef_off = s.d.sc_off.as<int64_t>();
+      s.sca.Kq = s.d.sc_Kq.as<int32_t>();
+      s.stream_smem = need;
+      s.stream_ok = true;
+    }
+  }
+  if (!s.tc) upload(s.d.tc_err, std::vector<int>(1, 0));   // error word of the bounded waits
+  s.sca.err = s.d.tc_err.as<int>();
+  upload(s.d.bar, std::vector<unsigned>(2, 0u));
   std::vector<double> minv(R.fmass_off[R.n_faces]);
   for (int f = 0; f < R.n_faces; ++f) {
     auto inv = inverse(R.face_mass.data() + R.fmass_off[f], R.face_M[f]);
@@ -1055,10 +1172,10 @@ mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32
 mss_status mss_sim_info(const mss_sim *s, int64_t info[8]) {
   return guard([&] {
     MSS_REQUIRE(s && info, MSS_ERR_INVALID_ARG, "null argument");
-    if (s->tc) {
+    {
       int e = 0;
       MSS_CUDA(cudaMemcpy(&e, s->d.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-      MSS_REQUIRE(e == 0, MSS_ERR_TIMEOUT, "a tensor-core cell kernel's bounded wait gave up");
+      MSS_REQUIRE(e == 0, MSS_ERR_TIMEOUT, "a bounded wait in a cell kernel or grid barrier gave up");
     }
     info[0] = s->n_src;
     info[1] = s->n_rcv;
@@ -1096,6 +1213,115 @@ mss_status mss_step_profile(mss_sim *s, int64_t n_steps, const double *waveform,
     cudaStream_t st = (cudaStream_t)stream;
     if (s->prec == MSS_FP64) profile_dispatch<double>(*s, n_steps, waveform, traces, ms, st);
     else profile_dispatch<float>(*s, n_steps, waveform, traces, ms, st);
+  });
+}
+
+static bool sched_allowed(const mss_sim &s, int sched) {
+  switch (sched) {
+    case MSS_SCHED_GRAPH: return true;
+    case MSS_SCHED_GRAPH_STREAM: return s.stream_ok;
+    case MSS_SCHED_PERSIST: return !s.tc;
+    case MSS_SCHED_PERSIST_STREAM: return s.stream_ok;
+    default: return false;
+  }
+}
+
+mss_status mss_sim_set_schedule(mss_sim *s, int32_t sched) {
+  return guard([&] {
+    MSS_REQUIRE(s, MSS_ERR_INVALID_ARG, "null argument");
+    MSS_REQUIRE(sched_allowed(*s, sched), MSS_ERR_INVALID_ARG, "schedule not available for this sim");
+    s->sched = sched;
+  });
+}
+
+mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *available) {
+  return guard([&] {
+    MSS_REQUIRE(s && sched, MSS_ERR_INVALID_ARG, "null argument");
+    *sched = s->sched;
+    if (available)
+      for (int k = 0; k < MSS_SCHED_COUNT; ++k) available[k] = sched_allowed(*s, k) ? 1 : 0;
+  });
+}
+
+mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *ms, int32_t *chosen) {
+  return guard([&] {
+    MSS_REQUIRE(s && n_steps >= 2, MSS_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = n_steps + (n_steps & 1);   // even: the time-level parity returns, graphs are reused
+    const size_t es = s->prec == MSS_FP64 ? 8 : 4;
+    const int64_t nf = s->face_rows * s->n_src, nc = std::max<int64_t>(1, s->cell_rows) * s->n_src;
+    DevMem keep[4], w, tr;
+    DevMem *lv[4] = {&s->d.fstate[0], &s->d.fstate[1], &s->d.cstate[0], &s->d.cstate[1]};
+    const int64_t cnt[4] = {nf, nf, nc, nc};
+    MSS_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < 4; ++i) {
+      keep[i].alloc(cnt[i] * es);
+      MSS_CUDA(cudaMemcpy(keep[i].p, lv[i]->p, cnt[i] * es, cudaMemcpyDeviceToDevice));
+    }
+    w.alloc((size_t)n * 8);
+    MSS_CUDA(cudaMemset(w.p, 0, (size_t)n * 8));
+    tr.alloc((size_t)n * std::max(1, s->n_rcv) * s->n_src * es);
+    const int cur0 = s->cur, sched0 = s->sched;
+    const int64_t steps0 = s->steps;
+    cudaEvent_t e0, e1;
+    MSS_CUDA(cudaEventCreate(&e0));
+    MSS_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_k = sched0;
+    auto restore = [&]() {
+      for (int i = 0; i < 4; ++i)
+        MSS_CUDA(cudaMemcpyAsync(lv[i]->p, keep[i].p, cnt[i] * es, cudaMemcpyDeviceToDevice, st));
+      s->cur = cur0;
+      s->steps = steps0;
+    };
+    try {
+      for (int k = 0; k < MSS_SCHED_COUNT; ++k) {
+        if (ms) ms[k] = -1.0;
+        if (!sched_allowed(*s, k)) continue;
+        s->sched = k;
+        auto run = [&]() {
+          if (s->prec == MSS_FP64) step_dispatch<double>(*s, n, w.as<double>(), tr.p, 1, st);
+          else step_dispatch<float>(*s, n, w.as<double>(), tr.p, 1, st);
+        };
+        run();   // warm-up (and graph capture)
+        MSS_CUDA(cudaEventRecord(e0, st));
+        run();
+        MSS_CUDA(cudaEventRecord(e1, st));
+        MSS_CUDA(cudaEventSynchronize(e1));
+        float t = 0;
+        MSS_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        int err = 0;
+        MSS_CUDA(cudaMemcpy(&err, s->d.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        MSS_REQUIRE(err == 0, MSS_ERR_TIMEOUT, "a bounded wait gave up during autotuning");
+        const double per = t / (double)n;
+        if (ms) ms[k] = per;
+        if (per < best) {
+          best = per;
+          best_k = k;
+        }
+        restore();
+      }
+    } catch (...) {
+      restore();
+      s->sched = sched0;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    MSS_CUDA(cudaStreamSynchronize(st));
+    // graphs recorded on the scratch buffers are dropped with them
+    for (auto it = s->graphs.begin(); it != s->graphs.end();) {
+      if (it->first.w == w.p) {
+        cudaGraphExecDestroy(it->second);
+        it = s->graphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    s->sched = best_k;
+    if (chosen) *chosen = best_k;
   });
 }
 
