@@ -166,8 +166,9 @@ def _kernel_model(rom_info, topo_K, topo_m, n_src, es):
     return byts, flops
 
 
-SCHED_NAMES = ["graph", "graph_stream", "persistent", "persistent_stream"]
-CELL_KERNEL = {0: ("k_cell<float,16>", ["online.cu"]), 1: ("k_cell_s", ["cell_stream.cuh", "online.cu"])}
+SCHED_NAMES = ["graph", "graph_stream", "persistent", "persistent_stream", "graph_split"]
+CELL_KERNEL = {0: ("k_cell<float,16>", ["online.cu"]), 1: ("k_cell_s", ["cell_stream.cuh", "online.cu"]),
+               4: ("k_flux+k_accel", ["cell_split.cuh", "online.cu"])}
 
 
 def _traffic_record(kernel: str, sources):
@@ -275,7 +276,7 @@ def run_native(args):
     tr32 = tr.double().cpu().numpy()
     # ---- per-kernel timing (eager, CUDA events on the launching stream)
     # per-kernel events need separate launches: profile the graph schedule with the same cell body
-    prof_sched = 1 if sched in (1, 3) else 0
+    prof_sched = {0: 0, 1: 1, 2: 0, 3: 1, 4: 4}[sched]
     kname, ksrc = CELL_KERNEL[prof_sched]
     sim.set_schedule(prof_sched)
     sim.reset()
@@ -394,7 +395,7 @@ def run_native(args):
                                    "l2": "flushed between steps (512 MB write)",
                                    "parallelism": "independent source batches per GPU" if world > 1 else "single GPU"}),
             "clocks": ck,
-            "gpu_launches": int(args.steps * (nst * kper if sched in (0, 1) else -(-nst // 512))),
+            "gpu_launches": int(args.steps * {0: nst * kper, 1: nst * kper, 4: nst * (kper + 1)}.get(sched, -(-nst // 512))),
             "schedule": {"chosen": SCHED_NAMES[sched],
                          "autotune_ms_per_time_step": {SCHED_NAMES[k]: (float(sched_ms[k]) if sched_ms[k] >= 0 else None)
                                                        for k in range(len(SCHED_NAMES))}},
@@ -424,7 +425,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--profile", type=int, default=0, help="run N eager time steps after setup and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32_tc"], help="precision of the --profile run")
-    ap.add_argument("--sched", type=int, default=0, choices=[0, 1, 2, 3], help="schedule of the --profile run")
+    ap.add_argument("--sched", type=int, default=0, choices=[0, 1, 2, 3, 4], help="schedule of the --profile run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

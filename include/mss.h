@@ -267,13 +267,17 @@ mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_
  *                    (FP32, 16-source tiles, K_i <= 128);
  *   PERSIST          one cooperative persistent kernel per block of up to 512 steps, phases
  *                    separated by a grid barrier with a 1 s time limit (CUDA-core precisions);
- *   PERSIST_STREAM   PERSIST with the streamed cell body.
+ *   PERSIST_STREAM   PERSIST with the streamed cell body;
+ *   GRAPH_SPLIT      as GRAPH with the cell phase split into a flux kernel and an acceleration
+ *                    kernel of one small CTA per (cell, matrix), fluxes through a scratch block
+ *                    (CUDA-core precisions).
  * The default is GRAPH; mss_sim_autotune times every available schedule and keeps the fastest. */
 #define MSS_SCHED_GRAPH 0
 #define MSS_SCHED_GRAPH_STREAM 1
 #define MSS_SCHED_PERSIST 2
 #define MSS_SCHED_PERSIST_STREAM 3
-#define MSS_SCHED_COUNT 4
+#define MSS_SCHED_GRAPH_SPLIT 4
+#define MSS_SCHED_COUNT 5
 /* Errors: INVALID_ARG (schedule not available for this sim's precision, tile or cell sizes). */
 mss_status mss_sim_set_schedule(mss_sim *s, int32_t sched);
 /* sched: current schedule; available (may be NULL): [MSS_SCHED_COUNT] 1 where usable. */
@@ -448,8 +452,9 @@ typedef struct mss_step_buffers {
  * one scratch array and leaves its contents behind (the step writes every flux slot before it
  * reads it, so nothing needs clearing); calls that overlap on the GPU (different streams, or
  * different threads) race on it and must be serialised by the caller.
- * Errors: INVALID_ARG (null pointers, counts, precision), INVALID_ARG if 2 FR S x element size
- * exceeds MSS_NOALLOC_SCRATCH_BYTES, CUDA. */
+ * The four state buffers must be 16-byte aligned (vector loads).
+ * Errors: INVALID_ARG (null pointers, counts, precision, alignment), INVALID_ARG if 2 FR S x
+ * element size exceeds MSS_NOALLOC_SCRATCH_BYTES, CUDA. */
 mss_status mss_step_noalloc(mss_step_buffers *b, int64_t n_steps, const double *waveform, void *traces,
                             void *stream);
 

@@ -19,8 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmss.so")
 
 FP64, FP32, FP32_TC, BF16_TC = 0, 1, 2, 3
-SCHED_GRAPH, SCHED_GRAPH_STREAM, SCHED_PERSIST, SCHED_PERSIST_STREAM = 0, 1, 2, 3
-SCHED_COUNT = 4
+SCHED_GRAPH, SCHED_GRAPH_STREAM, SCHED_PERSIST, SCHED_PERSIST_STREAM, SCHED_GRAPH_SPLIT = 0, 1, 2, 3, 4
+SCHED_COUNT = 5
 DIRICHLET, NEUMANN = 0, 1
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "KRYLOV_DEFLATION", 4: "LANCZOS_BREAKDOWN",

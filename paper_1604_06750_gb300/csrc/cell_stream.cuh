@@ -23,7 +23,7 @@
 namespace mss {
 
 constexpr int kStreamSlots = 4;
-constexpr int kStreamChunk = 8192;   // bytes per ring slot
+constexpr int kStreamChunk = 16384;  // bytes per ring slot
 constexpr int kStreamST = 16;
 constexpr unsigned long long kGridWaitNs = 1000000000ull;   // 1 s per grid barrier
 
@@ -118,94 +118,106 @@ __device__ bool cell_stream_item(const StepArgs<float> &a, const StreamArgs &t, 
   const int r = tid & 127, g = tid >> 7;          // row, column half
   const bool act = r < K && g < 2;
   const float tau2 = a.tau2;
-  float acc[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) acc[e] = 0.f;
-  int q = 0, j = 0;                               // matrix, row within it
-  for (int c = 0; c < nch; ++c) {
-    if (!stream_wait(full, gc0 + (unsigned)c, t.err)) {
-      if (tid == 0) atomicExch(t.err, 1);
-      stream_drain(full, gc0 + (unsigned)c, gc0 + (unsigned)min(nch, c + kStreamSlots));
-      gc = gc0 + (unsigned)nch;   // bookkeeping only; the caller stops
-      return false;
+  auto fail = [&](int c) {
+    if (tid == 0) atomicExch(t.err, 1);
+    stream_drain(full, gc0 + (unsigned)c, gc0 + (unsigned)min(nch, c + kStreamSlots));
+    gc = gc0 + (unsigned)nch;   // bookkeeping only; the caller stops
+  };
+  int c = 0;                                      // chunk being read
+  if (!stream_wait(full, gc0, t.err)) {
+    fail(0);
+    return false;
+  }
+  for (int q = 0; q < 2 * m - 1; ++q) {
+    if (q == m) {
+      // all fluxes are in X: publish F^1, then E^k = F^k - F^{k-1} into D
+      __syncthreads();
+      if (vec) {
+        for (int i = tid; i < K * (ST / 4); i += blockDim.x) {
+          const int rr = i / (ST / 4), v = i - rr * (ST / 4);
+          *reinterpret_cast<float4 *>(a.flux + rows[rr] * S + s0 + v * 4) = reinterpret_cast<const float4 *>(X)[i];
+        }
+      } else {
+        for (int i = tid; i < K * ST; i += blockDim.x) {
+          const int rr = i / ST, s = i - rr * ST;
+          if (s < ns) a.flux[rows[rr] * S + s0 + s] = X[i];
+        }
+      }
+      for (int i = tid; i < (m - 1) * K * ST; i += blockDim.x) {
+        const size_t jj = (size_t)K * ST + i;
+        D[jj] = X[jj] - X[jj - (size_t)K * ST];
+      }
+      __syncthreads();
     }
-    const float *slot = reinterpret_cast<const float *>(ring + (size_t)((gc0 + c) % kStreamSlots) * kStreamChunk);
-    const int nr = min(CR, total_rows - c * CR);
-    for (int lr = 0; lr < nr; ++lr) {
-      if (j == 0 && q == m) {
-        // all fluxes are in X: publish F^1, then E^k = F^k - F^{k-1} into D
+    const int layer = q < m ? q : q - m + 1;
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+    for (int j0 = 0; j0 < K;) {
+      const int fr = q * K + j0;
+      if (fr >= (c + 1) * CR) {
+        // chunk c consumed by every thread: refill its slot, move to the next chunk
         __syncthreads();
+        if (tid == 0 && c + kStreamSlots < nch) issue(c + kStreamSlots);
+        ++c;
+        if (!stream_wait(full, gc0 + (unsigned)c, t.err)) {
+          fail(c);
+          return false;
+        }
+      }
+      const int j1 = min(K, (c + 1) * CR - q * K);
+      if (act) {
+        const float *sp = reinterpret_cast<const float *>(ring + (size_t)((gc0 + c) % kStreamSlots) * kStreamChunk) +
+                          (size_t)(fr - c * CR) * Kq + r;
+        const float4 *dp = reinterpret_cast<const float4 *>(D + ((size_t)layer * K + j0) * ST) + 2 * g;
+        const int n = j1 - j0;
+#pragma unroll 4
+        for (int i = 0; i < n; ++i) {
+          const float gv = sp[(size_t)i * Kq];
+          const float4 d0 = dp[4 * i], d1 = dp[4 * i + 1];
+          acc[0] += gv * d0.x;
+          acc[1] += gv * d0.y;
+          acc[2] += gv * d0.z;
+          acc[3] += gv * d0.w;
+          acc[4] += gv * d1.x;
+          acc[5] += gv * d1.y;
+          acc[6] += gv * d1.z;
+          acc[7] += gv * d1.w;
+        }
+      }
+      j0 = j1;
+    }
+    // end of matrix q: row r of F^{q+1}, or leapfrog of U^k with Gamma-hat^k E^k
+    if (act) {
+      if (q < m) {
+        float4 *o = reinterpret_cast<float4 *>(X + ((size_t)q * K + r) * ST + 8 * g);
+        o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        o[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      } else {
+        const int k = q - m + 1;
+        const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + 8 * g;
         if (vec) {
-          for (int i = tid; i < K * (ST / 4); i += blockDim.x) {
-            const int rr = i / (ST / 4), v = i - rr * (ST / 4);
-            *reinterpret_cast<float4 *>(a.flux + rows[rr] * S + s0 + v * 4) = reinterpret_cast<const float4 *>(X)[i];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
+            float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
+            od.x = 2.f * nw.x - od.x + tau2 * acc[4 * h + 0];
+            od.y = 2.f * nw.y - od.y + tau2 * acc[4 * h + 1];
+            od.z = 2.f * nw.z - od.z + tau2 * acc[4 * h + 2];
+            od.w = 2.f * nw.w - od.w + tau2 * acc[4 * h + 3];
+            *reinterpret_cast<float4 *>(cso + base + 4 * h) = od;
           }
         } else {
-          for (int i = tid; i < K * ST; i += blockDim.x) {
-            const int rr = i / ST, s = i - rr * ST;
-            if (s < ns) a.flux[rows[rr] * S + s0 + s] = X[i];
-          }
-        }
-        for (int i = tid; i < (m - 1) * K * ST; i += blockDim.x) {
-          const size_t jj = (size_t)K * ST + i;
-          D[jj] = X[jj] - X[jj - (size_t)K * ST];
-        }
-        __syncthreads();
-      }
-      if (act) {
-        const float gv = slot[(size_t)lr * Kq + r];
-        const int layer = q < m ? q : q - m + 1;
-        const float4 *op = reinterpret_cast<const float4 *>(D + ((size_t)layer * K + j) * ST + 8 * g);
-        const float4 d0 = op[0], d1 = op[1];
-        acc[0] += gv * d0.x;
-        acc[1] += gv * d0.y;
-        acc[2] += gv * d0.z;
-        acc[3] += gv * d0.w;
-        acc[4] += gv * d1.x;
-        acc[5] += gv * d1.y;
-        acc[6] += gv * d1.z;
-        acc[7] += gv * d1.w;
-      }
-      if (++j == K) {
-        // end of matrix q
-        if (act) {
-          if (q < m) {
-            float4 *o = reinterpret_cast<float4 *>(X + ((size_t)q * K + r) * ST + 8 * g);
-            o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-            o[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-          } else {
-            const int k = q - m + 1;
-            const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + 8 * g;
-            if (vec) {
 #pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
-                float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
-                od.x = 2.f * nw.x - od.x + tau2 * acc[4 * h + 0];
-                od.y = 2.f * nw.y - od.y + tau2 * acc[4 * h + 1];
-                od.z = 2.f * nw.z - od.z + tau2 * acc[4 * h + 2];
-                od.w = 2.f * nw.w - od.w + tau2 * acc[4 * h + 3];
-                *reinterpret_cast<float4 *>(cso + base + 4 * h) = od;
-              }
-            } else {
-#pragma unroll
-              for (int e = 0; e < 8; ++e)
-                if (8 * g + e < ns) cso[base + e] = 2.f * cs[base + e] - cso[base + e] + tau2 * acc[e];
-            }
-          }
+          for (int e = 0; e < 8; ++e)
+            if (8 * g + e < ns) cso[base + e] = 2.f * cs[base + e] - cso[base + e] + tau2 * acc[e];
         }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) acc[e] = 0.f;
-        j = 0;
-        ++q;
       }
     }
-    __syncthreads();   // slot consumed by every thread
-    if (tid == 0 && c + kStreamSlots < nch) issue(c + kStreamSlots);
   }
+  __syncthreads();   // last chunk consumed (its slot may be refilled by the next item)
   if (m == 1) {
-    // no interior layers: the flux publish above never ran
-    __syncthreads();
+    // no interior layers: publish F^1 here
     for (int i = tid; i < K * ST; i += blockDim.x) {
       const int rr = i / ST, s = i - rr * ST;
       if (s < ns) a.flux[rows[rr] * S + s0 + s] = X[i];
@@ -272,7 +284,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, int *err) {
 // n_steps time steps in one launch: per step the cell items (streamed or plain), the face and
 // receiver items (receiver items hold blockDim.x / ST receivers), then the corner items.
 template <typename T, int ST, bool STREAM>
-__global__ void __launch_bounds__(kCellThreads, 1) k_persist(const StepArgs<T> a, const StreamArgs t, const int cur0,
+__global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 3 : 2) k_persist(const StepArgs<T> a, const StreamArgs t, const int cur0,
                                                              const int n_steps, const double *w, T *traces,
                                                              unsigned *bar, const int n_rcv_items) {
   extern __shared__ __align__(128) unsigned char smem_p[];

@@ -92,6 +92,8 @@ __device__ __forceinline__ void row_times_block(const T *__restrict__ G, int K, 
 template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
+__device__ __forceinline__ float4 pack_vec(const float (&d)[4]) { return make_float4(d[0], d[1], d[2], d[3]); }
+__device__ __forceinline__ double2 pack_vec(const double (&d)[2]) { return make_double2(d[0], d[1]); }
 
 // One (cell, source tile) of the cell phase with the CUDA cores; any block size.
 template <typename T, int ST>
@@ -212,11 +214,15 @@ __device__ __forceinline__ void face_item(const StepArgs<T> &a, const int cur, c
   const T *fs = cur ? a.fstate1 : a.fstate0;
   if (b < a.n_faces) {
     const int f = b, M = a.face_M[f];
+    const int j0 = a.corners ? a.fm_ptr[f] : 0, nm = a.corners ? a.fm_ptr[f + 1] - j0 : 0;
     T *sum = reinterpret_cast<T *>(smem_raw);    // M x ST flux sums
     T *nv = sum + (size_t)M * ST;                // M x ST new face values (corner correction only)
+    T *mi = nv + (size_t)M * ST;                 // M x M inverse face mass
+    T *rw = mi + (size_t)M * M;                  // nm x M rows of S_f of the face's hanging nodes
     const int64_t row0 = a.face_row[f];
     const bool two = a.face_two[f] != 0;
     const T wn = (T)(*w);
+    // stage everything the face needs in one round of independent loads
     for (int i = threadIdx.x; i < M * ST; i += blockDim.x) {
       const int r = i / ST, s = i - r * ST;
       T v = T(0);
@@ -228,13 +234,69 @@ __device__ __forceinline__ void face_item(const StepArgs<T> &a, const int cur, c
       }
       sum[i] = v;
     }
-    __syncthreads();
     const T *Mi = a.minv + a.face_minv[f];
+    for (int i = threadIdx.x; i < M * M; i += blockDim.x) mi[i] = Mi[i];
+    {
+      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int j = threadIdx.x >> 5; j < nm; j += nw) {
+        const T *src = a.cg_rows + a.mem_row[a.fm_member[j0 + j]];
+        for (int c = lane; c < M; c += 32) rw[j * M + c] = src[c];
+      }
+    }
+    __syncthreads();
     T *dst = cur ? a.fstate0 : a.fstate1;        // the old level becomes the new one
+    using V = typename Vec<T>::type;
+    constexpr int VN = Vec<T>::n;
+    constexpr int NV = ST % VN == 0 ? ST / VN : 1;
+    const bool vec = (ST % VN == 0) && (ns == ST) && (S % VN == 0);
+    if (vec) {
+      // same products in the same order as the scalar loops below, VN sources per thread
+      for (int i = threadIdx.x; i < M * NV; i += blockDim.x) {
+        const int r = i / NV, v = i - r * NV;
+        T acc[VN];
+#pragma unroll
+        for (int e = 0; e < VN; ++e) acc[e] = T(0);
+        for (int c = 0; c < M; ++c) {
+          const T mv = mi[r * M + c];
+          const V x = *reinterpret_cast<const V *>(sum + c * ST + v * VN);
+          const T *xe = reinterpret_cast<const T *>(&x);
+#pragma unroll
+          for (int e = 0; e < VN; ++e) acc[e] += mv * xe[e];
+        }
+        const int64_t idx = (row0 + r) * S + s0 + v * VN;
+        const V fv = *reinterpret_cast<const V *>(fs + idx);
+        V dv = *reinterpret_cast<const V *>(dst + idx);
+        const T *fe = reinterpret_cast<const T *>(&fv);
+        T *de = reinterpret_cast<T *>(&dv);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) de[e] = T(2) * fe[e] - de[e] + a.tau2 * acc[e];
+        *reinterpret_cast<V *>(dst + idx) = dv;
+        if (a.corners) *reinterpret_cast<V *>(nv + r * ST + v * VN) = dv;
+      }
+      if (nm > 0) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < nm * NV; i += blockDim.x) {
+          const int j = i / NV, v = i - j * NV;
+          const int l = a.fm_member[j0 + j];
+          T d[VN];
+#pragma unroll
+          for (int e = 0; e < VN; ++e) d[e] = T(0);
+          for (int c = 0; c < M; ++c) {
+            const T rv = rw[j * M + c];
+            const V x = *reinterpret_cast<const V *>(nv + c * ST + v * VN);
+            const T *xe = reinterpret_cast<const T *>(&x);
+#pragma unroll
+            for (int e = 0; e < VN; ++e) d[e] += rv * xe[e];
+          }
+          *reinterpret_cast<V *>(a.uhat + (int64_t)l * S + s0 + v * VN) = pack_vec(d);
+        }
+      }
+      return;
+    }
     for (int i = threadIdx.x; i < M * ST; i += blockDim.x) {
       const int r = i / ST, s = i - r * ST;
       T acc = T(0);
-      for (int c = 0; c < M; ++c) acc += Mi[(size_t)r * M + c] * sum[c * ST + s];
+      for (int c = 0; c < M; ++c) acc += mi[r * M + c] * sum[c * ST + s];
       if (s < ns) {
         const int64_t idx = (row0 + r) * S + s0 + s;
         const T v = T(2) * fs[idx] - dst[idx] + a.tau2 * acc;
@@ -244,18 +306,15 @@ __device__ __forceinline__ void face_item(const StepArgs<T> &a, const int cur, c
         nv[i] = T(0);
       }
     }
-    if (a.corners) {
+    if (nm > 0) {
       // values of this face's hanging nodes, u^_l = s_l . u~_f (Appendix D step 1), pre-correction
-      const int j0 = a.fm_ptr[f], nm = a.fm_ptr[f + 1] - j0;
-      if (nm == 0) return;
       __syncthreads();
       for (int i = threadIdx.x; i < nm * ST; i += blockDim.x) {
         const int j = i / ST, s = i - j * ST;
         if (s >= ns) continue;
         const int l = a.fm_member[j0 + j];
-        const T *row = a.cg_rows + a.mem_row[l];
         T d = T(0);
-        for (int c = 0; c < M; ++c) d += row[c] * nv[c * ST + s];
+        for (int c = 0; c < M; ++c) d += rw[j * M + c] * nv[c * ST + s];
         a.uhat[(int64_t)l * S + s0 + s] = d;
       }
     }
@@ -300,9 +359,61 @@ __device__ __forceinline__ void corner_item(const StepArgs<T> &a, const int cur,
   const int j0 = a.fm_ptr[f], nm = a.fm_ptr[f + 1] - j0;
   T *delta = reinterpret_cast<T *>(smem_raw);   // nm x ST
   T *rowsm = delta + (size_t)nm * ST;           // nm x M member rows of S_f
-  for (int i = threadIdx.x; i < nm * M; i += blockDim.x) {
-    const int j = i / M, c = i - j * M;
-    rowsm[i] = a.cg_rows[a.mem_row[a.fm_member[j0 + j]] + c];
+  {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = threadIdx.x >> 5; j < nm; j += nw) {
+      const T *src = a.cg_rows + a.mem_row[a.fm_member[j0 + j]];
+      for (int c = lane; c < M; c += 32) rowsm[j * M + c] = src[c];
+    }
+  }
+  using V = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  constexpr int NV = ST % VN == 0 ? ST / VN : 1;
+  if ((ST % VN == 0) && (ns == ST) && (S % VN == 0)) {
+    // same products in the same order as the scalar loops below, VN sources per thread
+    for (int i = threadIdx.x; i < nm * NV; i += blockDim.x) {
+      const int j = i / NV, v = i - j * NV;
+      const int l = a.fm_member[j0 + j];
+      const int g = a.mem_group[l];
+      T mean[VN];
+#pragma unroll
+      for (int e = 0; e < VN; ++e) mean[e] = T(0);
+#pragma unroll 4
+      for (int l2 = a.grp_ptr[g]; l2 < a.grp_ptr[g + 1]; ++l2) {
+        const T wv = a.cg_w[l2];
+        const V x = *reinterpret_cast<const V *>(a.uhat + (int64_t)l2 * S + s0 + v * VN);
+        const T *xe = reinterpret_cast<const T *>(&x);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) mean[e] += wv * xe[e];
+      }
+      const V self = *reinterpret_cast<const V *>(a.uhat + (int64_t)l * S + s0 + v * VN);
+      const T *se = reinterpret_cast<const T *>(&self);
+      T d[VN];
+#pragma unroll
+      for (int e = 0; e < VN; ++e) d[e] = mean[e] - se[e];
+      *reinterpret_cast<V *>(delta + j * ST + v * VN) = pack_vec(d);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < M * NV; i += blockDim.x) {
+      const int r = i / NV, v = i - r * NV;
+      T acc[VN];
+#pragma unroll
+      for (int e = 0; e < VN; ++e) acc[e] = T(0);
+      for (int j = 0; j < nm; ++j) {
+        const T rv = rowsm[j * M + r];
+        const V x = *reinterpret_cast<const V *>(delta + j * ST + v * VN);
+        const T *xe = reinterpret_cast<const T *>(&x);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) acc[e] += rv * xe[e];
+      }
+      T *o = dst + (row0 + r) * S + s0 + v * VN;
+      V ov = *reinterpret_cast<const V *>(o);
+      T *oe = reinterpret_cast<T *>(&ov);
+#pragma unroll
+      for (int e = 0; e < VN; ++e) oe[e] += acc[e];
+      *reinterpret_cast<V *>(o) = ov;
+    }
+    return;
   }
   for (int i = threadIdx.x; i < nm * ST; i += blockDim.x) {
     const int j = i / ST, s = i - j * ST;
@@ -311,6 +422,7 @@ __device__ __forceinline__ void corner_item(const StepArgs<T> &a, const int cur,
       const int l = a.fm_member[j0 + j];
       const int g = a.mem_group[l];
       T mean = T(0);
+#pragma unroll 4
       for (int l2 = a.grp_ptr[g]; l2 < a.grp_ptr[g + 1]; ++l2) mean += a.cg_w[l2] * a.uhat[(int64_t)l2 * S + s0 + s];
       d = mean - a.uhat[(int64_t)l * S + s0 + s];
     }
@@ -336,6 +448,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, co
 
 #include "cell_tc.cuh"
 #include "cell_stream.cuh"
+#include "cell_split.cuh"
 
 namespace mss {
 
@@ -349,6 +462,7 @@ struct SimDev {
   DevMem fstate[2], cstate[2], flux, uhat, cfaces, wbuf, tbuf;
   DevMem tc_blob, tc_off, tc_Kp, tc_Kr, tc_err;
   DevMem sc_coef, sc_off, sc_Kq, bar;   // streamed cell kernel blob, grid barrier words
+  DevMem flux_items, accel_items, f_off, F;   // split cell phase
 };
 
 struct GraphKey {
@@ -381,6 +495,8 @@ struct mss_sim {
   size_t stream_smem = 0;
   mss::StreamArgs sca{};
   int persist_block = 512;           // steps per persistent launch
+  int n_flux_items = 0, n_accel_items = 0;
+  size_t split_smem = 0;
   int64_t dev_bytes = 0;
   mss::SimDev d;
   std::map<mss::GraphKey, cudaGraphExec_t> graphs;
@@ -458,6 +574,8 @@ static void set_smem_attrs(const mss_sim &s) {
   MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
   if (s.stream_ok)
     MSS_CUDA(cudaFuncSetAttribute(k_cell_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.stream_smem));
+  MSS_CUDA(cudaFuncSetAttribute(k_flux<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.split_smem));
+  MSS_CUDA(cudaFuncSetAttribute(k_accel<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.split_smem));
   MSS_CUDA(cudaFuncSetAttribute(k_face<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.face_smem));
   MSS_CUDA(cudaFuncSetAttribute(k_corner<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.corner_smem));
 }
@@ -487,6 +605,23 @@ static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStr
     }
   }
   k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
+}
+
+template <typename T>
+static SplitArgs<T> make_split(const mss_sim &s) {
+  SplitArgs<T> p;
+  p.flux_items = s.d.flux_items.as<int2>();
+  p.accel_items = s.d.accel_items.as<int2>();
+  p.f_off = s.d.f_off.as<int64_t>();
+  p.F = s.d.F.as<T>();
+  return p;
+}
+
+template <typename T, int ST>
+static void launch_split(const mss_sim &s, const StepArgs<T> &a, const SplitArgs<T> &p, int cur, cudaStream_t st) {
+  k_flux<T, ST><<<dim3(s.n_flux_items, s.tiles), kSplitThreads, s.split_smem, st>>>(a, p, cur);
+  if (s.n_accel_items > 0)
+    k_accel<T, ST><<<dim3(s.n_accel_items, s.tiles), kSplitThreads, s.split_smem, st>>>(a, p, cur);
 }
 
 // Shared memory of the persistent kernel: the largest of its phases.
@@ -541,8 +676,10 @@ static void launch_steps(mss_sim &s, int64_t n, const double *w, T *traces, cuda
   const int rcv_blocks = (s.n_rcv + per - 1) / per;
   const dim3 gc(s.n_cells, s.tiles), gf(s.n_faces + rcv_blocks, s.tiles), gk(std::max(1, s.n_cfaces), s.tiles);
   int cur = s.cur;
+  const SplitArgs<T> sp = make_split<T>(s);
   for (int64_t j = 0; j < n; ++j) {
-    launch_cell<T, ST>(s, a, cur, st);
+    if (s.sched == MSS_SCHED_GRAPH_SPLIT) launch_split<T, ST>(s, a, sp, cur, st);
+    else launch_cell<T, ST>(s, a, cur, st);
     k_face<T, ST><<<gf, kFaceThreads, s.face_smem, st>>>(a, cur, w + j, traces + j * (int64_t)s.n_rcv * s.n_src);
     if (s.corners) k_corner<T, ST><<<gk, kFaceThreads, s.corner_smem, st>>>(a, cur);
     cur ^= 1;
@@ -595,6 +732,7 @@ static void profile_impl(mss_sim &s, int64_t n, const double *w, T *traces, doub
   const int per = kFaceThreads / ST;
   const int rcv_blocks = (s.n_rcv + per - 1) / per;
   const dim3 gc(s.n_cells, s.tiles), gf(s.n_faces + rcv_blocks, s.tiles), gk(std::max(1, s.n_cfaces), s.tiles);
+  const SplitArgs<T> sp = make_split<T>(s);
   cudaEvent_t ev[4];
   for (auto &e : ev) MSS_CUDA(cudaEventCreate(&e));
   double acc[3] = {0, 0, 0};
@@ -602,7 +740,8 @@ static void profile_impl(mss_sim &s, int64_t n, const double *w, T *traces, doub
   try {
     for (int64_t j = 0; j < n; ++j) {
       MSS_CUDA(cudaEventRecord(ev[0], st));
-      launch_cell<T, ST>(s, a, cur, st);
+      if (s.sched == MSS_SCHED_GRAPH_SPLIT) launch_split<T, ST>(s, a, sp, cur, st);
+      else launch_cell<T, ST>(s, a, cur, st);
       MSS_CUDA(cudaEventRecord(ev[1], st));
       k_face<T, ST><<<gf, kFaceThreads, s.face_smem, st>>>(a, cur, w + j, traces + j * (int64_t)s.n_rcv * s.n_src);
       MSS_CUDA(cudaEventRecord(ev[2], st));
@@ -841,6 +980,25 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
     }
   }
   s.cell_rows = srows;
+  {
+    // split cell phase: one item per (cell, matrix) and an F scratch block of m K rows per cell
+    std::vector<int2> fi, ai;
+    std::vector<int64_t> foff(R.n_cells);
+    int64_t frows = 0;
+    for (int c = 0; c < R.n_cells; ++c) {
+      foff[c] = frows;
+      frows += (int64_t)R.cell_m[c] * R.cell_K[c];
+      for (int k = 0; k < R.cell_m[c]; ++k) fi.push_back(make_int2(c, k));
+      for (int k = 1; k < R.cell_m[c]; ++k) ai.push_back(make_int2(c, k));
+    }
+    upload(s.d.flux_items, fi);
+    upload(s.d.accel_items, ai.empty() ? std::vector<int2>(1, make_int2(0, 1)) : ai);
+    upload(s.d.f_off, foff);
+    s.d.F.alloc((size_t)frows * S * es);
+    s.n_flux_items = (int)fi.size();
+    s.n_accel_items = (int)ai.size();
+    s.split_smem = (size_t)s.max_K * s.ST * es + 8 * (size_t)s.max_K;
+  }
   // streamed cell kernel: FP32 CUDA-core path with 16-source tiles and K_i <= 128; the same
   // matrices as coef, each row padded to Kq = K rounded up to 4 floats (16-byte rows)
   if (prec == MSS_FP32 && !s.tc && s.ST == kStreamST && s.max_K <= 128) {
@@ -930,6 +1088,8 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   }
   s.n_cfaces = (int)cfaces.size();
   s.corner_smem = std::max<size_t>(16, (size_t)s.max_nm * (s.ST + s.max_M) * es);
+  s.face_smem = std::max<size_t>(16, (2 * (size_t)s.max_M * s.ST + (size_t)s.max_M * s.max_M +
+                                      (s.corners ? (size_t)s.max_nm * s.max_M : 0)) * es);
   SimDev &d = s.d;
   upload(d.cell_K, R.cell_K);
   upload(d.cell_m, R.cell_m);
@@ -1085,7 +1245,7 @@ static void noalloc_impl(mss_step_buffers &b, int64_t n, const double *w, T *tra
   const size_t es = sizeof(T);
   const int tiles = (b.n_src + ST - 1) / ST;
   const size_t cell_smem = 2 * (size_t)b.max_m * b.max_K * ST * es + 8 * (size_t)b.max_K;
-  const size_t face_smem = std::max<size_t>(16, 2 * (size_t)b.max_M * ST * es);
+  const size_t face_smem = std::max<size_t>(16, (2 * (size_t)b.max_M * ST + (size_t)b.max_M * b.max_M) * es);
   int dev = 0, dev_smem = 0;
   MSS_CUDA(cudaGetDevice(&dev));
   MSS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -1145,6 +1305,8 @@ mss_status mss_step_noalloc(mss_step_buffers *b, int64_t n_steps, const double *
                     b->coef && b->minv && b->src_val && b->rcv_val && b->face_state[0] && b->face_state[1] &&
                     b->cell_state_buf[0] && b->cell_state_buf[1],
                 MSS_ERR_INVALID_ARG, "null pointer in mss_step_buffers");
+    for (const void *q : {b->face_state[0], b->face_state[1], b->cell_state_buf[0], b->cell_state_buf[1]})
+      MSS_REQUIRE(((uintptr_t)q & 15) == 0, MSS_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     const size_t es = b->precision == MSS_FP64 ? 8 : 4;
     const size_t need = (size_t)b->face_rows * 2 * (size_t)b->n_src * es;
     MSS_REQUIRE(need <= MSS_NOALLOC_SCRATCH_BYTES, MSS_ERR_INVALID_ARG,
@@ -1222,6 +1384,7 @@ static bool sched_allowed(const mss_sim &s, int sched) {
     case MSS_SCHED_GRAPH_STREAM: return s.stream_ok;
     case MSS_SCHED_PERSIST: return !s.tc;
     case MSS_SCHED_PERSIST_STREAM: return s.stream_ok;
+    case MSS_SCHED_GRAPH_SPLIT: return !s.tc && s.split_smem <= 48 * 1024;
     default: return false;
   }
 }

@@ -1,5 +1,5 @@
-"""Step schedules on the GPU: graph-captured kernels (plain or TMA-streamed cell kernel) and the
-persistent time-block kernel, against the oracle and against each other, plus the autotuner.
+"""Step schedules on the GPU: graph-captured kernels (plain, TMA-streamed or split cell phase) and
+the persistent time-block kernel, against the oracle and against each other, plus the autotuner.
 
 Every schedule runs the same per-item arithmetic in the same order (cell rows accumulate over
 the coefficient rows j = 0..K-1), so FP32 and FP64 traces are compared bit for bit across
@@ -94,7 +94,7 @@ def test_schedules_match_oracle_and_each_other(P, n_src, corners):
         outs = {}
         sim = _sim(P, topo, co, src, rcv, n_src, 4, tau, prec, cg)
         _, avail = sim.schedule()
-        assert avail[P.SCHED_GRAPH] and avail[P.SCHED_PERSIST]
+        assert avail[P.SCHED_GRAPH] and avail[P.SCHED_PERSIST] and avail[P.SCHED_GRAPH_SPLIT]
         assert bool(avail[P.SCHED_GRAPH_STREAM]) == (prec == P.FP32 and n_src >= 16)
         for k in range(P.SCHED_COUNT):
             if not avail[k]:
@@ -156,7 +156,7 @@ def test_streamed_kernel_full_launch_shape(P):
     ref = _oracle(topo, co, sub, rcv, 2, 8, w, tau, nst)
     sim = _sim(P, topo, co, src, rcv, 16, 8, tau, P.FP32)
     base = None
-    for k in (P.SCHED_GRAPH, P.SCHED_GRAPH_STREAM, P.SCHED_PERSIST_STREAM):
+    for k in (P.SCHED_GRAPH, P.SCHED_GRAPH_STREAM, P.SCHED_PERSIST_STREAM, P.SCHED_GRAPH_SPLIT):
         sim.reset()
         sim.set_schedule(k)
         out = _run(P, sim, w, nst, 16, 8, P.FP32)
