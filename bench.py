@@ -417,6 +417,90 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_many_sources(args):
+    """The 4096-cell, 256-source on-line shape of the 256^3 dipping-layer workload (synthetic SPD
+    coefficients, m_i in 3..6, uneven K_i): throughput of every precision, the CUDA-core FP32
+    schedule picked by the autotuner, per-kernel roofline of the cell phase.  One JSON line."""
+    import torch
+    import paper_1604_06750_gb300 as P
+    from paper_1604_06750_gb300 import build as B
+    B.build()
+    P.lib()
+    dev = torch.device("cuda", 0)
+    topo, co, src, rcv = synth.many_source_case(n_cells=(args.box,) * 3)
+    R = P.Rom.import_(topo, co)
+    R.set_io(256, src, 128, rcv)
+    del co
+    if args.profile:
+        prec = {"fp32": P.FP32, "fp32_tc": P.FP32_TC, "bf16_tc": P.BF16_TC}[args.prec]
+        sim = P.Sim(R, prec, 0.05)
+        if prec == P.FP32:
+            sim.set_schedule(args.sched)
+        w = torch.tensor(synth.ricker(np.arange(args.profile) * 0.05, 4.0), device=dev)
+        tr = torch.zeros((args.profile, 128, 256), device=dev, dtype=torch.float32)
+        sim.step(args.profile, w, tr, use_graph=False)
+        torch.cuda.synchronize()
+        sim.info()
+        print(json.dumps({"profile_steps": args.profile, "precision": args.prec, "box": args.box}))
+        return
+    Ks, ms = topo.cell_K(), topo.cell_m
+    nst, tau = args.many_steps, 0.05
+    w = torch.tensor(synth.ricker(np.arange(nst) * tau, 4.0), device=dev)
+    units = topo.n_cells * 256 * nst
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    algo_bytes, algo_flops = _kernel_model(None, Ks, ms, 256, 4)
+    flush = torch.empty(int(512e6) // 4, device=dev, dtype=torch.float32)
+    out = {"config": {"workload": "many_sources: %d cells (%d^3 box with walls, K_i 45..90), m_i 3..6, "
+                                  "256 sources, 128 receivers, synthetic SPD coefficients" % (topo.n_cells, args.box),
+                      "time_steps": nst},
+           "unit": UNIT, "precisions": {}}
+    clocks = Clocks(0)
+    clocks.start()
+    for name, prec in (("fp32", P.FP32), ("fp32_tc", P.FP32_TC), ("bf16_tc", P.BF16_TC), ("fp64", P.FP64)):
+        sim = P.Sim(R, prec, tau)
+        rec = {}
+        if prec == P.FP32:
+            k, msk = sim.autotune(20)
+            rec["schedule"] = SCHED_NAMES[k]
+            rec["autotune_ms_per_time_step"] = {SCHED_NAMES[i]: (float(msk[i]) if msk[i] >= 0 else None)
+                                                for i in range(len(SCHED_NAMES))}
+        tr = torch.zeros((nst, 128, 256), device=dev, dtype=torch.float64 if prec == P.FP64 else torch.float32)
+        sim.step(nst, w, tr)
+        times = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            sim.reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sim.step(nst, w, tr)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        sim.info()
+        t = statistics.mean(times)
+        rec.update({"value": units / t, "ms_per_time_step": 1e3 * t / nst})
+        cur, _ = sim.schedule()
+        if cur in (2, 3):
+            sim.set_schedule({2: 0, 3: 1}[cur])
+        sim.reset()
+        kms = sim.step_profile(min(nst, 50), w, tr)
+        es = 8 if prec == P.FP64 else 4
+        ab = _kernel_model(None, Ks, ms, 256, es)[0]
+        rec["cell_kernel_ms"] = kms[0]
+        rec["face_kernel_ms"] = kms[1]
+        rec["roofline"] = {"bound": "hbm", "achieved": ab / (kms[0] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": ab / (kms[0] / 1e3) / 1e9 / hbm, "algorithmic_bytes_per_launch": ab,
+                           "algorithmic_flops_per_launch": algo_flops}
+        out["precisions"][name] = rec
+        del sim, tr
+        torch.cuda.empty_cache()
+    out["clocks"] = clocks.stop()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,9 +508,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--profile", type=int, default=0, help="run N eager time steps after setup and exit")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32_tc"], help="precision of the --profile run")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32_tc", "bf16_tc"], help="precision of the --profile run")
     ap.add_argument("--sched", type=int, default=0, choices=[0, 1, 2, 3, 4], help="schedule of the --profile run")
+    ap.add_argument("--many-sources", action="store_true",
+                    help="measure the 4096-cell, 256-source launch shape instead (separate JSON line)")
+    ap.add_argument("--many-steps", type=int, default=200, help="time steps per timed run of --many-sources")
+    ap.add_argument("--box", type=int, default=16, help="cells per box edge of --many-sources")
     args = ap.parse_args()
+    if args.many_sources:
+        run_many_sources(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

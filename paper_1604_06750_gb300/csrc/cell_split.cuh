@@ -22,9 +22,10 @@ struct SplitArgs {
 
 template <typename T, int ST>
 __global__ void __launch_bounds__(kSplitThreads, 8) k_flux(const StepArgs<T> a, const SplitArgs<T> p, const int cur) {
-  const int2 it = p.flux_items[blockIdx.x];
+  const int tiles = (a.S + ST - 1) / ST;          // 1-D grid, tiles of an item adjacent
+  const int2 it = p.flux_items[blockIdx.x / tiles];
   const int cell = it.x, q = it.y;
-  const int s0 = blockIdx.y * ST;
+  const int s0 = (blockIdx.x % tiles) * ST;
   const int K = a.cell_K[cell], m = a.cell_m[cell];
   const int ns = min(ST, a.S - s0);
   const int S = a.S;
@@ -67,9 +68,10 @@ __global__ void __launch_bounds__(kSplitThreads, 8) k_flux(const StepArgs<T> a, 
 
 template <typename T, int ST>
 __global__ void __launch_bounds__(kSplitThreads, 8) k_accel(const StepArgs<T> a, const SplitArgs<T> p, const int cur) {
-  const int2 it = p.accel_items[blockIdx.x];
+  const int tiles = (a.S + ST - 1) / ST;
+  const int2 it = p.accel_items[blockIdx.x / tiles];
   const int cell = it.x, k = it.y;   // hidden layer k (0-based), k >= 1
-  const int s0 = blockIdx.y * ST;
+  const int s0 = (blockIdx.x % tiles) * ST;
   const int K = a.cell_K[cell];
   const int ns = min(ST, a.S - s0);
   const int S = a.S;

@@ -241,7 +241,8 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell_s(const StepArgs<float
   if (*(volatile const int *)t.err) return;
   stream_init(smem_s);
   unsigned gc = 0;
-  cell_stream_item(a, t, cur, blockIdx.x, blockIdx.y, smem_s, gc);
+  const int tiles = (a.S + kStreamST - 1) / kStreamST;   // 1-D grid, tiles of a cell adjacent
+  cell_stream_item(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_s, gc);
 }
 
 // Grid barrier for a cooperative launch.  bar[0] counts arrivals, bar[1] is the generation.
@@ -301,9 +302,9 @@ __global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 3 : 2) k_persis
   for (int step = 0; step < n_steps; ++step) {
     for (int it = blockIdx.x; it < n_cell_items; it += gridDim.x) {
       if constexpr (STREAM) {
-        if (!cell_stream_item(a, t, cur, it % a.n_cells, it / a.n_cells, smem_p, gc)) return;
+        if (!cell_stream_item(a, t, cur, it / tiles, it % tiles, smem_p, gc)) return;
       } else {
-        cell_item<T, ST>(a, cur, it % a.n_cells, it / a.n_cells, smem_p);
+        cell_item<T, ST>(a, cur, it / tiles, it % tiles, smem_p);
       }
       __syncthreads();
     }

@@ -125,10 +125,48 @@ __device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo
   *reinterpret_cast<__nv_bfloat16 *>(lo + off) = l;
 }
 
+// BF16 hi/lo split of a pair, packed as two 32-bit words (element 0 in the low half)
+__device__ __forceinline__ void split_pack2(float v0, float v1, uint32_t &hw, uint32_t &lw) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+  const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+  const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+  hw = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+  lw = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+}
+
+// Eight consecutive K-direction values (k0..k0+7, k0 % 8 == 0) of B row c, split into hi and lo:
+// one 16-byte core-matrix row each.
+__device__ __forceinline__ void store_core8(unsigned char *hi, unsigned char *lo, unsigned off, const float (&v)[8]) {
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split_pack2(v[2 * i], v[2 * i + 1], hw[i], lw[i]);
+  *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+// 8 x 8 transpose across each group of 8 consecutive lanes: on entry v[j] = M[lane % 8][j], on
+// return v[j] = M[j][lane % 8].  Three butterfly rounds; every lane of the warp must call it.
+__device__ __forceinline__ void transpose8(float (&v)[8], int lane) {
+#pragma unroll
+  for (int s = 1; s < 8; s <<= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if ((j & s) == 0) {
+        const float send = up ? v[j] : v[j + s];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, s);
+        if (up) v[j] = recv;
+        else v[j + s] = recv;
+      }
+    }
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float> a, const TcArgs t, const int cur) {
-  const int cell = blockIdx.x;
-  const int s0 = blockIdx.y * NT;
+  const int tiles = (a.S + NT - 1) / NT;           // 1-D grid, tiles of a cell adjacent (L2 reuse)
+  const int cell = blockIdx.x / tiles;
+  const int s0 = (blockIdx.x % tiles) * NT;
   const int K = a.cell_K[cell], m = a.cell_m[cell];
   const int Kp = t.Kp[cell], Kr = t.Kr[cell];
   const int S = a.S;
@@ -197,19 +235,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float>
     issued = 1;
     if (nmat > 1) { issue(1); issued = 2; }
   }
-  // stage B = U^{k+1} - U^k, k = 0..m-1 (U^0 = faces, U^m = 0), hi/lo, K-major core layout
-  for (int i = tid; i < m * Kp * NT; i += kTcThreads) {
-    const int k = i / (Kp * NT);
-    const int rem = i - k * Kp * NT;
-    const int r = rem / NT, c = rem - r * NT;
-    float v = 0.f;
-    if (r < K && c < ns) {
-      const float u0 = k == 0 ? fs[(rows[r] >> 1) * S + s0 + c] : cs[(so + (int64_t)(k - 1) * K + r) * S + s0 + c];
-      const float u1 = k + 1 < m ? cs[(so + (int64_t)k * K + r) * S + s0 + c] : 0.f;
-      v = u1 - u0;
+  // stage B = U^{k+1} - U^k, k = 0..m-1 (U^0 = faces, U^m = 0), hi/lo, K-major core layout:
+  // lanes run over sources (coalesced loads), each lane fills one 16-byte core row of 8 k values
+  {
+    constexpr int CPW = NT < 32 ? NT : 32;        // sources per warp pass
+    constexpr int RPW = 32 / CPW;                 // 8-row groups per warp pass
+    const int NR8 = Kp / 8, ngp = (NR8 + RPW - 1) / RPW, cblocks = NT / CPW;
+    const int cl = lane % CPW, sub = lane / CPW;
+    for (int tt = warp; tt < m * ngp * cblocks; tt += kTcThreads / 32) {
+      const int cb = tt % cblocks, t2 = tt / cblocks;
+      const int gp = t2 % ngp, k = t2 / ngp;
+      const int g8 = gp * RPW + sub, c = cb * CPW + cl;
+      if (g8 >= NR8) continue;
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = g8 * 8 + i;
+        float x = 0.f;
+        if (r < K && c < ns) {
+          const float u0 = k == 0 ? fs[(rows[r] >> 1) * S + s0 + c] : cs[(so + (int64_t)(k - 1) * K + r) * S + s0 + c];
+          const float u1 = k + 1 < m ? cs[(so + (int64_t)k * K + r) * S + s0 + c] : 0.f;
+          x = u1 - u0;
+        }
+        v[i] = x;
+      }
+      unsigned char *h = bb + (size_t)k * t.bbuf_bytes;
+      store_core8(h, h + NT * Kp * 2, core_off(c, g8 * 8, Kp), v);
     }
-    unsigned char *h = bb + (size_t)k * t.bbuf_bytes;
-    split_store(h, h + NT * Kp * 2, core_off(c, r, Kp), v);
   }
   fence_async_smem();
   __syncthreads();
@@ -262,22 +314,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float>
   // epilogue 1: publish F^1; E^k = F^k - F^{k-1} (k = 1..m-1) into B buffer k-1.
   // tcgen05.ld is warp-wide: the decision is made uniform over the CTA first.
   const bool go1 = __syncthreads_and(ok && !*abort_sm) != 0;
+  const bool vec_ok = (S % 4) == 0;
   if (go1) {
     for (int cc = 0; cc < NT / 2; cc += 8) {
       float prev[8], curv[8];
+      const bool full8 = vec_ok && (c0 + cc + 8 <= ns);
       for (int k = 0; k < m; ++k) {
         tc_ld8(tmem + lane_addr + (unsigned)(k * NT + c0 + cc), curv);
         if (k == 0) {
           if (r < K) {
+            float *o = a.flux + rows[r] * S + s0 + c0 + cc;
+            if (full8) {
+              reinterpret_cast<float4 *>(o)[0] = make_float4(curv[0], curv[1], curv[2], curv[3]);
+              reinterpret_cast<float4 *>(o)[1] = make_float4(curv[4], curv[5], curv[6], curv[7]);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (c0 + cc + j < ns) a.flux[rows[r] * S + s0 + c0 + cc + j] = curv[j];
+              for (int j = 0; j < 8; ++j)
+                if (c0 + cc + j < ns) o[j] = curv[j];
+            }
           }
-        } else if (r < Kp) {
-          unsigned char *h = bb + (size_t)(k - 1) * t.bbuf_bytes;
+        } else {
+          // E^k row r, 8 sources -> transpose in groups of 8 rows -> one core row per source
+          float e8[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            split_store(h, h + NT * Kp * 2, core_off(c0 + cc + j, r, Kp), r < K ? curv[j] - prev[j] : 0.f);
+          for (int j = 0; j < 8; ++j) e8[j] = r < K ? curv[j] - prev[j] : 0.f;
+          transpose8(e8, lane);
+          const int r0 = r & ~7;
+          if (r0 < Kp) {
+            unsigned char *h = bb + (size_t)(k - 1) * t.bbuf_bytes;
+            store_core8(h, h + NT * Kp * 2, core_off(c0 + cc + (lane & 7), r0, Kp), e8);
+          }
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) prev[j] = curv[j];
@@ -302,9 +368,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float>
         tc_ld8(tmem + lane_addr + (unsigned)((k - 1) * NT + c0 + cc), acc);
         if (r < K) {
           const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + c0 + cc;
+          if (vec_ok && c0 + cc + 8 <= ns) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (c0 + cc + j < ns) cso[base + j] = 2.f * cs[base + j] - cso[base + j] + tau2 * acc[j];
+            for (int h = 0; h < 2; ++h) {
+              const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
+              float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
+              od.x = 2.f * nw.x - od.x + tau2 * acc[4 * h + 0];
+              od.y = 2.f * nw.y - od.y + tau2 * acc[4 * h + 1];
+              od.z = 2.f * nw.z - od.z + tau2 * acc[4 * h + 2];
+              od.w = 2.f * nw.w - od.w + tau2 * acc[4 * h + 3];
+              *reinterpret_cast<float4 *>(cso + base + 4 * h) = od;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (c0 + cc + j < ns) cso[base + j] = 2.f * cs[base + j] - cso[base + j] + tau2 * acc[j];
+          }
         }
       }
     }

@@ -200,7 +200,9 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
 template <typename T, int ST>
 __global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 4 : 2) k_cell(const StepArgs<T> a, const int cur) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cell_item<T, ST>(a, cur, blockIdx.x, blockIdx.y, smem_raw);
+  // 1-D grid, source tiles of a cell adjacent so that they share its coefficients in L2
+  const int tiles = (a.S + ST - 1) / ST;
+  cell_item<T, ST>(a, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_raw);
 }
 
 // Item b of the face phase: b < n_faces is a face update, the rest are receiver blocks of
@@ -582,7 +584,7 @@ static void set_smem_attrs(const mss_sim &s) {
 
 template <int NT>
 static void launch_tc(const mss_sim &s, const StepArgs<float> &a, int cur, cudaStream_t st) {
-  const dim3 g(s.n_cells, (s.n_src + NT - 1) / NT);
+  const dim3 g(s.n_cells * ((s.n_src + NT - 1) / NT));
   k_cell_tc<NT><<<g, kTcThreads, s.tc_smem, st>>>(a, s.tca, cur);
 }
 
@@ -597,7 +599,7 @@ static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStr
       }
     }
   }
-  const dim3 gc(s.n_cells, s.tiles);
+  const dim3 gc(s.n_cells * s.tiles);
   if constexpr (std::is_same<T, float>::value && ST == kStreamST) {
     if (s.sched == MSS_SCHED_GRAPH_STREAM) {
       k_cell_s<<<gc, kCellThreads, s.stream_smem, st>>>(a, s.sca, cur);
@@ -619,9 +621,9 @@ static SplitArgs<T> make_split(const mss_sim &s) {
 
 template <typename T, int ST>
 static void launch_split(const mss_sim &s, const StepArgs<T> &a, const SplitArgs<T> &p, int cur, cudaStream_t st) {
-  k_flux<T, ST><<<dim3(s.n_flux_items, s.tiles), kSplitThreads, s.split_smem, st>>>(a, p, cur);
+  k_flux<T, ST><<<dim3(s.n_flux_items * s.tiles), kSplitThreads, s.split_smem, st>>>(a, p, cur);
   if (s.n_accel_items > 0)
-    k_accel<T, ST><<<dim3(s.n_accel_items, s.tiles), kSplitThreads, s.split_smem, st>>>(a, p, cur);
+    k_accel<T, ST><<<dim3(s.n_accel_items * s.tiles), kSplitThreads, s.split_smem, st>>>(a, p, cur);
 }
 
 // Shared memory of the persistent kernel: the largest of its phases.
@@ -1254,7 +1256,7 @@ static void noalloc_impl(mss_step_buffers &b, int64_t n, const double *w, T *tra
   MSS_CUDA(cudaFuncSetAttribute(k_face<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem));
   const int per = kFaceThreads / ST;
   const int rcv_blocks = (b.n_rcv + per - 1) / per;
-  const dim3 gc(b.n_cells, tiles), gf(b.n_faces + rcv_blocks, tiles);
+  const dim3 gc(b.n_cells * tiles), gf(b.n_faces + rcv_blocks, tiles);
   int cur = b.cur & 1;
   for (int64_t j = 0; j < n; ++j) {
     k_cell<T, ST><<<gc, kCellThreads, cell_smem, st>>>(a, cur);

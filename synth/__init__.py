@@ -396,6 +396,25 @@ def random_io(topo: RomTopology, n_src: int, n_rcv: int, seed: int = 0, density:
     return src, rcv
 
 
+def many_source_case(n_cells: Sequence[int] = (16, 16, 16), modes: int = 15, m_range: Tuple[int, int] = (3, 6),
+                     n_src: int = 256, n_rcv: int = 128, seed_index: int = 3):
+    """Synthetic coupled ROM of the shape of the 256^3 dipping-layer workload's on-line stage.
+
+    A box of 16^3 cells with walls (so wall cells have 3..5 faces and uneven K_i), ``modes``
+    modes per interior face, layer counts m_i drawn uniformly in ``m_range``, random SPD
+    coefficients with eigenvalues in [1/2, 1], ``n_src`` sources each projected on ~0.1% of
+    the faces and ``n_rcv`` receivers on two faces each.  Returns (topology, coefficients,
+    source entries, receiver entries).
+    """
+    rng = np.random.default_rng(SEED_BASE + 500 + seed_index)
+    nc = int(np.prod(n_cells))
+    ms = rng.integers(m_range[0], m_range[1] + 1, nc)
+    topo = box_topology(n_cells, modes=modes, m=ms, seed=seed_index)
+    co = random_coefficients(topo, seed=seed_index, spread=2.0)
+    src, rcv = random_io(topo, n_src, n_rcv, seed=seed_index, density=0.001)
+    return topo, co, src, rcv
+
+
 def random_state(topo: RomTopology, n_src: int, seed: int = 0):
     """Random face and interior states (two time levels), for energy and resume tests."""
     rng = np.random.default_rng(SEED_BASE + 400 + seed)
