@@ -264,7 +264,8 @@ mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_
  *                    CUDA graph when use_graph is set;
  *   GRAPH_STREAM     as GRAPH with the streamed FP32 cell kernel: each cell's coefficient stream
  *                    staged into shared memory by 1-D TMA bulk copies through a 4-slot ring
- *                    (FP32, 16-source tiles, K_i <= 128);
+ *                    (FP32, 16-source tiles, K_i <= 128; 256 or 512 threads, the autotuner
+ *                    picks; 512 by default);
  *   PERSIST          one cooperative persistent kernel per block of up to 512 steps, phases
  *                    separated by a grid barrier with a 1 s time limit (CUDA-core precisions);
  *   PERSIST_STREAM   PERSIST with the streamed cell body;

@@ -50,10 +50,14 @@ __device__ __forceinline__ void stream_drain(const uint64_t *full, unsigned gc_c
   __syncthreads();
 }
 
-// Streamed cell item.  gc: chunks this CTA has consumed so far (slot and parity bookkeeping that
-// persists across items); returns false if a wait timed out (error recorded, copies drained).
+// Streamed cell item, for 128 G threads (G column groups of 16 / G sources).  gc: chunks this
+// CTA has consumed so far (slot and parity bookkeeping that persists across items); returns false
+// if a wait timed out (error recorded, copies drained).
+template <int G>
 __device__ bool cell_stream_item(const StepArgs<float> &a, const StreamArgs &t, const int cur, const int cell,
                                  const int tile, unsigned char *smem, unsigned &gc) {
+  static_assert(G == 1 || G == 2 || G == 4, "16 sources split into 1, 2 or 4 column groups");
+  constexpr int CP = kStreamST / G;   // sources per thread
   constexpr int ST = kStreamST;
   const int s0 = tile * ST;
   const int K = a.cell_K[cell], m = a.cell_m[cell], Kq = t.Kq[cell];
@@ -115,8 +119,8 @@ __device__ bool cell_stream_item(const StepArgs<float> &a, const StreamArgs &t, 
     D[i] = (k + 1 < m ? X[i + (size_t)K * ST] : 0.f) - X[i];
   }
   __syncthreads();
-  const int r = tid & 127, g = tid >> 7;          // row, column half
-  const bool act = r < K && g < 2;
+  const int r = tid & 127, g = tid >> 7;          // row, column group
+  const bool act = r < K && g < G;
   const float tau2 = a.tau2;
   auto fail = [&](int c) {
     if (tid == 0) atomicExch(t.err, 1);
@@ -150,9 +154,9 @@ __device__ bool cell_stream_item(const StepArgs<float> &a, const StreamArgs &t, 
       __syncthreads();
     }
     const int layer = q < m ? q : q - m + 1;
-    float acc[8];
+    float acc[CP];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+    for (int e = 0; e < CP; ++e) acc[e] = 0.f;
     for (int j0 = 0; j0 < K;) {
       const int fr = q * K + j0;
       if (fr >= (c + 1) * CR) {
@@ -169,20 +173,19 @@ __device__ bool cell_stream_item(const StepArgs<float> &a, const StreamArgs &t, 
       if (act) {
         const float *sp = reinterpret_cast<const float *>(ring + (size_t)((gc0 + c) % kStreamSlots) * kStreamChunk) +
                           (size_t)(fr - c * CR) * Kq + r;
-        const float4 *dp = reinterpret_cast<const float4 *>(D + ((size_t)layer * K + j0) * ST) + 2 * g;
+        const float4 *dp = reinterpret_cast<const float4 *>(D + ((size_t)layer * K + j0) * ST) + (CP / 4) * g;
         const int n = j1 - j0;
 #pragma unroll 4
         for (int i = 0; i < n; ++i) {
           const float gv = sp[(size_t)i * Kq];
-          const float4 d0 = dp[4 * i], d1 = dp[4 * i + 1];
-          acc[0] += gv * d0.x;
-          acc[1] += gv * d0.y;
-          acc[2] += gv * d0.z;
-          acc[3] += gv * d0.w;
-          acc[4] += gv * d1.x;
-          acc[5] += gv * d1.y;
-          acc[6] += gv * d1.z;
-          acc[7] += gv * d1.w;
+#pragma unroll
+          for (int h = 0; h < CP / 4; ++h) {
+            const float4 d = dp[4 * i + h];
+            acc[4 * h + 0] += gv * d.x;
+            acc[4 * h + 1] += gv * d.y;
+            acc[4 * h + 2] += gv * d.z;
+            acc[4 * h + 3] += gv * d.w;
+          }
         }
       }
       j0 = j1;
@@ -190,15 +193,16 @@ __device__ bool cell_stream_item(const StepArgs<float> &a, const StreamArgs &t, 
     // end of matrix q: row r of F^{q+1}, or leapfrog of U^k with Gamma-hat^k E^k
     if (act) {
       if (q < m) {
-        float4 *o = reinterpret_cast<float4 *>(X + ((size_t)q * K + r) * ST + 8 * g);
-        o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        o[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        float4 *o = reinterpret_cast<float4 *>(X + ((size_t)q * K + r) * ST + CP * g);
+#pragma unroll
+        for (int h = 0; h < CP / 4; ++h)
+          o[h] = make_float4(acc[4 * h], acc[4 * h + 1], acc[4 * h + 2], acc[4 * h + 3]);
       } else {
         const int k = q - m + 1;
-        const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + 8 * g;
+        const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + CP * g;
         if (vec) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < CP / 4; ++h) {
             const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
             float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
             od.x = 2.f * nw.x - od.x + tau2 * acc[4 * h + 0];
@@ -209,8 +213,8 @@ __device__ bool cell_stream_item(const StepArgs<float> &a, const StreamArgs &t, 
           }
         } else {
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            if (8 * g + e < ns) cso[base + e] = 2.f * cs[base + e] - cso[base + e] + tau2 * acc[e];
+          for (int e = 0; e < CP; ++e)
+            if (CP * g + e < ns) cso[base + e] = 2.f * cs[base + e] - cso[base + e] + tau2 * acc[e];
         }
       }
     }
@@ -236,13 +240,15 @@ __device__ __forceinline__ void stream_init(unsigned char *smem) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kCellThreads, 2) k_cell_s(const StepArgs<float> a, const StreamArgs t, const int cur) {
+template <int G>
+__global__ void __launch_bounds__(128 * G, G == 4 ? 1 : 2) k_cell_s(const StepArgs<float> a, const StreamArgs t,
+                                                                     const int cur) {
   extern __shared__ __align__(128) unsigned char smem_s[];
   if (*(volatile const int *)t.err) return;
   stream_init(smem_s);
   unsigned gc = 0;
   const int tiles = (a.S + kStreamST - 1) / kStreamST;   // 1-D grid, tiles of a cell adjacent
-  cell_stream_item(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_s, gc);
+  cell_stream_item<G>(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_s, gc);
 }
 
 // Grid barrier for a cooperative launch.  bar[0] counts arrivals, bar[1] is the generation.
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 3 : 2) k_persis
   for (int step = 0; step < n_steps; ++step) {
     for (int it = blockIdx.x; it < n_cell_items; it += gridDim.x) {
       if constexpr (STREAM) {
-        if (!cell_stream_item(a, t, cur, it / tiles, it % tiles, smem_p, gc)) return;
+        if (!cell_stream_item<kCellThreads / 128>(a, t, cur, it / tiles, it % tiles, smem_p, gc)) return;
       } else {
         cell_item<T, ST>(a, cur, it / tiles, it % tiles, smem_p);
       }

@@ -49,8 +49,12 @@ struct StepArgs {
   // faces that carry members (cfaces)
   const int32_t *fm_ptr, *fm_member, *mem_group, *mem_face, *grp_ptr, *cfaces;
   const int64_t *mem_row;
+  // per face, its members' rows of S_f laid out contiguously (fm_rows from fm_roff[f]), and per
+  // member entry (member, first and past-last member of its group): one load, no index chains
+  const int64_t *fm_roff;
+  const int4 *fm_info;
   // values
-  const T *coef, *minv, *src_val, *rcv_val, *cg_rows, *cg_w;
+  const T *coef, *minv, *src_val, *rcv_val, *cg_rows, *cg_w, *fm_rows;
   T *fstate0, *fstate1, *cstate0, *cstate1, *flux, *uhat;
   int S, n_cells, n_faces, n_rcv, corners, n_cfaces;
   T tau2;
@@ -238,12 +242,9 @@ __device__ __forceinline__ void face_item(const StepArgs<T> &a, const int cur, c
     }
     const T *Mi = a.minv + a.face_minv[f];
     for (int i = threadIdx.x; i < M * M; i += blockDim.x) mi[i] = Mi[i];
-    {
-      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-      for (int j = threadIdx.x >> 5; j < nm; j += nw) {
-        const T *src = a.cg_rows + a.mem_row[a.fm_member[j0 + j]];
-        for (int c = lane; c < M; c += 32) rw[j * M + c] = src[c];
-      }
+    if (nm > 0) {
+      const T *src = a.fm_rows + a.fm_roff[f];
+      for (int i = threadIdx.x; i < nm * M; i += blockDim.x) rw[i] = src[i];
     }
     __syncthreads();
     T *dst = cur ? a.fstate0 : a.fstate1;        // the old level becomes the new one
@@ -362,11 +363,8 @@ __device__ __forceinline__ void corner_item(const StepArgs<T> &a, const int cur,
   T *delta = reinterpret_cast<T *>(smem_raw);   // nm x ST
   T *rowsm = delta + (size_t)nm * ST;           // nm x M member rows of S_f
   {
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int j = threadIdx.x >> 5; j < nm; j += nw) {
-      const T *src = a.cg_rows + a.mem_row[a.fm_member[j0 + j]];
-      for (int c = lane; c < M; c += 32) rowsm[j * M + c] = src[c];
-    }
+    const T *src = a.fm_rows + a.fm_roff[f];
+    for (int i = threadIdx.x; i < nm * M; i += blockDim.x) rowsm[i] = src[i];
   }
   using V = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n;
@@ -375,13 +373,13 @@ __device__ __forceinline__ void corner_item(const StepArgs<T> &a, const int cur,
     // same products in the same order as the scalar loops below, VN sources per thread
     for (int i = threadIdx.x; i < nm * NV; i += blockDim.x) {
       const int j = i / NV, v = i - j * NV;
-      const int l = a.fm_member[j0 + j];
-      const int g = a.mem_group[l];
+      const int4 info = a.fm_info[j0 + j];
+      const int l = info.x;
       T mean[VN];
 #pragma unroll
       for (int e = 0; e < VN; ++e) mean[e] = T(0);
 #pragma unroll 4
-      for (int l2 = a.grp_ptr[g]; l2 < a.grp_ptr[g + 1]; ++l2) {
+      for (int l2 = info.y; l2 < info.z; ++l2) {
         const T wv = a.cg_w[l2];
         const V x = *reinterpret_cast<const V *>(a.uhat + (int64_t)l2 * S + s0 + v * VN);
         const T *xe = reinterpret_cast<const T *>(&x);
@@ -421,11 +419,11 @@ __device__ __forceinline__ void corner_item(const StepArgs<T> &a, const int cur,
     const int j = i / ST, s = i - j * ST;
     T d = T(0);
     if (s < ns) {
-      const int l = a.fm_member[j0 + j];
-      const int g = a.mem_group[l];
+      const int4 info = a.fm_info[j0 + j];
+      const int l = info.x;
       T mean = T(0);
 #pragma unroll 4
-      for (int l2 = a.grp_ptr[g]; l2 < a.grp_ptr[g + 1]; ++l2) mean += a.cg_w[l2] * a.uhat[(int64_t)l2 * S + s0 + s];
+      for (int l2 = info.y; l2 < info.z; ++l2) mean += a.cg_w[l2] * a.uhat[(int64_t)l2 * S + s0 + s];
       d = mean - a.uhat[(int64_t)l * S + s0 + s];
     }
     delta[i] = d;
@@ -459,7 +457,7 @@ struct SimDev {
   DevMem cell_K, cell_m, cell_coef, cell_ghat, cell_state, cell_row, row_face_row, row_side;
   DevMem face_M, face_two, face_row, face_minv, fsrc_ptr, fsrc_index, fsrc_val;
   DevMem rcv_ptr, rcv_face, rcv_off;
-  DevMem fm_ptr, fm_member, mem_group, mem_face, grp_ptr, mem_row;
+  DevMem fm_ptr, fm_member, mem_group, mem_face, grp_ptr, mem_row, fm_roff, fm_info, fm_rows;
   DevMem coef, minv, src_val, rcv_val, cg_rows, cg_w;
   DevMem fstate[2], cstate[2], flux, uhat, cfaces, wbuf, tbuf;
   DevMem tc_blob, tc_off, tc_Kp, tc_Kr, tc_err;
@@ -470,9 +468,9 @@ struct SimDev {
 struct GraphKey {
   int64_t n;
   const void *w, *t;
-  int cur, sched;
+  int cur, sched, variant;
   bool operator<(const GraphKey &o) const {
-    return std::tie(n, w, t, cur, sched) < std::tie(o.n, o.w, o.t, o.cur, o.sched);
+    return std::tie(n, w, t, cur, sched, variant) < std::tie(o.n, o.w, o.t, o.cur, o.sched, o.variant);
   }
 };
 
@@ -494,6 +492,7 @@ struct mss_sim {
   // or the persistent time-block kernel with either cell body)
   int sched = MSS_SCHED_GRAPH;
   bool stream_ok = false;
+  int stream_groups = 4;             // column groups (128 threads each) of the streamed cell kernel
   size_t stream_smem = 0;
   mss::StreamArgs sca{};
   int persist_block = 512;           // steps per persistent launch
@@ -543,6 +542,9 @@ static StepArgs<T> make_args(const mss_sim &s) {
   a.mem_face = d.mem_face.as<int32_t>();
   a.grp_ptr = d.grp_ptr.as<int32_t>();
   a.mem_row = d.mem_row.as<int64_t>();
+  a.fm_roff = d.fm_roff.as<int64_t>();
+  a.fm_info = d.fm_info.as<int4>();
+  a.fm_rows = d.fm_rows.as<T>();
   a.coef = d.coef.as<T>();
   a.minv = d.minv.as<T>();
   a.src_val = d.src_val.as<T>();
@@ -575,7 +577,10 @@ static void set_smem_attrs(const mss_sim &s) {
   }
   MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
   if (s.stream_ok)
-    MSS_CUDA(cudaFuncSetAttribute(k_cell_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.stream_smem));
+  {
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_s<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.stream_smem));
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_s<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.stream_smem));
+  }
   MSS_CUDA(cudaFuncSetAttribute(k_flux<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.split_smem));
   MSS_CUDA(cudaFuncSetAttribute(k_accel<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.split_smem));
   MSS_CUDA(cudaFuncSetAttribute(k_face<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.face_smem));
@@ -602,7 +607,8 @@ static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStr
   const dim3 gc(s.n_cells * s.tiles);
   if constexpr (std::is_same<T, float>::value && ST == kStreamST) {
     if (s.sched == MSS_SCHED_GRAPH_STREAM) {
-      k_cell_s<<<gc, kCellThreads, s.stream_smem, st>>>(a, s.sca, cur);
+      if (s.stream_groups == 4) k_cell_s<4><<<gc, 512, s.stream_smem, st>>>(a, s.sca, cur);
+      else k_cell_s<2><<<gc, 256, s.stream_smem, st>>>(a, s.sca, cur);
       return;
     }
   }
@@ -700,7 +706,7 @@ static void step_impl(mss_sim &s, int64_t n, const double *w, void *traces, int 
     // capture and replay on the sim's own stream (the legacy stream cannot be captured)
     MSS_CUDA(cudaEventRecord(s.ev_in, st));
     MSS_CUDA(cudaStreamWaitEvent(s.cap, s.ev_in, 0));
-    GraphKey key{n, w, traces, s.cur, s.sched};
+    GraphKey key{n, w, traces, s.cur, s.sched, s.stream_groups};
     auto it = s.graphs.find(key);
     if (it == s.graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -1066,7 +1072,9 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   }
   // corner groups
   std::vector<int32_t> fm_ptr(R.n_faces + 1, 0), fm_member, mem_group, mem_face, grp_ptr, cfaces;
-  std::vector<int64_t> mem_row;
+  std::vector<int64_t> mem_row, fm_roff;
+  std::vector<int4> fm_info;
+  std::vector<double> fm_rows;
   if (s.corners) {
     const int G = (int)R.cg_ptr.size() - 1;
     grp_ptr = R.cg_ptr;
@@ -1086,6 +1094,16 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
       fm_ptr[f + 1] = (int32_t)fm_member.size();
       s.max_nm = std::max<int>(s.max_nm, (int)per[f].size());
       if (!per[f].empty()) cfaces.push_back(f);
+    }
+    fm_roff.assign(R.n_faces + 1, 0);
+    for (int f = 0; f < R.n_faces; ++f) {
+      for (int32_t l : per[f]) {
+        const double *row = R.cg_rows.data() + mem_row[l];
+        fm_rows.insert(fm_rows.end(), row, row + R.face_M[f]);
+        const int g = mem_group[l];
+        fm_info.push_back(make_int4(l, R.cg_ptr[g], R.cg_ptr[g + 1], 0));
+      }
+      fm_roff[f + 1] = (int64_t)fm_rows.size();
     }
   }
   s.n_cfaces = (int)cfaces.size();
@@ -1117,6 +1135,8 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   upload(d.mem_face, mem_face);
   upload(d.grp_ptr, grp_ptr);
   upload(d.mem_row, mem_row);
+  upload(d.fm_roff, fm_roff);
+  upload(d.fm_info, fm_info);
   upload(d.cfaces, cfaces);
   auto up = [&](DevMem &m, const std::vector<double> &v) {
     if (prec == MSS_FP64) upload_as<double>(m, v);
@@ -1128,6 +1148,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   up(d.rcv_val, R.rcv_vals);
   up(d.cg_rows, s.corners ? R.cg_rows : std::vector<double>());
   up(d.cg_w, s.corners ? R.cg_weight : std::vector<double>());
+  up(d.fm_rows, fm_rows);
   for (int l = 0; l < 2; ++l) {
     d.fstate[l].alloc((size_t)s.face_rows * S * es);
     d.cstate[l].alloc((size_t)std::max<int64_t>(1, s.cell_rows) * S * es);
@@ -1140,7 +1161,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
                     &d.row_side, &d.face_M, &d.face_two, &d.face_row, &d.face_minv, &d.fsrc_ptr, &d.fsrc_index,
                     &d.fsrc_val, &d.rcv_ptr, &d.rcv_face, &d.rcv_off, &d.fm_ptr, &d.fm_member, &d.mem_group,
                     &d.mem_face, &d.grp_ptr, &d.mem_row, &d.coef, &d.minv, &d.src_val, &d.rcv_val, &d.cg_rows,
-                    &d.cg_w, &d.fstate[0], &d.fstate[1], &d.cstate[0], &d.cstate[1], &d.flux, &d.uhat, &d.cfaces})
+                    &d.cg_w, &d.fm_rows, &d.fm_roff, &d.fm_info, &d.fstate[0], &d.fstate[1], &d.cstate[0], &d.cstate[1], &d.flux, &d.uhat, &d.cfaces})
     bytes += (int64_t)m->bytes;
   s.dev_bytes = bytes;
 }
@@ -1440,32 +1461,41 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
       s->steps = steps0;
     };
     try {
+      int best_groups = s->stream_groups;
       for (int k = 0; k < MSS_SCHED_COUNT; ++k) {
         if (ms) ms[k] = -1.0;
         if (!sched_allowed(*s, k)) continue;
         s->sched = k;
-        auto run = [&]() {
-          if (s->prec == MSS_FP64) step_dispatch<double>(*s, n, w.as<double>(), tr.p, 1, st);
-          else step_dispatch<float>(*s, n, w.as<double>(), tr.p, 1, st);
-        };
-        run();   // warm-up (and graph capture)
-        MSS_CUDA(cudaEventRecord(e0, st));
-        run();
-        MSS_CUDA(cudaEventRecord(e1, st));
-        MSS_CUDA(cudaEventSynchronize(e1));
-        float t = 0;
-        MSS_CUDA(cudaEventElapsedTime(&t, e0, e1));
-        int err = 0;
-        MSS_CUDA(cudaMemcpy(&err, s->d.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-        MSS_REQUIRE(err == 0, MSS_ERR_TIMEOUT, "a bounded wait gave up during autotuning");
-        const double per = t / (double)n;
-        if (ms) ms[k] = per;
-        if (per < best) {
-          best = per;
-          best_k = k;
+        // the streamed cell kernel also has a block-size variant (2 or 4 column groups)
+        const bool streamed = k == MSS_SCHED_GRAPH_STREAM;
+        for (int gv : {4, 2}) {
+          if (!streamed && gv != 4) continue;
+          if (streamed) s->stream_groups = gv;
+          auto run = [&]() {
+            if (s->prec == MSS_FP64) step_dispatch<double>(*s, n, w.as<double>(), tr.p, 1, st);
+            else step_dispatch<float>(*s, n, w.as<double>(), tr.p, 1, st);
+          };
+          run();   // warm-up (and graph capture)
+          MSS_CUDA(cudaEventRecord(e0, st));
+          run();
+          MSS_CUDA(cudaEventRecord(e1, st));
+          MSS_CUDA(cudaEventSynchronize(e1));
+          float t = 0;
+          MSS_CUDA(cudaEventElapsedTime(&t, e0, e1));
+          int err = 0;
+          MSS_CUDA(cudaMemcpy(&err, s->d.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+          MSS_REQUIRE(err == 0, MSS_ERR_TIMEOUT, "a bounded wait gave up during autotuning");
+          const double per = t / (double)n;
+          if (ms && (ms[k] < 0 || per < ms[k])) ms[k] = per;
+          if (per < best) {
+            best = per;
+            best_k = k;
+            if (streamed) best_groups = gv;
+          }
+          restore();
         }
-        restore();
       }
+      s->stream_groups = best_groups;
     } catch (...) {
       restore();
       s->sched = sched0;
