@@ -311,6 +311,7 @@ def run_native(args):
                  "other_kernels_ms": {"k_face": ms[1], "k_corner": ms[2]}})
     # ---- tensor-core cell products (split BF16, FP32 accumulation), same coefficients
     simtc = P.Sim(LR, P.FP32_TC, tau, corner_correction=True)
+    tc_sched, tc_ms = simtc.autotune(200)
     trtc = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
     for _ in range(2):
         simtc.reset()
@@ -401,8 +402,8 @@ def run_native(args):
                                                        for k in range(len(SCHED_NAMES))}},
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "fp64": {"value": units / t64, "unit": UNIT, "ms": 1e3 * t64},
-            "fp32_tc": {"value": units / ttc, "unit": UNIT, "ms": 1e3 * ttc,
-                        "kernel_ms": {"k_cell_tc": ms_tc[0], "k_face": ms_tc[1], "k_corner": ms_tc[2]},
+            "fp32_tc": {"value": units / ttc, "unit": UNIT, "ms": 1e3 * ttc, "schedule": SCHED_NAMES[tc_sched],
+                        "kernel_ms": {"cell_phase": ms_tc[0], "k_face": ms_tc[1], "k_corner": ms_tc[2]},
                         "rel_l2_vs_fp64": rel(trtc_np, ref64),
                         "note": "tcgen05 cell products, BF16 hi/lo split operands (3 products), FP32 accumulation"},
             "fine_grid": {"value": units / tfine, "unit": UNIT, "ms": 1e3 * tfine,
@@ -461,7 +462,7 @@ def run_many_sources(args):
     for name, prec in (("fp32", P.FP32), ("fp32_tc", P.FP32_TC), ("bf16_tc", P.BF16_TC), ("fp64", P.FP64)):
         sim = P.Sim(R, prec, tau)
         rec = {}
-        if prec == P.FP32:
+        if True:
             k, msk = sim.autotune(20)
             rec["schedule"] = SCHED_NAMES[k]
             rec["autotune_ms_per_time_step"] = {SCHED_NAMES[i]: (float(msk[i]) if msk[i] >= 0 else None)
@@ -485,6 +486,7 @@ def run_many_sources(args):
         cur, _ = sim.schedule()
         if cur in (2, 3):
             sim.set_schedule({2: 0, 3: 1}[cur])
+        rec["profiled_schedule"] = SCHED_NAMES[sim.schedule()[0]]
         sim.reset()
         kms = sim.step_profile(min(nst, 50), w, tr)
         es = 8 if prec == P.FP64 else 4
@@ -501,6 +503,134 @@ def run_many_sources(args):
     print(json.dumps(out))
 
 
+def run_surrogate(args):
+    """Learned-surrogate off-line stage beside the exact one on the 3D layered workload.
+
+    Training cells: 16^3 cells of 64^3 media from the same layered recipe (other random-field
+    seeds), labelled by the exact off-line stage; the network (4 stride/plain 3x3x3 conv layers
+    of 32 channels, dense head) is trained by the library's own kernels.  The 512-cell 128^3
+    workload's ROM is then built from a skeleton by inference + transfer-function screen +
+    exact fallback at several screen tolerances and stepped (FP32, corners) against the exact
+    ROM and the fine grid.  One JSON line."""
+    import torch
+    import paper_1604_06750_gb300 as P
+    from paper_1604_06750_gb300 import build as B
+    B.build()
+    P.lib()
+    dev = torch.device("cuda", 0)
+    wl = _workload()
+    m, nm = wl.m, wl.n_modes
+    s = -(2 * math.pi * wl.f_max) ** 2
+    io_slots = 8
+    Kp = 6 * nm + io_slots
+    D = (2 * m - 1) * Kp * (Kp + 1) // 2
+    # ---- training data: exact ROMs of the training media
+    t0 = time.perf_counter()
+    xs, fs, ts, ms_ = [], [], [], []
+    build_s = 0.0
+    for k in range(args.train_media):
+        tw = synth.workload_3d_layers(64, 16, m=m, n_modes=nm, n_src=4, n_steps=10, seed_index=100 + k)
+        L = P.Operator(tw.grid, tw.sigma, tw.rho)
+        LP = P.Partition(L, tw.cell, np.concatenate([tw.src_nodes, tw.rcv_nodes]).astype(np.int32))
+        cells = np.arange(int(LP.info()[0]))
+        tb = time.perf_counter()
+        LR = P.Rom.build(LP, m, nm, s, cg_tol=1e-12)
+        torch.cuda.synchronize()
+        build_s += time.perf_counter() - tb
+        t, mk = LR.pack(cells, nm, io_slots, m)
+        x, f = LP.cell_inputs(cells, nm, io_slots)
+        xs.append(x)
+        fs.append(f)
+        ts.append(t)
+        ms_.append(mk)
+    T = np.concatenate(ts)
+    MK = np.concatenate(ms_)
+    X = torch.from_numpy(np.concatenate(xs)).to(dev)
+    Fe = torch.from_numpy(np.concatenate(fs)).to(dev)
+    Td = torch.from_numpy(T.astype(np.float32)).to(dev)
+    Md = torch.from_numpy(MK).to(dev)
+    t_data = time.perf_counter() - t0
+    sur = P.Surrogate(16, 7, D, channels=32, hidden=128, seed=1)
+    sur.fit_output_transform(T, MK)
+    loss = torch.zeros(1, device=dev)
+    g = torch.Generator().manual_seed(0)
+    n = X.shape[0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    first = None
+    for it in range(args.train_iters):
+        idx = torch.randint(0, n, (args.batch,), generator=g).to(dev)
+        lr = 2e-3 if it < args.train_iters * 2 // 3 else 5e-4
+        sur.train_step(X[idx].contiguous(), Fe[idx].contiguous(), Td[idx].contiguous(), lr, loss=loss,
+                       mask=Md[idx].contiguous())
+        if it == 0:
+            torch.cuda.synchronize()
+            first = float(loss.item())
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    last = float(loss.item())
+    # ---- the workload: exact ROM, fine grid
+    L = P.Operator(wl.grid, wl.sigma, wl.rho)
+    LP = P.Partition(L, wl.cell, np.concatenate([wl.src_nodes, wl.rcv_nodes]).astype(np.int32))
+    lam = L.lambda_max(1e-7)
+    tau = wl.cfl_fraction * 2.0 / math.sqrt(lam)
+    cells = np.arange(int(LP.info()[0]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    LR = P.Rom.build(LP, m, nm, s, cg_tol=1e-12)
+    torch.cuda.synchronize()
+    t_exact = time.perf_counter() - t0
+    LR.set_io_nodes(LP, wl.src_nodes, wl.rcv_nodes)
+    nst, S, R = wl.n_steps, len(wl.src_nodes), len(wl.rcv_nodes)
+    w = torch.tensor(synth.ricker(np.arange(nst) * tau, wl.f_peak), device=dev)
+
+    def traces(rom):
+        sim = P.Sim(rom, P.FP32, tau, corner_correction=True)
+        tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+        sim.step(nst, w, tr)
+        torch.cuda.synchronize()
+        sim.info()
+        return tr.double().cpu().numpy()
+
+    ref = traces(LR)
+    fine = P.FineSim(L, P.FP32, tau, wl.src_nodes, wl.rcv_nodes)
+    trf = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+    fine.step(nst, w, trf)
+    torch.cuda.synchronize()
+    fine_tr = trf.double().cpu().numpy()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    runs = []
+    for tol in (1e-3, 1e-2, 5e-2, 1e300):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        SK = P.Rom.skeleton(LP, m, nm, s, cg_tol=1e-12)
+        err, fb = sur.infer(SK, cells, nm, io_slots, tol)
+        torch.cuda.synchronize()
+        t_sur = time.perf_counter() - t0
+        SK.set_io_nodes(LP, wl.src_nodes, wl.rcv_nodes)
+        try:
+            tr = traces(SK)
+            e_rom, e_fine = rel(tr, ref), rel(tr, fine_tr)
+        except P.MssError as ex:          # a surrogate ROM may fail the sim's checks
+            e_rom = e_fine = None
+            tr = None
+        runs.append({"screen_tol": None if tol > 1 else tol, "offline_s": t_sur, "fallback_cells": int(fb.sum()),
+                     "screen_err_median": float(np.median(err)), "screen_err_p10": float(np.percentile(err, 10)),
+                     "screen_err_p90": float(np.percentile(err, 90)),
+                     "receiver_rel_l2_vs_exact_rom": e_rom, "receiver_rel_l2_vs_fine": e_fine})
+    out = {"mode": "surrogate", "workload": wl.name, "cells": int(len(cells)),
+           "network": {"conv_layers": 4, "channels": 32, "hidden": 128, "outputs": D, "params": sur.n_params,
+                       "weights": "bf16 (fp32 masters)"},
+           "training": {"media": args.train_media, "cells": int(n), "iterations": args.train_iters,
+                        "batch": args.batch, "loss_first": first, "loss_last": last, "train_s": t_train,
+                        "label_build_s": build_s, "data_s": t_data},
+           "exact_offline_s": t_exact, "exact_rom_vs_fine": rel(ref, fine_tr), "runs": runs}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,7 +644,15 @@ def main():
                     help="measure the 4096-cell, 256-source launch shape instead (separate JSON line)")
     ap.add_argument("--many-steps", type=int, default=200, help="time steps per timed run of --many-sources")
     ap.add_argument("--box", type=int, default=16, help="cells per box edge of --many-sources")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="train the learned surrogate and compare surrogate ROMs with the exact one (JSON line)")
+    ap.add_argument("--train-media", type=int, default=24)
+    ap.add_argument("--train-iters", type=int, default=2000)
+    ap.add_argument("--batch", type=int, default=64)
     args = ap.parse_args()
+    if args.surrogate:
+        run_surrogate(args)
+        return
     if args.many_sources:
         run_many_sources(args)
         return

@@ -449,6 +449,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, co
 #include "cell_tc.cuh"
 #include "cell_stream.cuh"
 #include "cell_split.cuh"
+#include "cell_tc_split.cuh"
 
 namespace mss {
 
@@ -480,6 +481,8 @@ struct mss_sim {
   int prec = MSS_FP64;
   int tc = 0, tc_terms = 3, tc_nt = 16;       // tensor-core cell kernel
   size_t tc_smem = 0;
+  int tcs_nt = 16;                             // split tensor-core kernels: sources per CTA
+  size_t tcs_smem = 0;
   mss::TcArgs tca{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
@@ -571,6 +574,11 @@ static StepArgs<T> make_args(const mss_sim &s) {
 template <typename T, int ST>
 static void set_smem_attrs(const mss_sim &s) {
   if (s.tc) {
+    for (const void *kf : {(const void *)k_tc_split<16, true>, (const void *)k_tc_split<16, false>,
+                           (const void *)k_tc_split<32, true>, (const void *)k_tc_split<32, false>,
+                           (const void *)k_tc_split<64, true>, (const void *)k_tc_split<64, false>,
+                           (const void *)k_tc_split<128, true>, (const void *)k_tc_split<128, false>})
+      MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tcs_smem));
     MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
     MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
     MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
@@ -625,8 +633,27 @@ static SplitArgs<T> make_split(const mss_sim &s) {
   return p;
 }
 
+template <int NT>
+static void launch_tc_split(const mss_sim &s, const StepArgs<float> &a, const SplitArgs<float> &p, int cur,
+                            cudaStream_t st) {
+  const int tiles = (s.n_src + NT - 1) / NT;
+  k_tc_split<NT, true><<<dim3(s.n_flux_items * tiles), kTcsThreads, s.tcs_smem, st>>>(a, p, s.tca, cur);
+  if (s.n_accel_items > 0)
+    k_tc_split<NT, false><<<dim3(s.n_accel_items * tiles), kTcsThreads, s.tcs_smem, st>>>(a, p, s.tca, cur);
+}
+
 template <typename T, int ST>
 static void launch_split(const mss_sim &s, const StepArgs<T> &a, const SplitArgs<T> &p, int cur, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (s.tc) {
+      switch (s.tcs_nt) {
+        case 16: launch_tc_split<16>(s, a, p, cur, st); return;
+        case 32: launch_tc_split<32>(s, a, p, cur, st); return;
+        case 64: launch_tc_split<64>(s, a, p, cur, st); return;
+        default: launch_tc_split<128>(s, a, p, cur, st); return;
+      }
+    }
+  }
   k_flux<T, ST><<<dim3(s.n_flux_items * s.tiles), kSplitThreads, s.split_smem, st>>>(a, p, cur);
   if (s.n_accel_items > 0)
     k_accel<T, ST><<<dim3(s.n_accel_items * s.tiles), kSplitThreads, s.split_smem, st>>>(a, p, cur);
@@ -933,6 +960,8 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
                 "cells too large for the tensor-core kernel");
     s.tc_nt = nt;
     s.tc_smem = smem_of(nt);
+    s.tcs_nt = S <= 16 ? 16 : S <= 32 ? 32 : S <= 64 ? 64 : 128;
+    s.tcs_smem = tcs_smem_bytes(s.tcs_nt, kpmax);
     std::vector<uint16_t> blob;
     std::vector<int64_t> off;
     std::vector<int32_t> kp, kr;
@@ -1407,7 +1436,7 @@ static bool sched_allowed(const mss_sim &s, int sched) {
     case MSS_SCHED_GRAPH_STREAM: return s.stream_ok;
     case MSS_SCHED_PERSIST: return !s.tc;
     case MSS_SCHED_PERSIST_STREAM: return s.stream_ok;
-    case MSS_SCHED_GRAPH_SPLIT: return !s.tc && s.split_smem <= 48 * 1024;
+    case MSS_SCHED_GRAPH_SPLIT: return s.tc ? true : s.split_smem <= 48 * 1024;
     default: return false;
   }
 }

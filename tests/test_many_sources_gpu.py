@@ -87,3 +87,5 @@ def test_tensor_core(P, case, prec_tol):
     out, sim = _run(P, case, prec)
     assert sim.info()[3] == NST
     assert _rel(out, case["ref"]) <= tol
+    split, _ = _run(P, case, prec, P.SCHED_GRAPH_SPLIT)
+    assert np.array_equal(split, out)

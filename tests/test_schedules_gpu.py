@@ -164,3 +164,24 @@ def test_streamed_kernel_full_launch_shape(P):
         if base is None:
             base = out
         assert np.array_equal(out, base), k
+
+
+@pytest.mark.parametrize("n_src", [16, 37, 200])
+def test_tensor_core_fused_and_split_agree(P, n_src):
+    """The split tensor-core kernels (one product per CTA, N up to 128 sources) give the fused
+    kernel's traces bit for bit, within the precision's bar of the oracle."""
+    topo, co, src, rcv = _case(n_src=n_src, seed=30 + n_src)
+    tau, nst = 0.08, 100
+    w = synth.ricker(np.arange(nst) * tau, 0.6)
+    ref = _oracle(topo, co, src, rcv, n_src, 4, w, tau, nst)
+    for prec, tol in ((P.FP32_TC, 1e-3), (P.BF16_TC, 5e-2)):
+        sim = _sim(P, topo, co, src, rcv, n_src, 4, tau, prec)
+        _, avail = sim.schedule()
+        assert avail[P.SCHED_GRAPH] and avail[P.SCHED_GRAPH_SPLIT] and not avail[P.SCHED_PERSIST]
+        outs = []
+        for k in (P.SCHED_GRAPH, P.SCHED_GRAPH_SPLIT):
+            sim.reset()
+            sim.set_schedule(k)
+            outs.append(_run(P, sim, w, nst, n_src, 4, prec))
+            assert _rel(outs[-1], ref) <= tol, (prec, k)
+        assert np.array_equal(outs[0], outs[1]), (prec, _rel(outs[1], outs[0]))
