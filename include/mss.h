@@ -266,8 +266,10 @@ mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_
  *                    staged into shared memory by 1-D TMA bulk copies through a 4-slot ring
  *                    (FP32, 16-source tiles, K_i <= 128; 256 or 512 threads, the autotuner
  *                    picks; 512 by default);
- *   PERSIST          one cooperative persistent kernel per block of up to 512 steps, phases
- *                    separated by a grid barrier with a 1 s time limit (CUDA-core precisions);
+ *   PERSIST          CUDA-core precisions: one cooperative persistent kernel per block of up to
+ *                    512 steps, phases separated by a grid barrier with a 1 s time limit;
+ *                    tensor-core precisions: the split products on a resident grid that loops
+ *                    over (cell, matrix, tile) items with the next matrix's bulk copy in flight;
  *   PERSIST_STREAM   PERSIST with the streamed cell body;
  *   GRAPH_SPLIT      as GRAPH with the cell phase split into a flux kernel and an acceleration
  *                    kernel of one small CTA per (cell, matrix), fluxes through a scratch block

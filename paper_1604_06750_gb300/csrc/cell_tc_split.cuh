@@ -13,11 +13,123 @@
 
 namespace mss {
 
-constexpr int kTcsThreads = 128;   // 4 warps = the 128 TMEM lanes (accumulator rows)
+constexpr int kTcsThreads = 256;   // 8 warps: warp w reads TMEM lanes 32 (w % 4).. (accumulator rows),
+                                   // columns split in two halves by w / 4
 
 // Shared-memory bytes of one split tensor-core CTA with NT sources and KpMax columns.
 __host__ __device__ constexpr size_t tcs_smem_bytes(int NT, int kpmax) {
   return (size_t)2 * 128 * kpmax * 2 + (size_t)2 * NT * kpmax * 2 + 64;
+}
+
+// B operand of one split product into the core layout (hi, lo): D^k = U^{k+1} - U^k for the
+// flux, E^k = F^k - F^{k-1} for the acceleration; rows >= K zero.  Lanes run over sources
+// (coalesced loads); each warp takes two 8-row groups per pass so that 32 loads are in flight.
+template <int NT, bool FLUX>
+__device__ __forceinline__ void tcs_stage_b(const StepArgs<float> &a, const float *Fk, const float *fs, const float *cs,
+                                            int64_t rp, int64_t so, int k, int m, int K, int Kp, int s0, int ns,
+                                            unsigned char *Bh, unsigned char *Bl) {
+  constexpr int CPW = NT < 32 ? NT : 32;
+  constexpr int RPW = 32 / CPW;
+  const int S = a.S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int NR8 = Kp / 8, ngp = (NR8 + RPW - 1) / RPW, cblocks = NT / CPW;
+  const int cl = lane % CPW, sub = lane / CPW;
+  const int passes = ngp * cblocks;
+  auto load8 = [&](int tt, float (&v)[8], int &off) -> bool {
+    const int cb = tt % cblocks, gp = tt / cblocks;
+    const int g8 = gp * RPW + sub, c = cb * CPW + cl;
+    if (tt >= passes || g8 >= NR8) return false;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = g8 * 8 + i;
+      float x = 0.f;
+      if (r < K && c < ns) {
+        if (FLUX) {
+          const float u0 = k == 0 ? fs[(a.row_face_row[rp + r]) * S + s0 + c]
+                                  : cs[(so + (int64_t)(k - 1) * K + r) * S + s0 + c];
+          const float u1 = k + 1 < m ? cs[(so + (int64_t)k * K + r) * S + s0 + c] : 0.f;
+          x = u1 - u0;
+        } else {
+          x = Fk[(int64_t)r * S + c] - Fk[(int64_t)(r - K) * S + c];
+        }
+      }
+      v[i] = x;
+    }
+    off = (int)core_off(c, g8 * 8, Kp);
+    return true;
+  };
+  for (int tt = warp; tt < passes; tt += 2 * nw) {
+    float va[8], vb[8];
+    int oa = 0, ob = 0;
+    const bool ha = load8(tt, va, oa), hb = load8(tt + nw, vb, ob);
+    if (ha) store_core8(Bh, Bl, (unsigned)oa, va);
+    if (hb) store_core8(Bh, Bl, (unsigned)ob, vb);
+  }
+}
+
+// Epilogue of one split product: warp w reads TMEM lanes 32 (w % 4).. for the columns of half
+// w / 4; flux -> F scratch (and the face flux buffer for k = 0), acceleration -> leapfrog of
+// the hidden layer.  Two 8-column chunks per iteration keep their global loads in flight together.
+template <int NT, bool FLUX>
+__device__ __forceinline__ void tcs_epilogue(const StepArgs<float> &a, const SplitArgs<float> &p, unsigned tmem,
+                                             int cell, int k, int K, int s0, int ns, int64_t rp, int64_t so,
+                                             const float *cs, float *cso) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3, half = warp >> 2;
+  const int r = 32 * q + lane;
+  const unsigned lane_addr = (unsigned)(32 * q) << 16;
+  constexpr int CH = NT / 2;                        // columns per half (8 .. 64)
+  const int c0 = half * CH;
+  const int S = a.S;
+  const bool vec_ok = (S % 4) == 0;
+  const float tau2 = a.tau2;
+  for (int cc = 0; cc < CH; cc += 8) {
+    float acc[8];
+    __syncwarp();
+    tc_ld8(tmem + lane_addr + (unsigned)(c0 + cc), acc);   // every lane loads; stores are predicated
+    if (r >= K) continue;
+    const int col = c0 + cc;
+    const bool full8 = vec_ok && col + 8 <= ns;
+    if (FLUX) {
+      float *o = p.F + (p.f_off[cell] + (int64_t)k * K + r) * S + s0 + col;
+      float *fo = k == 0 ? a.flux + (a.row_face_row[rp + r] * 2 + a.row_side[rp + r]) * S + s0 + col : nullptr;
+      if (full8) {
+        const float4 v0 = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        const float4 v1 = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        reinterpret_cast<float4 *>(o)[0] = v0;
+        reinterpret_cast<float4 *>(o)[1] = v1;
+        if (fo) {
+          reinterpret_cast<float4 *>(fo)[0] = v0;
+          reinterpret_cast<float4 *>(fo)[1] = v1;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (col + e < ns) {
+            o[e] = acc[e];
+            if (fo) fo[e] = acc[e];
+          }
+      }
+    } else {
+      const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + col;
+      if (full8) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
+          float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
+          od.x = 2.f * nw.x - od.x + tau2 * acc[4 * h + 0];
+          od.y = 2.f * nw.y - od.y + tau2 * acc[4 * h + 1];
+          od.z = 2.f * nw.z - od.z + tau2 * acc[4 * h + 2];
+          od.w = 2.f * nw.w - od.w + tau2 * acc[4 * h + 3];
+          *reinterpret_cast<float4 *>(cso + base + 4 * h) = od;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (col + e < ns) cso[base + e] = 2.f * cs[base + e] - cso[base + e] + tau2 * acc[e];
+      }
+    }
+  }
 }
 
 template <int NT, bool FLUX>
@@ -81,35 +193,7 @@ __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<floa
   }
   // B: D^k = U^{k+1} - U^k (flux) or E^k = F^k - F^{k-1} (acceleration), rows >= K zero
   const float *Fk = p.F + (p.f_off[cell] + (int64_t)k * K) * S + s0;
-  {
-    constexpr int CPW = NT < 32 ? NT : 32;
-    constexpr int RPW = 32 / CPW;
-    const int NR8 = Kp / 8, ngp = (NR8 + RPW - 1) / RPW, cblocks = NT / CPW;
-    const int cl = lane % CPW, sub = lane / CPW;
-    for (int tt = warp; tt < ngp * cblocks; tt += kTcsThreads / 32) {
-      const int cb = tt % cblocks, gp = tt / cblocks;
-      const int g8 = gp * RPW + sub, c = cb * CPW + cl;
-      if (g8 >= NR8) continue;
-      float v[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int r = g8 * 8 + i;
-        float x = 0.f;
-        if (r < K && c < ns) {
-          if (FLUX) {
-            const float u0 = k == 0 ? fs[(a.row_face_row[rp + r]) * S + s0 + c]
-                                    : cs[(so + (int64_t)(k - 1) * K + r) * S + s0 + c];
-            const float u1 = k + 1 < m ? cs[(so + (int64_t)k * K + r) * S + s0 + c] : 0.f;
-            x = u1 - u0;
-          } else {
-            x = Fk[(int64_t)r * S + c] - Fk[(int64_t)(r - K) * S + c];
-          }
-        }
-        v[i] = x;
-      }
-      store_core8(Bh, Bl, core_off(c, g8 * 8, Kp), v);
-    }
-  }
+  tcs_stage_b<NT, FLUX>(a, Fk, fs, cs, rp, so, k, m, K, Kp, s0, ns, Bh, Bl);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -142,62 +226,148 @@ __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<floa
   const bool go = ok_sm != 0;
   tc_fence_after();
   if (go) {
-    const int r = 32 * warp + lane;                  // accumulator row = TMEM lane
-    const unsigned lane_addr = (unsigned)(32 * warp) << 16;
-    const bool vec_ok = (S % 4) == 0;
-    const float tau2 = a.tau2;
-    for (int cc = 0; cc < NT; cc += 8) {
-      float acc[8];
-      __syncwarp();
-      tc_ld8(tmem + lane_addr + (unsigned)cc, acc);   // every lane loads; stores are predicated
-      if (r < K) {
-      const bool full8 = vec_ok && cc + 8 <= ns;
-      if (FLUX) {
-        float *o = p.F + (p.f_off[cell] + (int64_t)k * K + r) * S + s0 + cc;
-        float *fo = k == 0 ? a.flux + (a.row_face_row[rp + r] * 2 + a.row_side[rp + r]) * S + s0 + cc : nullptr;
-        if (full8) {
-          const float4 v0 = make_float4(acc[0], acc[1], acc[2], acc[3]);
-          const float4 v1 = make_float4(acc[4], acc[5], acc[6], acc[7]);
-          reinterpret_cast<float4 *>(o)[0] = v0;
-          reinterpret_cast<float4 *>(o)[1] = v1;
-          if (fo) {
-            reinterpret_cast<float4 *>(fo)[0] = v0;
-            reinterpret_cast<float4 *>(fo)[1] = v1;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (cc + j < ns) {
-              o[j] = acc[j];
-              if (fo) fo[j] = acc[j];
-            }
-        }
-      } else {
-        const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + cc;
-        if (full8) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
-            float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
-            od.x = 2.f * nw.x - od.x + tau2 * acc[4 * h + 0];
-            od.y = 2.f * nw.y - od.y + tau2 * acc[4 * h + 1];
-            od.z = 2.f * nw.z - od.z + tau2 * acc[4 * h + 2];
-            od.w = 2.f * nw.w - od.w + tau2 * acc[4 * h + 3];
-            *reinterpret_cast<float4 *>(cso + base + 4 * h) = od;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (cc + j < ns) cso[base + j] = 2.f * cs[base + j] - cso[base + j] + tau2 * acc[j];
-        }
-      }
-      }
-    }
+    tcs_epilogue<NT, FLUX>(a, p, tmem, cell, k, K, s0, ns, rp, so, cs, cso);
   } else if (tid == 0) {
     atomicExch(t.err, 1);
     // the A copies must land, and issued products finish, before shared memory and TMEM go away
     mbar_wait(full, 0, nullptr);
     if (issued_sm) mbar_wait(done, 0, nullptr);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(cols) : "memory");
+  }
+}
+
+}  // namespace mss
+
+namespace mss {
+
+// Shared memory of the pipelined split kernel: barriers, two A slots of Kr_max rows (hi, lo),
+// one B buffer (hi, lo) and a tail so that the 128-row A reads of the last slot stay inside the
+// allocation (rows >= Kr of a product only feed accumulator rows that are never stored).
+__host__ __device__ constexpr size_t tcp_smem_bytes(int NT, int kpmax, int krmax) {
+  return 64 + (size_t)4 * krmax * kpmax * 2 + (size_t)2 * NT * kpmax * 2 + (size_t)(128 - krmax) * kpmax * 2 + 64;
+}
+
+// Pipelined form of k_tc_split: a resident grid loops over the (item, tile) list; while item j is
+// staged, multiplied and written back, the bulk copy of item j+1's matrix is already in flight
+// into the other A slot.  Same products and epilogues as k_tc_split (bit-identical).
+template <int NT, bool FLUX>
+__global__ void __launch_bounds__(kTcsThreads, 1) k_tc_pipe(const StepArgs<float> a, const SplitArgs<float> p,
+                                                            const TcArgs t, const int cur, const int n_items,
+                                                            const int krmax) {
+  const int tiles = (a.S + NT - 1) / NT;
+  const int total = n_items * tiles;
+  const int S = a.S;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int kpmax = (t.slot_bytes / 2) / (128 * 2);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);    // full0, full1, done
+  unsigned *tmem_sm = reinterpret_cast<unsigned *>(bars + 3);
+  const size_t half = (size_t)krmax * kpmax * 2;
+  unsigned char *A0 = smem + 64;                             // slot s: hi at A0 + 2s half, lo after it
+  unsigned char *Bh = A0 + 4 * half, *Bl = Bh + (size_t)NT * kpmax * 2;
+  const unsigned full[2] = {smem_u32(bars + 0), smem_u32(bars + 1)};
+  const unsigned done = smem_u32(bars + 2);
+  const float *fs = cur ? a.fstate1 : a.fstate0;
+  const float *cs = cur ? a.cstate1 : a.cstate0;
+  float *cso = cur ? a.cstate0 : a.cstate1;
+  unsigned cols = 32;
+  while (cols < (unsigned)NT) cols <<= 1;
+
+  __shared__ int bail, ok_sm;
+  if (tid == 0) bail = *(volatile const int *)t.err;
+  __syncthreads();
+  if (bail || (int)blockIdx.x >= total) return;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_sm)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(full[0], 1);
+    mbar_init(full[1], 1);
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *tmem_sm;
+  // thread 0 bookkeeping: copies issued / waited for, products committed / waited for
+  int n_issued = 0, n_landed = 0, n_committed = 0, n_done = 0;
+  auto issue_A = [&](int it, int slot) {
+    const int2 itm = FLUX ? p.flux_items[it / tiles] : p.accel_items[it / tiles];
+    const int c = itm.x, mm = a.cell_m[c];
+    const int mat = FLUX ? itm.y : mm + itm.y - 1;
+    const unsigned mh = (unsigned)t.Kr[c] * t.Kp[c] * 2;
+    const unsigned char *src = t.blob + t.blob_off[c] + (size_t)mat * 2 * mh;
+    unsigned char *dst = A0 + (size_t)2 * slot * half;
+    mbar_expect_tx(full[slot], t.terms == 3 ? 2 * mh : mh);
+    bulk_g2s(smem_u32(dst), src, mh, full[slot]);
+    if (t.terms == 3) bulk_g2s(smem_u32(dst + half), src + mh, mh, full[slot]);
+    ++n_issued;
+  };
+  if (tid == 0) issue_A(blockIdx.x, 0);
+  bool ok = true;
+  int j = 0;
+  for (int it = blockIdx.x; it < total; it += gridDim.x, ++j) {
+    const int slot = j & 1;
+    if (tid == 0 && it + (int)gridDim.x < total) issue_A(it + gridDim.x, slot ^ 1);
+    const int2 itm = FLUX ? p.flux_items[it / tiles] : p.accel_items[it / tiles];
+    const int cell = itm.x, k = itm.y;
+    const int s0 = (it % tiles) * NT;
+    const int K = a.cell_K[cell], m = a.cell_m[cell], Kp = t.Kp[cell];
+    const int ns = min(NT, S - s0);
+    const int64_t rp = a.cell_row[cell], so = a.cell_state[cell];
+    const float *Fk = p.F + (p.f_off[cell] + (int64_t)k * K) * S + s0;
+    tcs_stage_b<NT, FLUX>(a, Fk, fs, cs, rp, so, k, m, K, Kp, s0, ns, Bh, Bl);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      int good = mbar_wait(full[slot], (j >> 1) & 1, t.err) ? 1 : 0;
+      if (good) {
+        ++n_landed;
+        tc_fence_after();
+        const uint32_t idesc = idesc_bf16(128, NT);
+        const unsigned lbo = 128, sbo = 16u * Kp;
+        const unsigned ah = smem_u32(A0 + (size_t)2 * slot * half), al = ah + (unsigned)half;
+        const unsigned bh = smem_u32(Bh), bl = smem_u32(Bl);
+        for (int kk = 0; kk < Kp / 16; ++kk) {
+          const unsigned o = kk * 256;
+          mma_bf16(tmem, sdesc(ah + o, lbo, sbo), sdesc(bh + o, lbo, sbo), idesc, kk > 0 ? 1u : 0u);
+          if (t.terms == 3) {
+            mma_bf16(tmem, sdesc(ah + o, lbo, sbo), sdesc(bl + o, lbo, sbo), idesc, 1u);
+            mma_bf16(tmem, sdesc(al + o, lbo, sbo), sdesc(bh + o, lbo, sbo), idesc, 1u);
+          }
+        }
+        tc_commit(done);
+        ++n_committed;
+        good = mbar_wait(done, j & 1, t.err) ? 1 : 0;
+        if (good) ++n_done;
+      }
+      ok_sm = good;
+    }
+    __syncthreads();
+    if (!ok_sm) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    tcs_epilogue<NT, FLUX>(a, p, tmem, cell, k, K, s0, ns, rp, so, cs, cso);
+    tc_fence_before();
+    __syncthreads();   // TMEM, the B buffer and this item's A slot are free again
+  }
+  if (!ok && tid == 0) {
+    atomicExch(t.err, 1);
+    // wait (bounded) for this CTA's copies and products still in flight
+    for (int c = n_landed; c < n_issued; ++c) mbar_wait(full[c & 1], (c >> 1) & 1, nullptr);
+    if (n_committed > n_done) mbar_wait(done, (n_committed - 1) & 1, nullptr);
   }
   tc_fence_before();
   __syncthreads();

@@ -483,6 +483,8 @@ struct mss_sim {
   size_t tc_smem = 0;
   int tcs_nt = 16;                             // split tensor-core kernels: sources per CTA
   size_t tcs_smem = 0;
+  size_t tcp_smem = 0;                         // pipelined split tensor-core kernels
+  int tcp_krmax = 8, tcp_slots = 1;
   mss::TcArgs tca{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
@@ -579,6 +581,11 @@ static void set_smem_attrs(const mss_sim &s) {
                            (const void *)k_tc_split<64, true>, (const void *)k_tc_split<64, false>,
                            (const void *)k_tc_split<128, true>, (const void *)k_tc_split<128, false>})
       MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tcs_smem));
+    for (const void *kf : {(const void *)k_tc_pipe<16, true>, (const void *)k_tc_pipe<16, false>,
+                           (const void *)k_tc_pipe<32, true>, (const void *)k_tc_pipe<32, false>,
+                           (const void *)k_tc_pipe<64, true>, (const void *)k_tc_pipe<64, false>,
+                           (const void *)k_tc_pipe<128, true>, (const void *)k_tc_pipe<128, false>})
+      MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tcp_smem));
     MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
     MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
     MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
@@ -642,9 +649,33 @@ static void launch_tc_split(const mss_sim &s, const StepArgs<float> &a, const Sp
     k_tc_split<NT, false><<<dim3(s.n_accel_items * tiles), kTcsThreads, s.tcs_smem, st>>>(a, p, s.tca, cur);
 }
 
+template <int NT>
+static void launch_tc_pipe(const mss_sim &s, const StepArgs<float> &a, const SplitArgs<float> &p, int cur,
+                           cudaStream_t st) {
+  const int tiles = (s.n_src + NT - 1) / NT;
+  for (int ph = 0; ph < 2; ++ph) {
+    const int n_items = ph == 0 ? s.n_flux_items : s.n_accel_items;
+    if (n_items == 0) continue;
+    const int total = n_items * tiles;
+    const int grid = std::min(total, s.tcp_slots);
+    if (ph == 0)
+      k_tc_pipe<NT, true><<<grid, kTcsThreads, s.tcp_smem, st>>>(a, p, s.tca, cur, n_items, s.tcp_krmax);
+    else
+      k_tc_pipe<NT, false><<<grid, kTcsThreads, s.tcp_smem, st>>>(a, p, s.tca, cur, n_items, s.tcp_krmax);
+  }
+}
+
 template <typename T, int ST>
 static void launch_split(const mss_sim &s, const StepArgs<T> &a, const SplitArgs<T> &p, int cur, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
+    if (s.tc && s.sched == MSS_SCHED_PERSIST) {
+      switch (s.tcs_nt) {
+        case 16: launch_tc_pipe<16>(s, a, p, cur, st); return;
+        case 32: launch_tc_pipe<32>(s, a, p, cur, st); return;
+        case 64: launch_tc_pipe<64>(s, a, p, cur, st); return;
+        default: launch_tc_pipe<128>(s, a, p, cur, st); return;
+      }
+    }
     if (s.tc) {
       switch (s.tcs_nt) {
         case 16: launch_tc_split<16>(s, a, p, cur, st); return;
@@ -713,7 +744,7 @@ static void launch_steps(mss_sim &s, int64_t n, const double *w, T *traces, cuda
   int cur = s.cur;
   const SplitArgs<T> sp = make_split<T>(s);
   for (int64_t j = 0; j < n; ++j) {
-    if (s.sched == MSS_SCHED_GRAPH_SPLIT) launch_split<T, ST>(s, a, sp, cur, st);
+    if (s.sched == MSS_SCHED_GRAPH_SPLIT || (s.tc && s.sched == MSS_SCHED_PERSIST)) launch_split<T, ST>(s, a, sp, cur, st);
     else launch_cell<T, ST>(s, a, cur, st);
     k_face<T, ST><<<gf, kFaceThreads, s.face_smem, st>>>(a, cur, w + j, traces + j * (int64_t)s.n_rcv * s.n_src);
     if (s.corners) k_corner<T, ST><<<gk, kFaceThreads, s.corner_smem, st>>>(a, cur);
@@ -725,7 +756,7 @@ static void launch_steps(mss_sim &s, int64_t n, const double *w, T *traces, cuda
 template <typename T, int ST>
 static void step_impl(mss_sim &s, int64_t n, const double *w, void *traces, int use_graph, cudaStream_t st) {
   set_smem_attrs<T, ST>(s);
-  if (s.sched == MSS_SCHED_PERSIST || s.sched == MSS_SCHED_PERSIST_STREAM) {
+  if (!s.tc && (s.sched == MSS_SCHED_PERSIST || s.sched == MSS_SCHED_PERSIST_STREAM)) {
     launch_persist<T, ST>(s, n, w, (T *)traces, st);
   } else if (!use_graph) {
     launch_steps<T, ST>(s, n, w, (T *)traces, st);
@@ -775,7 +806,7 @@ static void profile_impl(mss_sim &s, int64_t n, const double *w, T *traces, doub
   try {
     for (int64_t j = 0; j < n; ++j) {
       MSS_CUDA(cudaEventRecord(ev[0], st));
-      if (s.sched == MSS_SCHED_GRAPH_SPLIT) launch_split<T, ST>(s, a, sp, cur, st);
+      if (s.sched == MSS_SCHED_GRAPH_SPLIT || (s.tc && s.sched == MSS_SCHED_PERSIST)) launch_split<T, ST>(s, a, sp, cur, st);
       else launch_cell<T, ST>(s, a, cur, st);
       MSS_CUDA(cudaEventRecord(ev[1], st));
       k_face<T, ST><<<gf, kFaceThreads, s.face_smem, st>>>(a, cur, w + j, traces + j * (int64_t)s.n_rcv * s.n_src);
@@ -962,6 +993,21 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
     s.tc_smem = smem_of(nt);
     s.tcs_nt = S <= 16 ? 16 : S <= 32 ? 32 : S <= 64 ? 64 : 128;
     s.tcs_smem = tcs_smem_bytes(s.tcs_nt, kpmax);
+    for (int K : R.cell_K) s.tcp_krmax = std::max(s.tcp_krmax, (K + 7) / 8 * 8);
+    s.tcp_smem = tcp_smem_bytes(s.tcs_nt, kpmax, s.tcp_krmax);
+    {
+      // resident CTAs of the pipelined kernels (shared memory bound; at most 2 per SM keeps
+      // TMEM at <= 2 x 128 columns)
+      int sms = 0, per = 0;
+      MSS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device));
+      const void *kf = s.tcs_nt == 16 ? (const void *)k_tc_pipe<16, true>
+                       : s.tcs_nt == 32 ? (const void *)k_tc_pipe<32, true>
+                       : s.tcs_nt == 64 ? (const void *)k_tc_pipe<64, true>
+                                        : (const void *)k_tc_pipe<128, true>;
+      MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tcp_smem));
+      MSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kf, kTcsThreads, s.tcp_smem));
+      s.tcp_slots = std::max(1, std::min(per, 2)) * sms;
+    }
     std::vector<uint16_t> blob;
     std::vector<int64_t> off;
     std::vector<int32_t> kp, kr;
@@ -1434,7 +1480,7 @@ static bool sched_allowed(const mss_sim &s, int sched) {
   switch (sched) {
     case MSS_SCHED_GRAPH: return true;
     case MSS_SCHED_GRAPH_STREAM: return s.stream_ok;
-    case MSS_SCHED_PERSIST: return !s.tc;
+    case MSS_SCHED_PERSIST: return true;   // tensor-core precisions: pipelined split kernels
     case MSS_SCHED_PERSIST_STREAM: return s.stream_ok;
     case MSS_SCHED_GRAPH_SPLIT: return s.tc ? true : s.split_smem <= 48 * 1024;
     default: return false;

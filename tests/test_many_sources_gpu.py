@@ -87,5 +87,6 @@ def test_tensor_core(P, case, prec_tol):
     out, sim = _run(P, case, prec)
     assert sim.info()[3] == NST
     assert _rel(out, case["ref"]) <= tol
-    split, _ = _run(P, case, prec, P.SCHED_GRAPH_SPLIT)
-    assert np.array_equal(split, out)
+    for k in (P.SCHED_GRAPH_SPLIT, P.SCHED_PERSIST):
+        other, _ = _run(P, case, prec, k)
+        assert np.array_equal(other, out), k

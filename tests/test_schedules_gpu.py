@@ -168,8 +168,9 @@ def test_streamed_kernel_full_launch_shape(P):
 
 @pytest.mark.parametrize("n_src", [16, 37, 200])
 def test_tensor_core_fused_and_split_agree(P, n_src):
-    """The split tensor-core kernels (one product per CTA, N up to 128 sources) give the fused
-    kernel's traces bit for bit, within the precision's bar of the oracle."""
+    """The split tensor-core kernels (one product per CTA, N up to 128 sources) and their
+    pipelined resident-grid form give the fused kernel's traces bit for bit, within the
+    precision's bar of the oracle."""
     topo, co, src, rcv = _case(n_src=n_src, seed=30 + n_src)
     tau, nst = 0.08, 100
     w = synth.ricker(np.arange(nst) * tau, 0.6)
@@ -177,11 +178,13 @@ def test_tensor_core_fused_and_split_agree(P, n_src):
     for prec, tol in ((P.FP32_TC, 1e-3), (P.BF16_TC, 5e-2)):
         sim = _sim(P, topo, co, src, rcv, n_src, 4, tau, prec)
         _, avail = sim.schedule()
-        assert avail[P.SCHED_GRAPH] and avail[P.SCHED_GRAPH_SPLIT] and not avail[P.SCHED_PERSIST]
+        assert avail[P.SCHED_GRAPH] and avail[P.SCHED_GRAPH_SPLIT] and avail[P.SCHED_PERSIST]
+        assert not avail[P.SCHED_GRAPH_STREAM] and not avail[P.SCHED_PERSIST_STREAM]
         outs = []
-        for k in (P.SCHED_GRAPH, P.SCHED_GRAPH_SPLIT):
+        for k in (P.SCHED_GRAPH, P.SCHED_GRAPH_SPLIT, P.SCHED_PERSIST):
             sim.reset()
             sim.set_schedule(k)
             outs.append(_run(P, sim, w, nst, n_src, 4, prec))
             assert _rel(outs[-1], ref) <= tol, (prec, k)
-        assert np.array_equal(outs[0], outs[1]), (prec, _rel(outs[1], outs[0]))
+        for o in outs[1:]:
+            assert np.array_equal(outs[0], o), (prec, _rel(o, outs[0]))
