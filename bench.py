@@ -435,8 +435,7 @@ def run_many_sources(args):
     if args.profile:
         prec = {"fp32": P.FP32, "fp32_tc": P.FP32_TC, "bf16_tc": P.BF16_TC}[args.prec]
         sim = P.Sim(R, prec, 0.05)
-        if prec == P.FP32:
-            sim.set_schedule(args.sched)
+        sim.set_schedule(args.sched)
         w = torch.tensor(synth.ricker(np.arange(args.profile) * 0.05, 4.0), device=dev)
         tr = torch.zeros((args.profile, 128, 256), device=dev, dtype=torch.float32)
         sim.step(args.profile, w, tr, use_graph=False)
