@@ -64,9 +64,12 @@ constexpr int kCellThreads = 256;
 constexpr int kFaceThreads = 128;
 constexpr int kChunk = 8;      // coefficients loaded ahead per thread (register pipeline)
 
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // acc[s] = sum_c G[c*K] * X[c*ST + s] for the thread's output row (G already offset by the row).
 // The column stream of G is software-pipelined in registers: the next kChunk loads are issued
-// before the current kChunk values are consumed, so ~2 kChunk loads per thread are in flight.
+// before the current kChunk values are consumed, and the chunk after that is prefetched into L2,
+// so each register load waits on L2 rather than on HBM.
 template <typename T, int ST>
 __device__ __forceinline__ void row_times_block(const T *__restrict__ G, int K, const T *__restrict__ X,
                                                 T (&acc)[ST]) {
@@ -74,9 +77,15 @@ __device__ __forceinline__ void row_times_block(const T *__restrict__ G, int K, 
   for (int s = 0; s < ST; ++s) acc[s] = T(0);
   T g[kChunk], gn[kChunk];
 #pragma unroll
+  for (int j = 0; j < 2 * kChunk; ++j)
+    if (kChunk + j < K) prefetch_l2(G + (size_t)(kChunk + j) * K);
+#pragma unroll
   for (int j = 0; j < kChunk; ++j) g[j] = j < K ? __ldg(G + (size_t)j * K) : T(0);
   for (int c0 = 0; c0 < K; c0 += kChunk) {
     const int c1 = c0 + kChunk;
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j)
+      if (c1 + 2 * kChunk + j < K) prefetch_l2(G + (size_t)(c1 + 2 * kChunk + j) * K);
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) gn[j] = (c1 + j < K) ? __ldg(G + (size_t)(c1 + j) * K) : T(0);
 #pragma unroll
