@@ -270,7 +270,10 @@ mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_
  *                    512 steps, phases separated by a grid barrier with a 1 s time limit;
  *                    tensor-core precisions: the split products on a resident grid that loops
  *                    over (cell, matrix, tile) items with the next matrix's bulk copy in flight;
- *   PERSIST_STREAM   PERSIST with the streamed cell body;
+ *   PERSIST_STREAM   CUDA-core: PERSIST with the streamed cell body; tensor-core precisions: a
+ *                    warp-specialised persistent kernel (one CTA per SM, a producer warp
+ *                    streaming the matrices through a 4-slot mbarrier ring, compute warps
+ *                    issuing the products and epilogues);
  *   GRAPH_SPLIT      as GRAPH with the cell phase split into a flux kernel and an acceleration
  *                    kernel of one small CTA per (cell, matrix), fluxes through a scratch block
  *                    (CUDA-core precisions).

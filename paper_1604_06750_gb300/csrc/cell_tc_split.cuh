@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<floa
   const int K = a.cell_K[cell], m = a.cell_m[cell];
   const int Kp = t.Kp[cell], Kr = t.Kr[cell];
   const int S = a.S, ns = min(NT, S - s0);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   extern __shared__ __align__(128) unsigned char smem[];
   // layout: A hi (128 x KpMax), A lo, B hi (NT x KpMax), B lo, then barriers; the A halves and
   // the B halves are KpMax-strided so that one allocation serves every cell

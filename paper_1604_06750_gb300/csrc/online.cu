@@ -459,6 +459,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, co
 #include "cell_stream.cuh"
 #include "cell_split.cuh"
 #include "cell_tc_split.cuh"
+#include "cell_tc_pipe.cuh"
 
 namespace mss {
 
@@ -494,6 +495,8 @@ struct mss_sim {
   size_t tcs_smem = 0;
   size_t tcp_smem = 0;                         // pipelined split tensor-core kernels
   int tcp_krmax = 8, tcp_slots = 1;
+  int tcq_nt = 0, tcq_grid = 1;                // warp-specialised persistent tensor-core kernel
+  size_t tcq_smem = 0;
   mss::TcArgs tca{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
@@ -584,6 +587,10 @@ static StepArgs<T> make_args(const mss_sim &s) {
 
 template <typename T, int ST>
 static void set_smem_attrs(const mss_sim &s) {
+  if (s.tc && s.tcq_nt) {
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_tcp<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tcq_smem));
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_tcp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tcq_smem));
+  }
   if (s.tc) {
     for (const void *kf : {(const void *)k_tc_split<16, true>, (const void *)k_tc_split<16, false>,
                            (const void *)k_tc_split<32, true>, (const void *)k_tc_split<32, false>,
@@ -612,6 +619,12 @@ static void set_smem_attrs(const mss_sim &s) {
 }
 
 template <int NT>
+static void launch_tcp(const mss_sim &s, const StepArgs<float> &a, int cur, cudaStream_t st) {
+  const int total = s.n_cells * ((s.n_src + NT - 1) / NT);
+  k_cell_tcp<NT><<<std::min(total, s.tcq_grid), kTcpThreads, s.tcq_smem, st>>>(a, s.tca, cur, s.tcp_krmax, s.max_m);
+}
+
+template <int NT>
 static void launch_tc(const mss_sim &s, const StepArgs<float> &a, int cur, cudaStream_t st) {
   const dim3 g(s.n_cells * ((s.n_src + NT - 1) / NT));
   k_cell_tc<NT><<<g, kTcThreads, s.tc_smem, st>>>(a, s.tca, cur);
@@ -620,6 +633,11 @@ static void launch_tc(const mss_sim &s, const StepArgs<float> &a, int cur, cudaS
 template <typename T, int ST>
 static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
+    if (s.tc && s.sched == MSS_SCHED_PERSIST_STREAM) {
+      if (s.tcq_nt == 32) launch_tcp<32>(s, a, cur, st);
+      else launch_tcp<16>(s, a, cur, st);
+      return;
+    }
     if (s.tc) {
       switch (s.tc_nt) {
         case 16: launch_tc<16>(s, a, cur, st); return;
@@ -1016,6 +1034,17 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
       MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tcp_smem));
       MSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kf, kTcsThreads, s.tcp_smem));
       s.tcp_slots = std::max(1, std::min(per, 2)) * sms;
+      // warp-specialised persistent kernel: 32-source tiles when they fit, else 16
+      for (int ntv : {32, 16}) {
+        if (ntv == 32 && S <= 16) continue;
+        const size_t need = tcp_smem(ntv, kpmax, s.tcp_krmax, s.max_m, s.max_K);
+        if (need <= (size_t)dev_smem && (size_t)s.max_m * ntv <= 512) {
+          s.tcq_nt = ntv;
+          s.tcq_smem = need;
+          break;
+        }
+      }
+      s.tcq_grid = sms;
     }
     std::vector<uint16_t> blob;
     std::vector<int64_t> off;
@@ -1490,7 +1519,7 @@ static bool sched_allowed(const mss_sim &s, int sched) {
     case MSS_SCHED_GRAPH: return true;
     case MSS_SCHED_GRAPH_STREAM: return s.stream_ok;
     case MSS_SCHED_PERSIST: return true;   // tensor-core precisions: pipelined split kernels
-    case MSS_SCHED_PERSIST_STREAM: return s.stream_ok;
+    case MSS_SCHED_PERSIST_STREAM: return s.tc ? s.tcq_nt > 0 : s.stream_ok;
     case MSS_SCHED_GRAPH_SPLIT: return s.tc ? true : s.split_smem <= 48 * 1024;
     default: return false;
   }

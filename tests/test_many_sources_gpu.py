@@ -87,6 +87,6 @@ def test_tensor_core(P, case, prec_tol):
     out, sim = _run(P, case, prec)
     assert sim.info()[3] == NST
     assert _rel(out, case["ref"]) <= tol
-    for k in (P.SCHED_GRAPH_SPLIT, P.SCHED_PERSIST):
+    for k in (P.SCHED_GRAPH_SPLIT, P.SCHED_PERSIST, P.SCHED_PERSIST_STREAM):
         other, _ = _run(P, case, prec, k)
         assert np.array_equal(other, out), k

@@ -168,9 +168,9 @@ def test_streamed_kernel_full_launch_shape(P):
 
 @pytest.mark.parametrize("n_src", [16, 37, 200])
 def test_tensor_core_fused_and_split_agree(P, n_src):
-    """The split tensor-core kernels (one product per CTA, N up to 128 sources) and their
-    pipelined resident-grid form give the fused kernel's traces bit for bit, within the
-    precision's bar of the oracle."""
+    """The split tensor-core kernels (one product per CTA, N up to 128 sources), their pipelined
+    resident-grid form and the warp-specialised persistent kernel give the fused kernel's traces
+    bit for bit, within the precision's bar of the oracle."""
     topo, co, src, rcv = _case(n_src=n_src, seed=30 + n_src)
     tau, nst = 0.08, 100
     w = synth.ricker(np.arange(nst) * tau, 0.6)
@@ -179,9 +179,9 @@ def test_tensor_core_fused_and_split_agree(P, n_src):
         sim = _sim(P, topo, co, src, rcv, n_src, 4, tau, prec)
         _, avail = sim.schedule()
         assert avail[P.SCHED_GRAPH] and avail[P.SCHED_GRAPH_SPLIT] and avail[P.SCHED_PERSIST]
-        assert not avail[P.SCHED_GRAPH_STREAM] and not avail[P.SCHED_PERSIST_STREAM]
+        assert avail[P.SCHED_PERSIST_STREAM] and not avail[P.SCHED_GRAPH_STREAM]
         outs = []
-        for k in (P.SCHED_GRAPH, P.SCHED_GRAPH_SPLIT, P.SCHED_PERSIST):
+        for k in (P.SCHED_GRAPH, P.SCHED_GRAPH_SPLIT, P.SCHED_PERSIST, P.SCHED_PERSIST_STREAM):
             sim.reset()
             sim.set_schedule(k)
             outs.append(_run(P, sim, w, nst, n_src, 4, prec))
