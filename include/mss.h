@@ -286,12 +286,21 @@ mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_
 #define MSS_SCHED_COUNT 5
 /* Errors: INVALID_ARG (schedule not available for this sim's precision, tile or cell sizes). */
 mss_status mss_sim_set_schedule(mss_sim *s, int32_t sched);
-/* sched: current schedule; available (may be NULL): [MSS_SCHED_COUNT] 1 where usable. */
-mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *available);
-/* Time n_steps (rounded up to even) of every available schedule on zero input, after one
- * untimed pass each, restoring the state after each; keep the fastest.  ms (host, may be NULL):
- * [MSS_SCHED_COUNT] ms per step, -1 where unavailable; chosen (may be NULL) receives the pick.
- * Synchronises the stream.  Errors: INVALID_ARG, TIMEOUT, CUDA. */
+/* Tile of the step kernels (values <= 0 leave a field unchanged): CUDA-core source tile (a power
+ * of two up to the one chosen at creation; 16 is needed by the streamed schedules, the schedule
+ * falls back to GRAPH otherwise), sources per CTA of the split tensor-core kernels (16, 32, 64,
+ * 128), thread groups of the streamed FP32 kernel (2 or 4).  Errors: INVALID_ARG. */
+mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources, int32_t groups);
+/* sched: current schedule; available (may be NULL): [MSS_SCHED_COUNT] 1 where usable; tile (may
+ * be NULL): [3] = CUDA-core source tile, sources per CTA of the split tensor-core kernels (0 for
+ * CUDA-core precisions), thread groups of the streamed FP32 kernel. */
+mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *available, int32_t *tile);
+/* Time n_steps (rounded up to even) of every available schedule and tile variant (CUDA-core
+ * source tile 16 or 8, split tensor-core N of 16..128, streamed-kernel block size) on zero
+ * input, after one untimed pass each, restoring the state after each; keep the fastest.  ms
+ * (host, may be NULL): [MSS_SCHED_COUNT] best ms per step of each schedule, -1 where unavailable;
+ * chosen (may be NULL) receives the schedule.  Synchronises the stream.
+ * Errors: INVALID_ARG, TIMEOUT, CUDA. */
 mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *ms, int32_t *chosen);
 mss_status mss_sim_load_state(mss_sim *s, const double *now, const double *old, int64_t steps_taken);
 void mss_sim_destroy(mss_sim *s);

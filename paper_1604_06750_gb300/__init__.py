@@ -124,7 +124,8 @@ _SIGS = [
     ("mss_surrogate_fit_output_transform", C.c_int32, [_P, C.c_int32, _P, _P]),
     ("mss_surrogate_predict", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P]),
     ("mss_sim_set_schedule", C.c_int32, [_P, C.c_int32]),
-    ("mss_sim_get_schedule", C.c_int32, [_P, _P, _P]),
+    ("mss_sim_get_schedule", C.c_int32, [_P, _P, _P, _P]),
+    ("mss_sim_set_tile", C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32]),
     ("mss_sim_autotune", C.c_int32, [_P, C.c_int32, _P, _P, _P]),
     ("mss_surrogate_infer", C.c_int32, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
 ]
@@ -489,8 +490,18 @@ class Sim(_Handle):
         """(current schedule, availability mask [SCHED_COUNT])."""
         cur = np.zeros(1, np.int32)
         av = np.zeros(SCHED_COUNT, np.int32)
-        _check(lib().mss_sim_get_schedule(self._h, _ptr(cur), _ptr(av)))
+        _check(lib().mss_sim_get_schedule(self._h, _ptr(cur), _ptr(av), None))
         return int(cur[0]), av
+
+    def set_tile(self, source_tile: int = 0, tc_sources: int = 0, groups: int = 0):
+        _check(lib().mss_sim_set_tile(self._h, int(source_tile), int(tc_sources), int(groups)))
+
+    def tile(self):
+        """(CUDA-core source tile, split tensor-core sources per CTA, streamed-kernel groups)."""
+        t = np.zeros(3, np.int32)
+        cur = np.zeros(1, np.int32)
+        _check(lib().mss_sim_get_schedule(self._h, _ptr(cur), None, _ptr(t)))
+        return tuple(int(x) for x in t)
 
     def autotune(self, n_steps: int = 32, stream=None):
         """Time every available schedule, keep the fastest; returns (chosen, ms per step)."""

@@ -497,6 +497,8 @@ struct mss_sim {
   int tcp_krmax = 8, tcp_slots = 1;
   int tcq_nt = 0, tcq_grid = 1;                // warp-specialised persistent tensor-core kernel
   size_t tcq_smem = 0;
+  int tc_kpmax = 16, st_max = 1, dev_smem = 0;
+  bool stream_blob = false;                    // streamed-kernel coefficient copy present
   mss::TcArgs tca{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
@@ -791,7 +793,7 @@ static void step_impl(mss_sim &s, int64_t n, const double *w, void *traces, int 
     // capture and replay on the sim's own stream (the legacy stream cannot be captured)
     MSS_CUDA(cudaEventRecord(s.ev_in, st));
     MSS_CUDA(cudaStreamWaitEvent(s.cap, s.ev_in, 0));
-    GraphKey key{n, w, traces, s.cur, s.sched, s.stream_groups};
+    GraphKey key{n, w, traces, s.cur, s.sched, s.stream_groups + 8 * s.ST + 4096 * s.tcs_nt};
     auto it = s.graphs.find(key);
     if (it == s.graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -967,6 +969,37 @@ static void build_tc_blob(const Rom &R, std::vector<uint16_t> &blob, std::vector
   }
 }
 
+// Sizes that depend on the CUDA-core source tile ST (every per-column result is independent of
+// the tiling, so changing ST leaves the arithmetic of each source unchanged).
+static void apply_tile(mss_sim &s, int ST) {
+  const size_t es = s.prec == MSS_FP64 ? 8 : 4;
+  s.ST = ST;
+  s.tiles = (s.n_src + ST - 1) / ST;
+  s.cell_smem = 2 * (size_t)s.max_m * s.max_K * ST * es + 8 * (size_t)s.max_K;
+  s.corner_smem = std::max<size_t>(16, (size_t)s.max_nm * (ST + s.max_M) * es);
+  s.face_smem = std::max<size_t>(16, (2 * (size_t)s.max_M * ST + (size_t)s.max_M * s.max_M +
+                                      (s.corners ? (size_t)s.max_nm * s.max_M : 0)) * es);
+  s.split_smem = (size_t)s.max_K * ST * es + 8 * (size_t)s.max_K;
+  s.stream_ok = s.stream_blob && ST == kStreamST;
+}
+
+// Sizes and residency of the split / pipelined tensor-core kernels with NT sources per CTA.
+static void apply_tcs_nt(mss_sim &s, int nt) {
+  s.tcs_nt = nt;
+  s.tcs_smem = tcs_smem_bytes(nt, s.tc_kpmax);
+  s.tcp_smem = tcp_smem_bytes(nt, s.tc_kpmax, s.tcp_krmax);
+  int sms = 0, per = 0;
+  MSS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device));
+  const void *kf = nt == 16 ? (const void *)k_tc_pipe<16, true>
+                   : nt == 32 ? (const void *)k_tc_pipe<32, true>
+                   : nt == 64 ? (const void *)k_tc_pipe<64, true>
+                              : (const void *)k_tc_pipe<128, true>;
+  MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tcp_smem));
+  MSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kf, kTcsThreads, s.tcp_smem));
+  // at most 2 resident CTAs per SM keeps TMEM at <= 2 x 128 columns
+  s.tcp_slots = std::max(1, std::min(per, 2)) * sms;
+}
+
 static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corners) {
   MSS_REQUIRE(prec == MSS_FP64 || prec == MSS_FP32 || prec == MSS_FP32_TC || prec == MSS_BF16_TC, MSS_ERR_INVALID_ARG,
               "precision must be MSS_FP64, MSS_FP32, MSS_FP32_TC or MSS_BF16_TC");
@@ -1018,22 +1051,12 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
                 "cells too large for the tensor-core kernel");
     s.tc_nt = nt;
     s.tc_smem = smem_of(nt);
-    s.tcs_nt = S <= 16 ? 16 : S <= 32 ? 32 : S <= 64 ? 64 : 128;
-    s.tcs_smem = tcs_smem_bytes(s.tcs_nt, kpmax);
+    s.tc_kpmax = kpmax;
     for (int K : R.cell_K) s.tcp_krmax = std::max(s.tcp_krmax, (K + 7) / 8 * 8);
-    s.tcp_smem = tcp_smem_bytes(s.tcs_nt, kpmax, s.tcp_krmax);
+    apply_tcs_nt(s, S <= 16 ? 16 : S <= 32 ? 32 : S <= 64 ? 64 : 128);
     {
-      // resident CTAs of the pipelined kernels (shared memory bound; at most 2 per SM keeps
-      // TMEM at <= 2 x 128 columns)
-      int sms = 0, per = 0;
+      int sms = 0;
       MSS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device));
-      const void *kf = s.tcs_nt == 16 ? (const void *)k_tc_pipe<16, true>
-                       : s.tcs_nt == 32 ? (const void *)k_tc_pipe<32, true>
-                       : s.tcs_nt == 64 ? (const void *)k_tc_pipe<64, true>
-                                        : (const void *)k_tc_pipe<128, true>;
-      MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tcp_smem));
-      MSS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kf, kTcsThreads, s.tcp_smem));
-      s.tcp_slots = std::max(1, std::min(per, 2)) * sms;
       // warp-specialised persistent kernel: 32-source tiles when they fit, else 16
       for (int ntv : {32, 16}) {
         if (ntv == 32 && S <= 16) continue;
@@ -1147,6 +1170,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
       s.sca.coef_off = s.d.sc_off.as<int64_t>();
       s.sca.Kq = s.d.sc_Kq.as<int32_t>();
       s.stream_smem = need;
+      s.stream_blob = true;
       s.stream_ok = true;
     }
   }
@@ -1221,8 +1245,9 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   }
   s.n_cfaces = (int)cfaces.size();
   s.corner_smem = std::max<size_t>(16, (size_t)s.max_nm * (s.ST + s.max_M) * es);
-  s.face_smem = std::max<size_t>(16, (2 * (size_t)s.max_M * s.ST + (size_t)s.max_M * s.max_M +
-                                      (s.corners ? (size_t)s.max_nm * s.max_M : 0)) * es);
+  s.dev_smem = dev_smem;
+  s.st_max = s.ST;
+  apply_tile(s, s.ST);
   SimDev &d = s.d;
   upload(d.cell_K, R.cell_K);
   upload(d.cell_m, R.cell_m);
@@ -1533,12 +1558,41 @@ mss_status mss_sim_set_schedule(mss_sim *s, int32_t sched) {
   });
 }
 
-mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *available) {
+mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources, int32_t groups) {
+  return guard([&] {
+    MSS_REQUIRE(s, MSS_ERR_INVALID_ARG, "null argument");
+    if (source_tile > 0) {
+      MSS_REQUIRE(source_tile <= s->st_max && (source_tile & (source_tile - 1)) == 0, MSS_ERR_INVALID_ARG,
+                  "source tile must be a power of two up to the sim's largest");
+      apply_tile(*s, source_tile);
+      if (!sched_allowed(*s, s->sched)) s->sched = MSS_SCHED_GRAPH;
+    }
+    if (tc_sources > 0) {
+      MSS_REQUIRE(s->tc, MSS_ERR_INVALID_ARG, "tensor-core tile on a CUDA-core sim");
+      MSS_REQUIRE(tc_sources == 16 || tc_sources == 32 || tc_sources == 64 || tc_sources == 128, MSS_ERR_INVALID_ARG,
+                  "tensor-core tile must be 16, 32, 64 or 128 sources");
+      MSS_REQUIRE(tcs_smem_bytes(tc_sources, s->tc_kpmax) <= (size_t)s->dev_smem, MSS_ERR_INVALID_ARG,
+                  "tensor-core tile too large for shared memory");
+      apply_tcs_nt(*s, tc_sources);
+    }
+    if (groups > 0) {
+      MSS_REQUIRE(groups == 2 || groups == 4, MSS_ERR_INVALID_ARG, "thread groups must be 2 or 4");
+      s->stream_groups = groups;
+    }
+  });
+}
+
+mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *available, int32_t *tile) {
   return guard([&] {
     MSS_REQUIRE(s && sched, MSS_ERR_INVALID_ARG, "null argument");
     *sched = s->sched;
     if (available)
       for (int k = 0; k < MSS_SCHED_COUNT; ++k) available[k] = sched_allowed(*s, k) ? 1 : 0;
+    if (tile) {
+      tile[0] = s->ST;
+      tile[1] = s->tc ? s->tcs_nt : 0;
+      tile[2] = s->stream_groups;
+    }
   });
 }
 
@@ -1561,6 +1615,7 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
     MSS_CUDA(cudaMemset(w.p, 0, (size_t)n * 8));
     tr.alloc((size_t)n * std::max(1, s->n_rcv) * s->n_src * es);
     const int cur0 = s->cur, sched0 = s->sched;
+    const int st_keep = s->ST, nt_keep = s->tcs_nt, g_keep = s->stream_groups;
     const int64_t steps0 = s->steps;
     cudaEvent_t e0, e1;
     MSS_CUDA(cudaEventCreate(&e0));
@@ -1574,44 +1629,75 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
       s->steps = steps0;
     };
     try {
-      int best_groups = s->stream_groups;
+      // candidates: every available schedule x its tile variants (CUDA-core source tile ST,
+      // tensor-core split N, streamed-kernel thread groups); every variant computes each source's
+      // columns with the same operations, so the choice does not change the arithmetic
+      struct Cand { int sched, st, nt, groups; };
+      std::vector<Cand> cands;
+      const int st0 = s->ST, nt0 = s->tcs_nt, g0 = s->stream_groups;
       for (int k = 0; k < MSS_SCHED_COUNT; ++k) {
         if (ms) ms[k] = -1.0;
         if (!sched_allowed(*s, k)) continue;
-        s->sched = k;
-        // the streamed cell kernel also has a block-size variant (2 or 4 column groups)
-        const bool streamed = k == MSS_SCHED_GRAPH_STREAM;
-        for (int gv : {4, 2}) {
-          if (!streamed && gv != 4) continue;
-          if (streamed) s->stream_groups = gv;
-          auto run = [&]() {
-            if (s->prec == MSS_FP64) step_dispatch<double>(*s, n, w.as<double>(), tr.p, 1, st);
-            else step_dispatch<float>(*s, n, w.as<double>(), tr.p, 1, st);
-          };
-          run();   // warm-up (and graph capture)
-          MSS_CUDA(cudaEventRecord(e0, st));
-          run();
-          MSS_CUDA(cudaEventRecord(e1, st));
-          MSS_CUDA(cudaEventSynchronize(e1));
-          float t = 0;
-          MSS_CUDA(cudaEventElapsedTime(&t, e0, e1));
-          int err = 0;
-          MSS_CUDA(cudaMemcpy(&err, s->d.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-          MSS_REQUIRE(err == 0, MSS_ERR_TIMEOUT, "a bounded wait gave up during autotuning");
-          const double per = t / (double)n;
-          if (ms && (ms[k] < 0 || per < ms[k])) ms[k] = per;
-          if (per < best) {
-            best = per;
-            best_k = k;
-            if (streamed) best_groups = gv;
+        if (!s->tc) {
+          const bool streamed = k == MSS_SCHED_GRAPH_STREAM || k == MSS_SCHED_PERSIST_STREAM;
+          for (int st : {s->st_max, s->st_max / 2}) {
+            if (st < 8 && st != s->st_max) continue;
+            if (streamed && st != kStreamST) continue;
+            if (k == MSS_SCHED_GRAPH_STREAM) {
+              for (int gv : {4, 2}) cands.push_back({k, st, nt0, gv});
+            } else {
+              cands.push_back({k, st, nt0, g0});
+            }
           }
-          restore();
+        } else if (k == MSS_SCHED_GRAPH_SPLIT || k == MSS_SCHED_PERSIST) {
+          for (int nt : {16, 32, 64, 128}) {
+            if (nt > 16 && nt / 2 >= s->n_src) continue;
+            if (tcs_smem_bytes(nt, s->tc_kpmax) > (size_t)s->dev_smem) continue;
+            cands.push_back({k, st0, nt, g0});
+          }
+        } else {
+          cands.push_back({k, st0, nt0, g0});
         }
       }
+      Cand best_c{sched0, st0, nt0, g0};
+      for (const Cand &c : cands) {
+        s->sched = c.sched;
+        if (c.st != s->ST) apply_tile(*s, c.st);
+        if (s->tc && c.nt != s->tcs_nt) apply_tcs_nt(*s, c.nt);
+        s->stream_groups = c.groups;
+        auto run = [&]() {
+          if (s->prec == MSS_FP64) step_dispatch<double>(*s, n, w.as<double>(), tr.p, 1, st);
+          else step_dispatch<float>(*s, n, w.as<double>(), tr.p, 1, st);
+        };
+        run();   // warm-up (and graph capture)
+        MSS_CUDA(cudaEventRecord(e0, st));
+        run();
+        MSS_CUDA(cudaEventRecord(e1, st));
+        MSS_CUDA(cudaEventSynchronize(e1));
+        float t = 0;
+        MSS_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        int err = 0;
+        MSS_CUDA(cudaMemcpy(&err, s->d.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        MSS_REQUIRE(err == 0, MSS_ERR_TIMEOUT, "a bounded wait gave up during autotuning");
+        const double per = t / (double)n;
+        if (ms && (ms[c.sched] < 0 || per < ms[c.sched])) ms[c.sched] = per;
+        if (per < best) {
+          best = per;
+          best_k = c.sched;
+          best_c = c;
+        }
+        restore();
+      }
+      if (best_c.st != s->ST) apply_tile(*s, best_c.st);
+      if (s->tc && best_c.nt != s->tcs_nt) apply_tcs_nt(*s, best_c.nt);
+      const int best_groups = best_c.groups;
       s->stream_groups = best_groups;
     } catch (...) {
       restore();
       s->sched = sched0;
+      if (s->ST != st_keep) apply_tile(*s, st_keep);
+      if (s->tc && s->tcs_nt != nt_keep) apply_tcs_nt(*s, nt_keep);
+      s->stream_groups = g_keep;
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       throw;

@@ -131,15 +131,25 @@ def test_autotune_keeps_state_and_picks_fastest(P):
     full = _run(P, sim, w, nst, 32, 4, P.FP32)
     sim.reset()
     a = _run(P, sim, w[:90], 90, 32, 4, P.FP32)
+    _, avail = sim.schedule()              # availability at the sim's initial tile
     chosen, ms = sim.autotune(16)
-    cur, avail = sim.schedule()
-    assert cur == chosen and avail[chosen]
+    cur, avail_after = sim.schedule()
+    assert cur == chosen and avail_after[chosen]
     times = {k: ms[k] for k in range(P.SCHED_COUNT) if avail[k]}
     assert all(t > 0 for t in times.values()) and all(ms[k] == -1 for k in range(P.SCHED_COUNT) if not avail[k])
     assert chosen == min(times, key=times.get)
+    assert sim.tile()[0] in (8, 16)
     assert sim.info()[3] == 90
     b = _run(P, sim, w[90:], nst - 90, 32, 4, P.FP32)
     assert np.array_equal(np.concatenate([a, b]), full)
+    # the tile variants do not change any source's arithmetic
+    for k in (P.SCHED_GRAPH, P.SCHED_GRAPH_SPLIT, P.SCHED_PERSIST):
+        for st in (16, 8, 4):
+            sim.reset()
+            sim.set_schedule(k)
+            sim.set_tile(source_tile=st)
+            assert sim.tile()[0] == st
+            assert np.array_equal(_run(P, sim, w, nst, 32, 4, P.FP32), full), (k, st)
 
 
 def test_streamed_kernel_full_launch_shape(P):
@@ -188,3 +198,26 @@ def test_tensor_core_fused_and_split_agree(P, n_src):
             assert _rel(outs[-1], ref) <= tol, (prec, k)
         for o in outs[1:]:
             assert np.array_equal(outs[0], o), (prec, _rel(o, outs[0]))
+
+
+def test_tensor_core_tiles(P):
+    """Split tensor-core products with 16..128 sources per CTA, against the oracle; every tile
+    within the bar, and the autotuner's pick among them."""
+    n_src = 150
+    topo, co, src, rcv = _case(n_src=n_src, seed=77)
+    tau, nst = 0.08, 80
+    w = synth.ricker(np.arange(nst) * tau, 0.6)
+    ref = _oracle(topo, co, src, rcv, n_src, 4, w, tau, nst)
+    sim = _sim(P, topo, co, src, rcv, n_src, 4, tau, P.FP32_TC)
+    outs = {}
+    for nt in (16, 32, 64, 128):
+        sim.reset()
+        sim.set_schedule(P.SCHED_GRAPH_SPLIT)
+        sim.set_tile(tc_sources=nt)
+        assert sim.tile()[1] == nt
+        outs[nt] = _run(P, sim, w, nst, n_src, 4, P.FP32_TC)
+        assert _rel(outs[nt], ref) <= 1e-3, nt
+    for nt in (32, 64, 128):
+        assert _rel(outs[nt], outs[16]) <= 1e-6, nt
+    chosen, ms = sim.autotune(8)
+    assert sim.tile()[1] in (16, 32, 64, 128) and ms[chosen] > 0
