@@ -181,10 +181,8 @@ __device__ bool cell_stream_item(const StepArgs<float> &a, const StreamArgs &t, 
 #pragma unroll
           for (int h = 0; h < CP / 4; ++h) {
             const float4 d = dp[4 * i + h];
-            acc[4 * h + 0] += gv * d.x;
-            acc[4 * h + 1] += gv * d.y;
-            acc[4 * h + 2] += gv * d.z;
-            acc[4 * h + 3] += gv * d.w;
+            fma2(acc[4 * h + 0], acc[4 * h + 1], gv, d.x, d.y);
+            fma2(acc[4 * h + 2], acc[4 * h + 3], gv, d.z, d.w);
           }
         }
       }

@@ -66,6 +66,15 @@ constexpr int kChunk = 8;      // coefficients loaded ahead per thread (register
 
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// d0 += a b0, d1 += a b1 as one paired FP32 FMA (fma.rn.f32x2): each lane rounds exactly like
+// a scalar FMA, half the instructions.
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a, float b0, float b1) {
+  asm("{\n .reg .b64 pa, pb, pc;\n mov.b64 pa, {%2, %2};\n mov.b64 pb, {%3, %4};\n mov.b64 pc, {%0, %1};\n"
+      " fma.rn.f32x2 pc, pa, pb, pc;\n mov.b64 {%0, %1}, pc;\n}"
+      : "+f"(d0), "+f"(d1)
+      : "f"(a), "f"(b0), "f"(b1));
+}
+
 // acc[s] = sum_c G[c*K] * X[c*ST + s] for the thread's output row (G already offset by the row).
 // The column stream of G is software-pipelined in registers: the next kChunk loads are issued
 // before the current kChunk values are consumed, and the chunk after that is prefetched into L2,
@@ -92,8 +101,13 @@ __device__ __forceinline__ void row_times_block(const T *__restrict__ G, int K, 
     for (int j = 0; j < kChunk; ++j) {
       if (c0 + j < K) {
         const T *x = X + (c0 + j) * ST;
+        if constexpr (std::is_same<T, float>::value && ST % 2 == 0) {
 #pragma unroll
-        for (int s = 0; s < ST; ++s) acc[s] += g[j] * x[s];
+          for (int s = 0; s < ST; s += 2) fma2(acc[s], acc[s + 1], g[j], x[s], x[s + 1]);
+        } else {
+#pragma unroll
+          for (int s = 0; s < ST; ++s) acc[s] += g[j] * x[s];
+        }
       }
     }
 #pragma unroll
