@@ -286,6 +286,19 @@ mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_
 #define MSS_SCHED_COUNT 5
 /* Errors: INVALID_ARG (schedule not available for this sim's precision, tile or cell sizes). */
 mss_status mss_sim_set_schedule(mss_sim *s, int32_t sched);
+/* Failure-path hooks for tests (they cannot fault: each only makes a bounded wait run out, after
+ * which the kernel records MSS_ERR_TIMEOUT in the sim's error word and returns):
+ *   MSS_DEBUG_GRID_EXTRA_ARRIVALS  the persistent CUDA-core kernel's grid barrier waits for
+ *                                  `value` CTAs beyond the grid (a missing neighbour);
+ *   MSS_DEBUG_TC_EXTRA_TX          the split tensor-core kernels' matrix barrier expects `value`
+ *                                  bytes beyond their copies.
+ * value 0 restores normal operation.  mss_sim_clear_error resets the error word (and the grid
+ * barrier) after a reported TIMEOUT; the state of the failed steps is undefined (reset or load a
+ * saved state).  Errors: INVALID_ARG, CUDA. */
+#define MSS_DEBUG_GRID_EXTRA_ARRIVALS 1
+#define MSS_DEBUG_TC_EXTRA_TX 2
+mss_status mss_sim_debug(mss_sim *s, int32_t knob, int32_t value);
+mss_status mss_sim_clear_error(mss_sim *s, void *stream);
 /* Tile of the step kernels (values <= 0 leave a field unchanged): CUDA-core source tile (a power
  * of two up to the one chosen at creation; 16 is needed by the streamed schedules, the schedule
  * falls back to GRAPH otherwise), sources per CTA of the split tensor-core kernels (16, 32, 64,

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libmss.so")
 FP64, FP32, FP32_TC, BF16_TC = 0, 1, 2, 3
 SCHED_GRAPH, SCHED_GRAPH_STREAM, SCHED_PERSIST, SCHED_PERSIST_STREAM, SCHED_GRAPH_SPLIT = 0, 1, 2, 3, 4
 SCHED_COUNT = 5
+DEBUG_GRID_EXTRA_ARRIVALS, DEBUG_TC_EXTRA_TX = 1, 2
 DIRICHLET, NEUMANN = 0, 1
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "KRYLOV_DEFLATION", 4: "LANCZOS_BREAKDOWN",
@@ -126,6 +127,8 @@ _SIGS = [
     ("mss_sim_set_schedule", C.c_int32, [_P, C.c_int32]),
     ("mss_sim_get_schedule", C.c_int32, [_P, _P, _P, _P]),
     ("mss_sim_set_tile", C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32]),
+    ("mss_sim_debug", C.c_int32, [_P, C.c_int32, C.c_int32]),
+    ("mss_sim_clear_error", C.c_int32, [_P, _P]),
     ("mss_sim_autotune", C.c_int32, [_P, C.c_int32, _P, _P, _P]),
     ("mss_surrogate_infer", C.c_int32, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
 ]
@@ -492,6 +495,13 @@ class Sim(_Handle):
         av = np.zeros(SCHED_COUNT, np.int32)
         _check(lib().mss_sim_get_schedule(self._h, _ptr(cur), _ptr(av), None))
         return int(cur[0]), av
+
+    def debug(self, knob: int, value: int):
+        """Failure-path test hooks (make a bounded device wait run out; see mss_sim_debug)."""
+        _check(lib().mss_sim_debug(self._h, int(knob), int(value)))
+
+    def clear_error(self, stream=None):
+        _check(lib().mss_sim_clear_error(self._h, _stream(stream)))
 
     def set_tile(self, source_tile: int = 0, tc_sources: int = 0, groups: int = 0):
         _check(lib().mss_sim_set_tile(self._h, int(source_tile), int(tc_sources), int(groups)))

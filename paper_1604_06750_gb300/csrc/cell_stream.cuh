@@ -32,6 +32,7 @@ struct StreamArgs {
   const int64_t *coef_off;  // per cell, floats
   const int32_t *Kq;
   int *err;                 // 1: an mbarrier wait timed out; 2: a grid barrier timed out
+  int extra_arrivals;       // failure-path test hook: arrivals a grid barrier waits for beyond the grid
 };
 
 // Wait for chunk c's slot; uniform over the CTA.  On failure the caller drains and returns.
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(128 * G, G == 4 ? 1 : 2) k_cell_s(const StepAr
 // Grid barrier for a cooperative launch.  bar[0] counts arrivals, bar[1] is the generation.
 // Returns false (uniformly over the CTA) if the wait exceeded kGridWaitNs or another CTA
 // recorded an error.
-__device__ __forceinline__ bool grid_sync(unsigned *bar, int *err) {
+__device__ __forceinline__ bool grid_sync(unsigned *bar, int *err, int extra = 0) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -261,7 +262,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, int *err) {
     const unsigned gen = *vgen;
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
+    if (arrived == gridDim.x - 1 + (unsigned)extra) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -312,20 +313,20 @@ __global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 3 : 2) k_persis
       }
       __syncthreads();
     }
-    if (!grid_sync(bar, t.err)) return;
+    if (!grid_sync(bar, t.err, t.extra_arrivals)) return;
     const int nfb = a.n_faces + n_rcv_items;
     for (int it = blockIdx.x; it < n_face_items; it += gridDim.x) {
       face_item<T, ST>(a, cur, it % nfb, it / nfb, w + step, traces + (int64_t)step * a.n_rcv * a.S, aux);
       __syncthreads();
     }
     if (n_corner > 0) {
-      if (!grid_sync(bar, t.err)) return;
+      if (!grid_sync(bar, t.err, t.extra_arrivals)) return;
       for (int it = blockIdx.x; it < n_corner; it += gridDim.x) {
         corner_item<T, ST>(a, cur, it % a.n_cfaces, it / a.n_cfaces, aux);
         __syncthreads();
       }
     }
-    if (!grid_sync(bar, t.err)) return;
+    if (!grid_sync(bar, t.err, t.extra_arrivals)) return;
     cur ^= 1;
   }
 }

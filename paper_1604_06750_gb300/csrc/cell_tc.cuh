@@ -34,6 +34,8 @@ struct TcArgs {
   int max_m;
   int terms;                   // 3: split BF16 (FP32-class products), 1: plain BF16
   unsigned tmem_cols;
+  unsigned extra_tx;           // failure-path test hook: bytes a split kernel's matrix barrier waits
+                               // for beyond its copies (the wait then runs out)
 };
 
 constexpr int kTcThreads = 256;

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<floa
   }
   __syncthreads();
   if (tid == 0) {
-    mbar_expect_tx(full, 2 * mat_half);
+    mbar_expect_tx(full, 2 * mat_half + t.extra_tx);
     bulk_g2s(smem_u32(Ah), src, mat_half, full);
     bulk_g2s(smem_u32(Al), src + mat_half, mat_half, full);
   }

@@ -1572,6 +1572,27 @@ mss_status mss_sim_set_schedule(mss_sim *s, int32_t sched) {
   });
 }
 
+mss_status mss_sim_debug(mss_sim *s, int32_t knob, int32_t value) {
+  return guard([&] {
+    MSS_REQUIRE(s && value >= 0, MSS_ERR_INVALID_ARG, "bad argument");
+    switch (knob) {
+      case MSS_DEBUG_GRID_EXTRA_ARRIVALS: s->sca.extra_arrivals = value; break;
+      case MSS_DEBUG_TC_EXTRA_TX: s->tca.extra_tx = (unsigned)value; break;
+      default: MSS_REQUIRE(false, MSS_ERR_INVALID_ARG, "unknown debug knob");
+    }
+  });
+}
+
+mss_status mss_sim_clear_error(mss_sim *s, void *stream) {
+  return guard([&] {
+    MSS_REQUIRE(s, MSS_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    MSS_CUDA(cudaMemsetAsync(s->d.tc_err.p, 0, sizeof(int), st));
+    MSS_CUDA(cudaMemsetAsync(s->d.bar.p, 0, 2 * sizeof(unsigned), st));
+    MSS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
 mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources, int32_t groups) {
   return guard([&] {
     MSS_REQUIRE(s, MSS_ERR_INVALID_ARG, "null argument");
