@@ -13,7 +13,9 @@
 // i.e. leading (K-direction) core stride 128 B, stride (row-direction) core stride 16 Kp B.
 // The coefficient matrices are stored in HBM already in this layout (rows rounded up to 8,
 // columns to 16, zero padded, hi then lo), so each one is a single 1-D TMA bulk copy
-// (cp.async.bulk) into a two-slot ring; the A tile is 128 rows (rows >= K stay zero).
+// (cp.async.bulk) into a two-slot ring of KrMax-row slots.  The MMA reads 128 rows from a slot;
+// rows at and beyond the cell's Kr are whatever follows in shared memory and only feed
+// accumulator rows >= K, which are never stored (E rows >= K are written as zero).
 // B = U^{k+1} - U^k (then E^k) is staged by the threads from FP32 state, split into hi/lo.
 // The MMA issuer is one thread; TMEM holds m accumulators of NT columns.  Every wait on an
 // mbarrier is bounded; on timeout the CTA records an error, drains its own copies (bounded),
@@ -29,7 +31,8 @@ struct TcArgs {
   const int64_t *blob_off;     // per cell, bytes
   const int32_t *Kp, *Kr;      // columns rounded up to 16, rows rounded up to 8
   int *err;                    // set to 1 by a CTA whose wait timed out
-  int slot_bytes;              // one A slot: hi + lo of 128 rows x KpMax
+  int slot_bytes;              // one A slot of the fused kernel: hi + lo of KrMax rows x KpMax
+  int kpmax, krmax;            // largest K rounded to 16 (columns) and to 8 (rows) over the cells
   int bbuf_bytes;              // one B buffer: hi + lo of NT rows x KpMax
   int max_m;
   int terms;                   // 3: split BF16 (FP32-class products), 1: plain BF16
@@ -165,7 +168,7 @@ __device__ __forceinline__ void transpose8(float (&v)[8], int lane) {
 }
 
 template <int NT>
-__global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float> a, const TcArgs t, const int cur) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_cell_tc(const StepArgs<float> a, const TcArgs t, const int cur) {
   const int tiles = (a.S + NT - 1) / NT;           // 1-D grid, tiles of a cell adjacent (L2 reuse)
   const int cell = blockIdx.x / tiles;
   const int s0 = (blockIdx.x % tiles) * NT;
@@ -176,8 +179,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float>
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char *slot[2] = {smem, smem + t.slot_bytes};
+  const unsigned lo_off = (unsigned)t.krmax * t.kpmax * 2;   // lo half of a slot
   unsigned char *bb = smem + 2 * t.slot_bytes;                 // B buffers: max_m x bbuf_bytes
-  int64_t *rows = reinterpret_cast<int64_t *>(bb + (size_t)t.max_m * t.bbuf_bytes);
+  // rows and barriers sit after a 128-row gap so that no 128-row A read reaches them
+  int64_t *rows = reinterpret_cast<int64_t *>(bb + (size_t)t.max_m * t.bbuf_bytes + (size_t)128 * t.kpmax * 2);
   uint64_t *bars = reinterpret_cast<uint64_t *>(rows + 128);   // full0 full1 empty0 empty1 done
   unsigned *tmem_base_sm = reinterpret_cast<unsigned *>(bars + 5);
   int *abort_sm = reinterpret_cast<int *>(tmem_base_sm + 1);
@@ -209,15 +214,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float>
     fence_mbar_init();
   }
   for (int r = tid; r < K; r += kTcThreads) rows[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
-  // zero the pad rows (Kr..127) of both slots (hi and lo); the copies never write them
-  for (int s = 0; s < 2; ++s) {
-    unsigned char *h = slot[s], *l = slot[s] + 256 * Kp;
-    const int pad0 = Kr * Kp * 2, pad1 = 128 * Kp * 2;
-    for (int i = pad0 / 16 + tid; i < pad1 / 16; i += kTcThreads) {
-      reinterpret_cast<int4 *>(h)[i] = make_int4(0, 0, 0, 0);
-      reinterpret_cast<int4 *>(l)[i] = make_int4(0, 0, 0, 0);
-    }
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -230,7 +226,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float>
     const unsigned char *src = cblob + (size_t)p * 2 * mat_half;
     mbar_expect_tx(full[sl], 2 * mat_half);
     bulk_g2s(smem_u32(slot[sl]), src, mat_half, full[sl]);
-    bulk_g2s(smem_u32(slot[sl] + 256 * Kp), src + mat_half, mat_half, full[sl]);
+    bulk_g2s(smem_u32(slot[sl] + lo_off), src + mat_half, mat_half, full[sl]);
   };
   if (tid == 0) {
     issue(0);
@@ -279,7 +275,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cell_tc(const StepArgs<float>
       if (!mbar_wait(full[sl], (p >> 1) & 1, t.err)) { *abort_sm = 1; break; }
       consumed = p + 1;
       tc_fence_after();
-      const unsigned ah = smem_u32(slot[sl]), al = ah + 256 * Kp;
+      const unsigned ah = smem_u32(slot[sl]), al = ah + lo_off;
       const unsigned bh = smem_u32(bb + (size_t)bi * t.bbuf_bytes), bl = bh + NT * Kp * 2;
       const unsigned dcol = tmem + (unsigned)(bi * NT);
       for (int kk = 0; kk < ksteps; ++kk) {

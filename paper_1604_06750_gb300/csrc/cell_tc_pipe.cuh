@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1) k_cell_tcp(const StepArgs<floa
   const int S = a.S;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int kpmax = (t.slot_bytes / 2) / (128 * 2);
+  const int kpmax = t.kpmax;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);      // full[4] empty[4] mdone
   int *ctl = reinterpret_cast<int *>(smem + 128);              // [0] tmem base, [1] ok, [2] copies issued,
                                                                // [3] copies consumed, [4] commits, [5] waited

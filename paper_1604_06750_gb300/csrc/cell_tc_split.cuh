@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<floa
   extern __shared__ __align__(128) unsigned char smem[];
   // layout: A hi (128 x KpMax), A lo, B hi (NT x KpMax), B lo, then barriers; the A halves and
   // the B halves are KpMax-strided so that one allocation serves every cell
-  const int kpmax = (t.slot_bytes / 2) / (128 * 2);
+  const int kpmax = t.kpmax;
   unsigned char *Ah = smem, *Al = smem + 128 * kpmax * 2;
   unsigned char *Bh = smem + 2 * 128 * kpmax * 2, *Bl = Bh + NT * kpmax * 2;
   uint64_t *bars = reinterpret_cast<uint64_t *>(Bl + NT * kpmax * 2);   // full, done
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kTcsThreads, 1) k_tc_pipe(const StepArgs<float
   const int S = a.S;
   const int tid = threadIdx.x, warp = tid >> 5;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int kpmax = (t.slot_bytes / 2) / (128 * 2);
+  const int kpmax = t.kpmax;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);    // full0, full1, done
   unsigned *tmem_sm = reinterpret_cast<unsigned *>(bars + 3);
   const size_t half = (size_t)krmax * kpmax * 2;

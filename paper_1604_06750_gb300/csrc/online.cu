@@ -1052,8 +1052,13 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
     int kpmax = 0;
     for (int K : R.cell_K) kpmax = std::max(kpmax, (K + 15) / 16 * 16);
     int nt = S <= 16 ? 16 : S <= 32 ? 32 : 64;
+    int krmax = 8;
+    for (int K : R.cell_K) krmax = std::max(krmax, (K + 7) / 8 * 8);
+    // two A slots of KrMax rows, max_m B buffers, rows, barriers, and a tail so that the 128-row
+    // reads of the last slot stay inside the allocation
     auto smem_of = [&](int ntv) {
-      return (size_t)2 * (2 * 128 * kpmax * 2) + (size_t)s.max_m * (2 * ntv * kpmax * 2) + 128 * 8 + 8 * 8;
+      return (size_t)2 * (2 * krmax * kpmax * 2) + (size_t)s.max_m * (2 * ntv * kpmax * 2) + 128 * 8 + 8 * 8 +
+             (size_t)128 * kpmax * 2;
     };
     auto cols_of = [&](int ntv) {
       unsigned c = 32;
@@ -1097,7 +1102,9 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
     s.tca.Kp = s.d.tc_Kp.as<int32_t>();
     s.tca.Kr = s.d.tc_Kr.as<int32_t>();
     s.tca.err = s.d.tc_err.as<int>();
-    s.tca.slot_bytes = 2 * 128 * kpmax * 2;
+    s.tca.slot_bytes = 2 * krmax * kpmax * 2;
+    s.tca.kpmax = kpmax;
+    s.tca.krmax = krmax;
     s.tca.bbuf_bytes = 2 * nt * kpmax * 2;
     s.tca.max_m = s.max_m;
     s.tca.terms = s.tc_terms;
