@@ -286,6 +286,13 @@ mss_status mss_sim_save_state(const mss_sim *s, double *now, double *old, int64_
 #define MSS_SCHED_COUNT 5
 /* Errors: INVALID_ARG (schedule not available for this sim's precision, tile or cell sizes). */
 mss_status mss_sim_set_schedule(mss_sim *s, int32_t sched);
+/* Stability (CFL) check of tau for this sim: n_steps source-free steps from a seeded random
+ * state with zero velocity through the sim's own kernels; growth = |u_n| / |u_0| (Euclidean,
+ * FP64 on the host).  Below the CFL limit the leapfrog conserves the discrete energy and the
+ * growth stays bounded; above it grows geometrically.  The sim's state and step counter are
+ * restored.  Errors: CFL (growth > max_growth or not finite), INVALID_ARG, CUDA. */
+mss_status mss_sim_check_stability(mss_sim *s, int32_t n_steps, uint64_t seed, double max_growth, double *growth,
+                                   void *stream);
 /* Failure-path hooks for tests (they cannot fault: each only makes a bounded wait run out, after
  * which the kernel records MSS_ERR_TIMEOUT in the sim's error word and returns):
  *   MSS_DEBUG_GRID_EXTRA_ARRIVALS  the persistent CUDA-core kernel's grid barrier waits for

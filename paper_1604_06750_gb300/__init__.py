@@ -128,6 +128,7 @@ _SIGS = [
     ("mss_sim_get_schedule", C.c_int32, [_P, _P, _P, _P]),
     ("mss_sim_set_tile", C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32]),
     ("mss_sim_debug", C.c_int32, [_P, C.c_int32, C.c_int32]),
+    ("mss_sim_check_stability", C.c_int32, [_P, C.c_int32, C.c_uint64, C.c_double, _P, _P]),
     ("mss_sim_clear_error", C.c_int32, [_P, _P]),
     ("mss_sim_autotune", C.c_int32, [_P, C.c_int32, _P, _P, _P]),
     ("mss_surrogate_infer", C.c_int32, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
@@ -495,6 +496,13 @@ class Sim(_Handle):
         av = np.zeros(SCHED_COUNT, np.int32)
         _check(lib().mss_sim_get_schedule(self._h, _ptr(cur), _ptr(av), None))
         return int(cur[0]), av
+
+    def check_stability(self, n_steps: int = 200, seed: int = 0, max_growth: float = 1e3, stream=None) -> float:
+        """Growth of the state norm over source-free steps; raises MssError (CFL) above max_growth."""
+        g = np.zeros(1)
+        _check(lib().mss_sim_check_stability(self._h, int(n_steps), C.c_uint64(seed), C.c_double(max_growth), _ptr(g),
+                                             _stream(stream)))
+        return float(g[0])
 
     def debug(self, knob: int, value: int):
         """Failure-path test hooks (make a bounded device wait run out; see mss_sim_debug)."""
