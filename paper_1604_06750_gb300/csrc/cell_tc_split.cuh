@@ -83,50 +83,76 @@ __device__ __forceinline__ void tcs_epilogue(const StepArgs<float> &a, const Spl
   const int S = a.S;
   const bool vec_ok = (S % 4) == 0;
   const float tau2 = a.tau2;
-  for (int cc = 0; cc < CH; cc += 8) {
-    float acc[8];
-    __syncwarp();
-    tc_ld8(tmem + lane_addr + (unsigned)(c0 + cc), acc);   // every lane loads; stores are predicated
-    if (r >= K) continue;
-    const int col = c0 + cc;
-    const bool full8 = vec_ok && col + 8 <= ns;
-    if (FLUX) {
-      float *o = p.F + (p.f_off[cell] + (int64_t)k * K + r) * S + s0 + col;
-      float *fo = k == 0 ? a.flux + (a.row_face_row[rp + r] * 2 + a.row_side[rp + r]) * S + s0 + col : nullptr;
-      if (full8) {
-        const float4 v0 = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        const float4 v1 = make_float4(acc[4], acc[5], acc[6], acc[7]);
-        reinterpret_cast<float4 *>(o)[0] = v0;
-        reinterpret_cast<float4 *>(o)[1] = v1;
-        if (fo) {
-          reinterpret_cast<float4 *>(fo)[0] = v0;
-          reinterpret_cast<float4 *>(fo)[1] = v1;
-        }
-      } else {
+  // U chunks of 8 columns per iteration: their TMEM loads, then all their global loads in flight
+  // together, then the arithmetic and the stores
+  constexpr int U = CH >= 32 ? 4 : CH / 8;
+  for (int cb = 0; cb < CH; cb += 8 * U) {
+    float acc[U][8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (col + e < ns) {
-            o[e] = acc[e];
-            if (fo) fo[e] = acc[e];
+    for (int u = 0; u < U; ++u) {
+      __syncwarp();
+      tc_ld8(tmem + lane_addr + (unsigned)(c0 + cb + 8 * u), acc[u]);   // every lane loads
+    }
+    if (r >= K) continue;
+    if (FLUX) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int col = c0 + cb + 8 * u;
+        const bool full8 = vec_ok && col + 8 <= ns;
+        float *o = p.F + (p.f_off[cell] + (int64_t)k * K + r) * S + s0 + col;
+        float *fo = k == 0 ? a.flux + (a.row_face_row[rp + r] * 2 + a.row_side[rp + r]) * S + s0 + col : nullptr;
+        if (full8) {
+          const float4 v0 = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+          const float4 v1 = make_float4(acc[u][4], acc[u][5], acc[u][6], acc[u][7]);
+          reinterpret_cast<float4 *>(o)[0] = v0;
+          reinterpret_cast<float4 *>(o)[1] = v1;
+          if (fo) {
+            reinterpret_cast<float4 *>(fo)[0] = v0;
+            reinterpret_cast<float4 *>(fo)[1] = v1;
           }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (col + e < ns) {
+              o[e] = acc[u][e];
+              if (fo) fo[e] = acc[u][e];
+            }
+        }
       }
     } else {
-      const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + col;
-      if (full8) {
+      const int64_t base0 = (so + (int64_t)(k - 1) * K + r) * S + s0 + c0 + cb;
+      if (vec_ok && c0 + cb + 8 * U <= ns) {
+        float4 nw[U][2], od[U][2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
-          float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
-          od.x = 2.f * nw.x - od.x + tau2 * acc[4 * h + 0];
-          od.y = 2.f * nw.y - od.y + tau2 * acc[4 * h + 1];
-          od.z = 2.f * nw.z - od.z + tau2 * acc[4 * h + 2];
-          od.w = 2.f * nw.w - od.w + tau2 * acc[4 * h + 3];
-          *reinterpret_cast<float4 *>(cso + base + 4 * h) = od;
-        }
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            nw[u][h] = *reinterpret_cast<const float4 *>(cs + base0 + 8 * u + 4 * h);
+            od[u][h] = *reinterpret_cast<const float4 *>(cso + base0 + 8 * u + 4 * h);
+          }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float4 o = od[u][h];
+            const float4 n = nw[u][h];
+            o.x = 2.f * n.x - o.x + tau2 * acc[u][4 * h + 0];
+            o.y = 2.f * n.y - o.y + tau2 * acc[u][4 * h + 1];
+            o.z = 2.f * n.z - o.z + tau2 * acc[u][4 * h + 2];
+            o.w = 2.f * n.w - o.w + tau2 * acc[u][4 * h + 3];
+            *reinterpret_cast<float4 *>(cso + base0 + 8 * u + 4 * h) = o;
+          }
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (col + e < ns) cso[base + e] = 2.f * cs[base + e] - cso[base + e] + tau2 * acc[e];
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int col = c0 + cb + 8 * u + e;
+            if (col < ns) {
+              const int64_t i = base0 + 8 * u + e;
+              cso[i] = 2.f * cs[i] - cso[i] + tau2 * acc[u][e];
+            }
+          }
       }
     }
   }
