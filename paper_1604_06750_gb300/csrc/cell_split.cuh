@@ -35,6 +35,8 @@ __global__ void __launch_bounds__(kSplitThreads, 8) k_flux(const StepArgs<T> a, 
   const T *fs = cur ? a.fstate1 : a.fstate0;
   const T *cs = cur ? a.cstate1 : a.cstate0;
   const int64_t rp = a.cell_row[cell], so = a.cell_state[cell];
+  const T *G = a.coef + a.cell_coef[cell] + (size_t)q * K * K;
+  if (s0 == 0) prefetch_l2_range(G, sizeof(T) * (size_t)K * K);
   if (q == 0)
     for (int r = threadIdx.x; r < K; r += blockDim.x) rows[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
   __syncthreads();
@@ -50,7 +52,6 @@ __global__ void __launch_bounds__(kSplitThreads, 8) k_flux(const StepArgs<T> a, 
     D[i] = v;
   }
   __syncthreads();
-  const T *G = a.coef + a.cell_coef[cell] + (size_t)q * K * K;
   T *Fo = p.F + (p.f_off[cell] + (int64_t)q * K) * S + s0;
   for (int r = threadIdx.x; r < K; r += blockDim.x) {
     T acc[ST];
@@ -81,12 +82,13 @@ __global__ void __launch_bounds__(kSplitThreads, 8) k_accel(const StepArgs<T> a,
   T *cso = cur ? a.cstate0 : a.cstate1;
   const int64_t so = a.cell_state[cell];
   const T *Fk = p.F + (p.f_off[cell] + (int64_t)k * K) * S + s0;
+  const T *H = a.coef + a.cell_ghat[cell] + (size_t)(k - 1) * K * K;
+  if (s0 == 0) prefetch_l2_range(H, sizeof(T) * (size_t)K * K);
   for (int i = threadIdx.x; i < K * ST; i += blockDim.x) {
     const int r = i / ST, s = i - r * ST;
     E[i] = s < ns ? Fk[(int64_t)r * S + s] - Fk[(int64_t)(r - K) * S + s] : T(0);
   }
   __syncthreads();
-  const T *H = a.coef + a.cell_ghat[cell] + (size_t)(k - 1) * K * K;
   const T tau2 = a.tau2;
   for (int r = threadIdx.x; r < K; r += blockDim.x) {
     T acc[ST];

@@ -64,7 +64,20 @@ constexpr int kCellThreads = 256;
 constexpr int kFaceThreads = 128;
 constexpr int kChunk = 8;      // coefficients loaded ahead per thread (register pipeline)
 
-__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+// Bulk prefetch of [p, p + bytes) into L2 (cp.async.bulk.prefetch), trimmed inward to 16-byte
+// boundaries, in 32 KB pieces issued by the first threads of the block.  Nothing outside the range
+// is touched.
+__device__ __forceinline__ void prefetch_l2_range(const void *p, size_t bytes) {
+  constexpr uintptr_t kPiece = 32768;
+  const uintptr_t lo = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  const uintptr_t hi = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  const uintptr_t at = lo + (uintptr_t)threadIdx.x * kPiece;
+  if (lo < hi && at < hi) {
+    const unsigned n = (unsigned)(hi - at < kPiece ? hi - at : kPiece);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(at), "r"(n) : "memory");
+  }
+}
+
 
 // d0 += a b0, d1 += a b1 as one paired FP32 FMA (fma.rn.f32x2): each lane rounds exactly like
 // a scalar FMA, half the instructions.
@@ -86,15 +99,9 @@ __device__ __forceinline__ void row_times_block(const T *__restrict__ G, int K, 
   for (int s = 0; s < ST; ++s) acc[s] = T(0);
   T g[kChunk], gn[kChunk];
 #pragma unroll
-  for (int j = 0; j < 2 * kChunk; ++j)
-    if (kChunk + j < K) prefetch_l2(G + (size_t)(kChunk + j) * K);
-#pragma unroll
   for (int j = 0; j < kChunk; ++j) g[j] = j < K ? __ldg(G + (size_t)j * K) : T(0);
   for (int c0 = 0; c0 < K; c0 += kChunk) {
     const int c1 = c0 + kChunk;
-#pragma unroll
-    for (int j = 0; j < kChunk; ++j)
-      if (c1 + 2 * kChunk + j < K) prefetch_l2(G + (size_t)(c1 + 2 * kChunk + j) * K);
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) gn[j] = (c1 + j < K) ? __ldg(G + (size_t)(c1 + j) * K) : T(0);
 #pragma unroll
@@ -138,6 +145,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
   const int64_t rp = a.cell_row[cell];
   const int64_t so = a.cell_state[cell];
   const int S = a.S;
+  if (tile == 0) prefetch_l2_range(a.coef + a.cell_coef[cell], sizeof(T) * (size_t)(2 * m - 1) * K * K);
   for (int r = threadIdx.x; r < K; r += blockDim.x) rows[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
   __syncthreads();
   using V = typename Vec<T>::type;
