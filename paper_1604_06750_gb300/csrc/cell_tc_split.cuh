@@ -23,11 +23,14 @@ __host__ __device__ constexpr size_t tcs_smem_bytes(int NT, int kpmax) {
 
 // B operand of one split product into the core layout (hi, lo): D^k = U^{k+1} - U^k for the
 // flux, E^k = F^k - F^{k-1} for the acceleration; rows >= K zero.  Lanes run over sources
-// (coalesced loads); each warp takes two 8-row groups per pass so that 32 loads are in flight.
+// (coalesced loads); each warp takes kStageRounds 8-row groups per round and issues all their
+// loads (two per element, 64 per thread) before any conversion.  rows_sm holds
+// the cell's face rows (face row * 2 + side) and is read for the flux of k = 0 only.
+constexpr int kStageRounds = 4;
 template <int NT, bool FLUX>
 __device__ __forceinline__ void tcs_stage_b(const StepArgs<float> &a, const float *Fk, const float *fs, const float *cs,
-                                            int64_t rp, int64_t so, int k, int m, int K, int Kp, int s0, int ns,
-                                            unsigned char *Bh, unsigned char *Bl) {
+                                            const int64_t *rows_sm, int64_t so, int k, int m, int K, int Kp, int s0,
+                                            int ns, unsigned char *Bh, unsigned char *Bl) {
   constexpr int CPW = NT < 32 ? NT : 32;
   constexpr int RPW = 32 / CPW;
   const int S = a.S;
@@ -35,45 +38,70 @@ __device__ __forceinline__ void tcs_stage_b(const StepArgs<float> &a, const floa
   const int NR8 = Kp / 8, ngp = (NR8 + RPW - 1) / RPW, cblocks = NT / CPW;
   const int cl = lane % CPW, sub = lane / CPW;
   const int passes = ngp * cblocks;
-  auto load8 = [&](int tt, float (&v)[8], int &off) -> bool {
+  // Branch-free loads: every element of a round is loaded (masked-off ones from a safe address
+  // and dropped by a select) before any is converted, so all the round's loads are in flight.
+  const float *dummy = cs;
+  auto load8 = [&](int tt, float (&x0)[8], float (&x1)[8], unsigned &mask, int &off) -> bool {
     const int cb = tt % cblocks, gp = tt / cblocks;
     const int g8 = gp * RPW + sub, c = cb * CPW + cl;
     if (tt >= passes || g8 >= NR8) return false;
+    const int r0 = g8 * 8;
+    mask = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int r = g8 * 8 + i;
-      float x = 0.f;
-      if (r < K && c < ns) {
-        if (FLUX) {
-          const float u0 = k == 0 ? fs[(a.row_face_row[rp + r]) * S + s0 + c]
-                                  : cs[(so + (int64_t)(k - 1) * K + r) * S + s0 + c];
-          const float u1 = k + 1 < m ? cs[(so + (int64_t)k * K + r) * S + s0 + c] : 0.f;
-          x = u1 - u0;
-        } else {
-          x = Fk[(int64_t)r * S + c] - Fk[(int64_t)(r - K) * S + c];
-        }
+    for (int i = 0; i < 8; ++i) mask |= (r0 + i < K && c < ns) ? 1u << i : 0u;
+    if (FLUX) {
+      // lower level U^k (face rows for k = 0) and upper level U^{k+1} (zero past the last layer)
+      const bool has_hi = k + 1 < m;
+      const float *lo = cs + (so + (int64_t)(k - 1) * K + r0) * S + s0 + c;
+      const float *hi = cs + (so + (int64_t)k * K + r0) * S + s0 + c;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const bool ok = (mask >> i) & 1u;
+        const float *p0 = !ok ? dummy : k == 0 ? fs + (rows_sm[r0 + i] >> 1) * S + s0 + c : lo + (int64_t)i * S;
+        const float *p1 = ok && has_hi ? hi + (int64_t)i * S : dummy;
+        x0[i] = *p0;
+        x1[i] = *p1;
       }
-      v[i] = x;
+      if (!has_hi) mask |= 1u << 8;   // upper level is zero
+    } else {
+      const float *f1 = Fk + (int64_t)r0 * S + c;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const bool ok = (mask >> i) & 1u;
+        x1[i] = *(ok ? f1 + (int64_t)i * S : dummy);
+        x0[i] = *(ok ? f1 + (int64_t)(i - K) * S : dummy);
+      }
     }
-    off = (int)core_off(c, g8 * 8, Kp);
+    off = (int)core_off(c, r0, Kp);
     return true;
   };
-  for (int tt = warp; tt < passes; tt += 2 * nw) {
-    float va[8], vb[8];
-    int oa = 0, ob = 0;
-    const bool ha = load8(tt, va, oa), hb = load8(tt + nw, vb, ob);
-    if (ha) store_core8(Bh, Bl, (unsigned)oa, va);
-    if (hb) store_core8(Bh, Bl, (unsigned)ob, vb);
+  for (int t0 = warp; t0 < passes; t0 += kStageRounds * nw) {
+    float x0[kStageRounds][8], x1[kStageRounds][8];
+    unsigned mask[kStageRounds];
+    int off[kStageRounds];
+    bool has[kStageRounds];
+#pragma unroll
+    for (int u = 0; u < kStageRounds; ++u) has[u] = load8(t0 + u * nw, x0[u], x1[u], mask[u], off[u]);
+#pragma unroll
+    for (int u = 0; u < kStageRounds; ++u)
+      if (has[u]) {
+        float v[8];
+        const bool zero_hi = (mask[u] >> 8) & 1u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = ((mask[u] >> i) & 1u) ? (zero_hi ? 0.f : x1[u][i]) - x0[u][i] : 0.f;
+        store_core8(Bh, Bl, (unsigned)off[u], v);
+      }
   }
 }
 
 // Epilogue of one split product: warp w reads TMEM lanes 32 (w % 4).. for the columns of half
-// w / 4; flux -> F scratch (and the face flux buffer for k = 0), acceleration -> leapfrog of
-// the hidden layer.  Two 8-column chunks per iteration keep their global loads in flight together.
+// w / 4; flux -> F scratch rows from f_row (and the face flux buffer for k = 0, rows from
+// rows_sm), acceleration -> leapfrog of the hidden layer.  Up to four 8-column chunks per
+// iteration keep their global loads in flight together; the row pointers are formed once.
 template <int NT, bool FLUX>
 __device__ __forceinline__ void tcs_epilogue(const StepArgs<float> &a, const SplitArgs<float> &p, unsigned tmem,
-                                             int cell, int k, int K, int s0, int ns, int64_t rp, int64_t so,
-                                             const float *cs, float *cso) {
+                                             int k, int K, int s0, int ns, int64_t f_row, const int64_t *rows_sm,
+                                             int64_t so, const float *cs, float *cso) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3, half = warp >> 2;
   const int r = 32 * q + lane;
@@ -83,6 +111,20 @@ __device__ __forceinline__ void tcs_epilogue(const StepArgs<float> &a, const Spl
   const int S = a.S;
   const bool vec_ok = (S % 4) == 0;
   const float tau2 = a.tau2;
+  const bool live = r < K;
+  float *orow = nullptr, *frow = nullptr;
+  const float *nrow = nullptr;
+  float *crow = nullptr;
+  if (live) {
+    if (FLUX) {
+      orow = p.F + (f_row + r) * S + s0;
+      if (k == 0) frow = a.flux + rows_sm[r] * S + s0;
+    } else {
+      const int64_t b = (so + (int64_t)(k - 1) * K + r) * S + s0;
+      nrow = cs + b;
+      crow = cso + b;
+    }
+  }
   // U chunks of 8 columns per iteration: their TMEM loads, then all their global loads in flight
   // together, then the arithmetic and the stores
   constexpr int U = CH >= 32 ? 4 : CH / 8;
@@ -93,15 +135,14 @@ __device__ __forceinline__ void tcs_epilogue(const StepArgs<float> &a, const Spl
       __syncwarp();
       tc_ld8(tmem + lane_addr + (unsigned)(c0 + cb + 8 * u), acc[u]);   // every lane loads
     }
-    if (r >= K) continue;
+    if (!live) continue;
     if (FLUX) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int col = c0 + cb + 8 * u;
-        const bool full8 = vec_ok && col + 8 <= ns;
-        float *o = p.F + (p.f_off[cell] + (int64_t)k * K + r) * S + s0 + col;
-        float *fo = k == 0 ? a.flux + (a.row_face_row[rp + r] * 2 + a.row_side[rp + r]) * S + s0 + col : nullptr;
-        if (full8) {
+        float *o = orow + col;
+        float *fo = frow ? frow + col : nullptr;
+        if (vec_ok && col + 8 <= ns) {
           const float4 v0 = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
           const float4 v1 = make_float4(acc[u][4], acc[u][5], acc[u][6], acc[u][7]);
           reinterpret_cast<float4 *>(o)[0] = v0;
@@ -120,15 +161,15 @@ __device__ __forceinline__ void tcs_epilogue(const StepArgs<float> &a, const Spl
         }
       }
     } else {
-      const int64_t base0 = (so + (int64_t)(k - 1) * K + r) * S + s0 + c0 + cb;
-      if (vec_ok && c0 + cb + 8 * U <= ns) {
+      const int cc = c0 + cb;
+      if (vec_ok && cc + 8 * U <= ns) {
         float4 nw[U][2], od[U][2];
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            nw[u][h] = *reinterpret_cast<const float4 *>(cs + base0 + 8 * u + 4 * h);
-            od[u][h] = *reinterpret_cast<const float4 *>(cso + base0 + 8 * u + 4 * h);
+            nw[u][h] = *reinterpret_cast<const float4 *>(nrow + cc + 8 * u + 4 * h);
+            od[u][h] = *reinterpret_cast<const float4 *>(crow + cc + 8 * u + 4 * h);
           }
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -140,18 +181,15 @@ __device__ __forceinline__ void tcs_epilogue(const StepArgs<float> &a, const Spl
             o.y = 2.f * n.y - o.y + tau2 * acc[u][4 * h + 1];
             o.z = 2.f * n.z - o.z + tau2 * acc[u][4 * h + 2];
             o.w = 2.f * n.w - o.w + tau2 * acc[u][4 * h + 3];
-            *reinterpret_cast<float4 *>(cso + base0 + 8 * u + 4 * h) = o;
+            *reinterpret_cast<float4 *>(crow + cc + 8 * u + 4 * h) = o;
           }
       } else {
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const int col = c0 + cb + 8 * u + e;
-            if (col < ns) {
-              const int64_t i = base0 + 8 * u + e;
-              cso[i] = 2.f * cs[i] - cso[i] + tau2 * acc[u][e];
-            }
+            const int col = cc + 8 * u + e;
+            if (col < ns) crow[col] = 2.f * nrow[col] - crow[col] + tau2 * acc[u][e];
           }
       }
     }
@@ -189,7 +227,10 @@ __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<floa
   while (cols < (unsigned)NT) cols <<= 1;
 
   __shared__ int bail;
+  __shared__ int64_t rows_sm[128];                   // face rows of the cell (flux of k = 0)
   if (tid == 0) bail = *(volatile const int *)t.err;
+  if (FLUX && k == 0)
+    for (int r = tid; r < K; r += kTcsThreads) rows_sm[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
   __syncthreads();
   if (bail) return;
   if (warp == 0) {
@@ -218,8 +259,9 @@ __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<floa
     }
   }
   // B: D^k = U^{k+1} - U^k (flux) or E^k = F^k - F^{k-1} (acceleration), rows >= K zero
-  const float *Fk = p.F + (p.f_off[cell] + (int64_t)k * K) * S + s0;
-  tcs_stage_b<NT, FLUX>(a, Fk, fs, cs, rp, so, k, m, K, Kp, s0, ns, Bh, Bl);
+  const int64_t f_row = p.f_off[cell] + (int64_t)k * K;
+  const float *Fk = p.F + f_row * S + s0;
+  tcs_stage_b<NT, FLUX>(a, Fk, fs, cs, rows_sm, so, k, m, K, Kp, s0, ns, Bh, Bl);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -252,7 +294,7 @@ __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<floa
   const bool go = ok_sm != 0;
   tc_fence_after();
   if (go) {
-    tcs_epilogue<NT, FLUX>(a, p, tmem, cell, k, K, s0, ns, rp, so, cs, cso);
+    tcs_epilogue<NT, FLUX>(a, p, tmem, k, K, s0, ns, f_row, rows_sm, so, cs, cso);
   } else if (tid == 0) {
     atomicExch(t.err, 1);
     // the A copies must land, and issued products finish, before shared memory and TMEM go away
@@ -304,6 +346,7 @@ __global__ void __launch_bounds__(kTcsThreads, 1) k_tc_pipe(const StepArgs<float
   while (cols < (unsigned)NT) cols <<= 1;
 
   __shared__ int bail, ok_sm;
+  __shared__ int64_t rows_sm[128];                   // face rows of the item's cell (flux of k = 0)
   if (tid == 0) bail = *(volatile const int *)t.err;
   __syncthreads();
   if (bail || (int)blockIdx.x >= total) return;
@@ -349,8 +392,13 @@ __global__ void __launch_bounds__(kTcsThreads, 1) k_tc_pipe(const StepArgs<float
     const int K = a.cell_K[cell], m = a.cell_m[cell], Kp = t.Kp[cell];
     const int ns = min(NT, S - s0);
     const int64_t rp = a.cell_row[cell], so = a.cell_state[cell];
-    const float *Fk = p.F + (p.f_off[cell] + (int64_t)k * K) * S + s0;
-    tcs_stage_b<NT, FLUX>(a, Fk, fs, cs, rp, so, k, m, K, Kp, s0, ns, Bh, Bl);
+    const int64_t f_row = p.f_off[cell] + (int64_t)k * K;
+    const float *Fk = p.F + f_row * S + s0;
+    if (FLUX && k == 0) {   // uniform over the CTA; the previous item's epilogue has synchronised
+      for (int r = tid; r < K; r += kTcsThreads) rows_sm[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
+      __syncthreads();
+    }
+    tcs_stage_b<NT, FLUX>(a, Fk, fs, cs, rows_sm, so, k, m, K, Kp, s0, ns, Bh, Bl);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -385,7 +433,7 @@ __global__ void __launch_bounds__(kTcsThreads, 1) k_tc_pipe(const StepArgs<float
       break;
     }
     tc_fence_after();
-    tcs_epilogue<NT, FLUX>(a, p, tmem, cell, k, K, s0, ns, rp, so, cs, cso);
+    tcs_epilogue<NT, FLUX>(a, p, tmem, k, K, s0, ns, f_row, rows_sm, so, cs, cso);
     tc_fence_before();
     __syncthreads();   // TMEM, the B buffer and this item's A slot are free again
   }
