@@ -403,6 +403,8 @@ def run_native(args):
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "fp64": {"value": units / t64, "unit": UNIT, "ms": 1e3 * t64},
             "fp32_tc": {"value": units / ttc, "unit": UNIT, "ms": 1e3 * ttc, "schedule": SCHED_NAMES[tc_sched],
+                        "autotune_ms_per_time_step": {SCHED_NAMES[k]: (float(tc_ms[k]) if tc_ms[k] >= 0 else None)
+                                                      for k in range(len(SCHED_NAMES))},
                         "kernel_ms": {"cell_phase": ms_tc[0], "k_face": ms_tc[1], "k_corner": ms_tc[2]},
                         "rel_l2_vs_fp64": rel(trtc_np, ref64),
                         "note": "tcgen05 cell products, BF16 hi/lo split operands (3 products), FP32 accumulation"},

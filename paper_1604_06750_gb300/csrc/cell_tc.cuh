@@ -42,6 +42,7 @@ struct TcArgs {
 };
 
 constexpr int kTcThreads = 256;
+constexpr int kStageRounds = 4;   // row groups per warp whose staging loads are in flight together
 constexpr unsigned long long kWaitNs = 100000000ull;   // 100 ms: a wait longer than this is declared hung
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -167,6 +168,126 @@ __device__ __forceinline__ void transpose8(float (&v)[8], int lane) {
   }
 }
 
+// B^k = U^{k+1} - U^k, k = 0..m-1 (U^0 = the cell's face rows, U^m = 0) of one (cell, source
+// tile) into the K-major core layout, split hi/lo: buffer k at bb + k * bstride, its lo half
+// lo_off bytes after the hi half; rows >= K zero.  Warp wi of nwarps stagers; lanes run over
+// sources (coalesced loads), each lane fills one 16-byte core row of 8 k values.  Branch-free:
+// every element of a round of kStageRounds row groups is loaded (masked-off ones from a safe
+// address, dropped by a select) before any is converted, so the round's loads are in flight
+// together.  rows[r] = face row * 2 + side of the cell's boundary row r.
+template <int NT>
+__device__ __forceinline__ void tc_stage_layers(const float *fs, const float *cs, const int64_t *rows, int64_t so,
+                                                int S, int s0, int ns, int K, int Kp, int m, unsigned char *bb,
+                                                size_t bstride, size_t lo_off, int wi, int nwarps, int lane) {
+  constexpr int CPW = NT < 32 ? NT : 32;        // sources per warp pass
+  constexpr int RPW = 32 / CPW;                 // 8-row groups per warp pass
+  const int NR8 = Kp / 8, ngp = (NR8 + RPW - 1) / RPW, cblocks = NT / CPW;
+  const int cl = lane % CPW, sub = lane / CPW;
+  const int passes = m * ngp * cblocks;
+  const float *dummy = cs;
+  auto load8 = [&](int tt, float (&x0)[8], float (&x1)[8], unsigned &mask, int &kb, int &off) -> bool {
+    if (tt >= passes) return false;
+    const int cb = tt % cblocks, t2 = tt / cblocks;
+    const int gp = t2 % ngp, k = t2 / ngp;
+    const int g8 = gp * RPW + sub, c = cb * CPW + cl;
+    if (g8 >= NR8) return false;
+    const int r0 = g8 * 8;
+    mask = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mask |= (r0 + i < K && c < ns) ? 1u << i : 0u;
+    const bool has_hi = k + 1 < m;
+    const float *lo = cs + (so + (int64_t)(k - 1) * K + r0) * S + s0 + c;
+    const float *hi = cs + (so + (int64_t)k * K + r0) * S + s0 + c;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const bool ok = (mask >> i) & 1u;
+      const float *p0 = !ok ? dummy : k == 0 ? fs + (rows[r0 + i] >> 1) * S + s0 + c : lo + (int64_t)i * S;
+      const float *p1 = ok && has_hi ? hi + (int64_t)i * S : dummy;
+      x0[i] = *p0;
+      x1[i] = *p1;
+    }
+    if (!has_hi) mask |= 1u << 8;   // upper level is zero
+    kb = k;
+    off = (int)core_off(c, r0, Kp);
+    return true;
+  };
+  for (int t0 = wi; t0 < passes; t0 += kStageRounds * nwarps) {
+    float x0[kStageRounds][8], x1[kStageRounds][8];
+    unsigned mask[kStageRounds];
+    int kb[kStageRounds], off[kStageRounds];
+    bool has[kStageRounds];
+#pragma unroll
+    for (int u = 0; u < kStageRounds; ++u) has[u] = load8(t0 + u * nwarps, x0[u], x1[u], mask[u], kb[u], off[u]);
+#pragma unroll
+    for (int u = 0; u < kStageRounds; ++u)
+      if (has[u]) {
+        float v[8];
+        const bool zero_hi = (mask[u] >> 8) & 1u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = ((mask[u] >> i) & 1u) ? (zero_hi ? 0.f : x1[u][i]) - x0[u][i] : 0.f;
+        unsigned char *h = bb + (size_t)kb[u] * bstride;
+        store_core8(h, h + lo_off, (unsigned)off[u], v);
+      }
+  }
+}
+
+// Hidden-layer leapfrog U^k <- 2 U^k - U^k_old + tau^2 (Gamma-hat^k E^k), k = 2..m, from the
+// accumulators of acceleration product k-1 at TMEM columns (k-2) NT.. : accumulator row r (the
+// thread's TMEM lane), columns c0 .. c0 + CH - 1 of the tile.  TMEM loads in every lane; up to four
+// 8-column chunks per iteration keep their global loads in flight together.
+template <int NT, int CH>
+__device__ __forceinline__ void tc_leapfrog(unsigned tmem, unsigned lane_addr, const float *cs, float *cso,
+                                            int64_t so, int K, int S, int s0, int ns, int m, int r, int c0,
+                                            float tau2) {
+  constexpr int U = CH >= 32 ? 4 : CH / 8;
+  const bool vec_ok = (S % 4) == 0;
+  for (int k = 1; k < m; ++k) {
+    const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + c0;
+    for (int cb = 0; cb < CH; cb += 8 * U) {
+      float acc[U][8];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        __syncwarp();
+        tc_ld8(tmem + lane_addr + (unsigned)((k - 1) * NT + c0 + cb + 8 * u), acc[u]);
+      }
+      if (r >= K) continue;
+      const float *nrow = cs + base + cb;
+      float *crow = cso + base + cb;
+      if (vec_ok && c0 + cb + 8 * U <= ns) {
+        float4 nw[U][2], od[U][2];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            nw[u][h] = *reinterpret_cast<const float4 *>(nrow + 8 * u + 4 * h);
+            od[u][h] = *reinterpret_cast<const float4 *>(crow + 8 * u + 4 * h);
+          }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float4 o = od[u][h];
+            const float4 n = nw[u][h];
+            o.x = 2.f * n.x - o.x + tau2 * acc[u][4 * h + 0];
+            o.y = 2.f * n.y - o.y + tau2 * acc[u][4 * h + 1];
+            o.z = 2.f * n.z - o.z + tau2 * acc[u][4 * h + 2];
+            o.w = 2.f * n.w - o.w + tau2 * acc[u][4 * h + 3];
+            *reinterpret_cast<float4 *>(crow + 8 * u + 4 * h) = o;
+          }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (c0 + cb + 8 * u + j < ns) {
+              const int e = 8 * u + j;
+              crow[e] = 2.f * nrow[e] - crow[e] + tau2 * acc[u][j];
+            }
+      }
+    }
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(kTcThreads, 2) k_cell_tc(const StepArgs<float> a, const TcArgs t, const int cur) {
   const int tiles = (a.S + NT - 1) / NT;           // 1-D grid, tiles of a cell adjacent (L2 reuse)
@@ -233,34 +354,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_cell_tc(const StepArgs<float>
     issued = 1;
     if (nmat > 1) { issue(1); issued = 2; }
   }
-  // stage B = U^{k+1} - U^k, k = 0..m-1 (U^0 = faces, U^m = 0), hi/lo, K-major core layout:
-  // lanes run over sources (coalesced loads), each lane fills one 16-byte core row of 8 k values
-  {
-    constexpr int CPW = NT < 32 ? NT : 32;        // sources per warp pass
-    constexpr int RPW = 32 / CPW;                 // 8-row groups per warp pass
-    const int NR8 = Kp / 8, ngp = (NR8 + RPW - 1) / RPW, cblocks = NT / CPW;
-    const int cl = lane % CPW, sub = lane / CPW;
-    for (int tt = warp; tt < m * ngp * cblocks; tt += kTcThreads / 32) {
-      const int cb = tt % cblocks, t2 = tt / cblocks;
-      const int gp = t2 % ngp, k = t2 / ngp;
-      const int g8 = gp * RPW + sub, c = cb * CPW + cl;
-      if (g8 >= NR8) continue;
-      float v[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int r = g8 * 8 + i;
-        float x = 0.f;
-        if (r < K && c < ns) {
-          const float u0 = k == 0 ? fs[(rows[r] >> 1) * S + s0 + c] : cs[(so + (int64_t)(k - 1) * K + r) * S + s0 + c];
-          const float u1 = k + 1 < m ? cs[(so + (int64_t)k * K + r) * S + s0 + c] : 0.f;
-          x = u1 - u0;
-        }
-        v[i] = x;
-      }
-      unsigned char *h = bb + (size_t)k * t.bbuf_bytes;
-      store_core8(h, h + NT * Kp * 2, core_off(c, g8 * 8, Kp), v);
-    }
-  }
+  // stage B^k = U^{k+1} - U^k, k = 0..m-1 (U^0 = faces, U^m = 0)
+  tc_stage_layers<NT>(fs, cs, rows, so, S, s0, ns, K, Kp, m, bb, t.bbuf_bytes, (size_t)NT * Kp * 2, warp,
+                      kTcThreads / 32, lane);
   fence_async_smem();
   __syncthreads();
   const unsigned lbo = 128, sbo = 16u * Kp;
@@ -356,35 +452,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_cell_tc(const StepArgs<float>
   if (tid == 0 && go1 && m > 1) run_products(m, nmat);
   ok = (go1 && m > 1) ? mbar_wait(done, 1, t.err) : go1;
   tc_fence_after();
-  // epilogue 2: hidden-layer leapfrog (loads in every lane, stores for rows < K)
+  // epilogue 2: hidden-layer leapfrog
   const bool go2 = __syncthreads_and(ok && !*abort_sm) != 0;
   if (go2) {
-    const float tau2 = a.tau2;
-    for (int k = 1; k < m; ++k) {
-      for (int cc = 0; cc < NT / 2; cc += 8) {
-        float acc[8];
-        tc_ld8(tmem + lane_addr + (unsigned)((k - 1) * NT + c0 + cc), acc);
-        if (r < K) {
-          const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + c0 + cc;
-          if (vec_ok && c0 + cc + 8 <= ns) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
-              float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
-              od.x = 2.f * nw.x - od.x + tau2 * acc[4 * h + 0];
-              od.y = 2.f * nw.y - od.y + tau2 * acc[4 * h + 1];
-              od.z = 2.f * nw.z - od.z + tau2 * acc[4 * h + 2];
-              od.w = 2.f * nw.w - od.w + tau2 * acc[4 * h + 3];
-              *reinterpret_cast<float4 *>(cso + base + 4 * h) = od;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (c0 + cc + j < ns) cso[base + j] = 2.f * cs[base + j] - cso[base + j] + tau2 * acc[j];
-          }
-        }
-      }
-    }
+    tc_leapfrog<NT, NT / 2>(tmem, lane_addr, cs, cso, so, K, S, s0, ns, m, r, c0, a.tau2);
   } else if (tid == 0) {
     *abort_sm = 1;
   }

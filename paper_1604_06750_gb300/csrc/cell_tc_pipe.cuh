@@ -129,51 +129,9 @@ __global__ void __launch_bounds__(kTcpThreads, 1) k_cell_tcp(const StepArgs<floa
       const int64_t rp = a.cell_row[cell], so = a.cell_state[cell];
       for (int i = ct; i < K; i += kTcpCompute) rows[i] = a.row_face_row[rp + i] * 2 + a.row_side[rp + i];
       compute_bar();
-      // stage B^k = U^{k+1} - U^k, k = 0..m-1: lanes over sources, one 16-byte core row per lane,
-      // two passes per warp iteration so that 32 loads are in flight
-      {
-        constexpr int CPW = NT < 32 ? NT : 32;
-        constexpr int RPW = 32 / CPW;
-        const int NR8 = Kp / 8, ngp = (NR8 + RPW - 1) / RPW, cblocks = NT / CPW;
-        const int cl = lane % CPW, sub = lane / CPW;
-        const int passes = m * ngp * cblocks;
-        constexpr int NW = kTcpCompute / 32;
-        auto load8 = [&](int tt, float (&v)[8], unsigned &off, int &kk) -> bool {
-          if (tt >= passes) return false;
-          const int cb = tt % cblocks, t2 = tt / cblocks;
-          const int gp = t2 % ngp, k = t2 / ngp;
-          const int g8 = gp * RPW + sub, c = cb * CPW + cl;
-          if (g8 >= NR8) return false;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int rr = g8 * 8 + i;
-            float x = 0.f;
-            if (rr < K && c < ns) {
-              const float u0 = k == 0 ? fs[(rows[rr] >> 1) * S + s0 + c] : cs[(so + (int64_t)(k - 1) * K + rr) * S + s0 + c];
-              const float u1 = k + 1 < m ? cs[(so + (int64_t)k * K + rr) * S + s0 + c] : 0.f;
-              x = u1 - u0;
-            }
-            v[i] = x;
-          }
-          off = core_off(c, g8 * 8, Kp);
-          kk = k;
-          return true;
-        };
-        for (int tt = cw; tt < passes; tt += 2 * NW) {
-          float va[8], vb[8];
-          unsigned oa = 0, ob = 0;
-          int ka = 0, kb = 0;
-          const bool ha = load8(tt, va, oa, ka), hb = load8(tt + NW, vb, ob, kb);
-          if (ha) {
-            unsigned char *h = bbuf + (size_t)ka * bstride;
-            store_core8(h, h + NT * kpmax * 2, oa, va);
-          }
-          if (hb) {
-            unsigned char *h = bbuf + (size_t)kb * bstride;
-            store_core8(h, h + NT * kpmax * 2, ob, vb);
-          }
-        }
-      }
+      // stage B^k = U^{k+1} - U^k, k = 0..m-1
+      tc_stage_layers<NT>(fs, cs, rows, so, S, s0, ns, K, Kp, m, bbuf, bstride, (size_t)NT * kpmax * 2, cw,
+                          kTcpCompute / 32, lane);
       fence_async_smem();
       tc_fence_before();
       compute_bar();
@@ -277,33 +235,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1) k_cell_tcp(const StepArgs<floa
       if (!ctl[1]) break;
       tc_fence_after();
       // ---- hidden-layer leapfrog
-      for (int k = 1; k < m; ++k) {
-        for (int ch = 0; ch < CH; ch += 8) {
-          const int cc = c0 + ch;
-          float acc[8];
-          __syncwarp();
-          tc_ld8(tmem + lane_addr + (unsigned)((k - 1) * NT + cc), acc);
-          if (r < K) {
-            const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + cc;
-            if (vec_ok && cc + 8 <= ns) {
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
-                float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
-                od.x = 2.f * nw.x - od.x + tau2 * acc[4 * h + 0];
-                od.y = 2.f * nw.y - od.y + tau2 * acc[4 * h + 1];
-                od.z = 2.f * nw.z - od.z + tau2 * acc[4 * h + 2];
-                od.w = 2.f * nw.w - od.w + tau2 * acc[4 * h + 3];
-                *reinterpret_cast<float4 *>(cso + base + 4 * h) = od;
-              }
-            } else {
-#pragma unroll
-              for (int j = 0; j < 8; ++j)
-                if (cc + j < ns) cso[base + j] = 2.f * cs[base + j] - cso[base + j] + tau2 * acc[j];
-            }
-          }
-        }
-      }
+      tc_leapfrog<NT, CH>(tmem, lane_addr, cs, cso, so, K, S, s0, ns, m, r, c0, tau2);
       tc_fence_before();
       compute_bar();   // TMEM columns, B buffers and rows are free for the next item
     }

@@ -26,7 +26,6 @@ __host__ __device__ constexpr size_t tcs_smem_bytes(int NT, int kpmax) {
 // (coalesced loads); each warp takes kStageRounds 8-row groups per round and issues all their
 // loads (two per element, 64 per thread) before any conversion.  rows_sm holds
 // the cell's face rows (face row * 2 + side) and is read for the flux of k = 0 only.
-constexpr int kStageRounds = 4;
 template <int NT, bool FLUX>
 __device__ __forceinline__ void tcs_stage_b(const StepArgs<float> &a, const float *Fk, const float *fs, const float *cs,
                                             const int64_t *rows_sm, int64_t so, int k, int m, int K, int Kp, int s0,
