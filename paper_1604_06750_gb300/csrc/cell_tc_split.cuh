@@ -49,19 +49,27 @@ __device__ __forceinline__ void tcs_stage_b(const StepArgs<float> &a, const floa
 #pragma unroll
     for (int i = 0; i < 8; ++i) mask |= (r0 + i < K && c < ns) ? 1u << i : 0u;
     if (FLUX) {
-      // lower level U^k (face rows for k = 0) and upper level U^{k+1} (zero past the last layer)
+      // lower level U^k (face rows for k = 0) and upper level U^{k+1} (zero past the last layer);
+      // k and the upper layer's presence are uniform over the CTA
       const bool has_hi = k + 1 < m;
-      const float *lo = cs + (so + (int64_t)(k - 1) * K + r0) * S + s0 + c;
-      const float *hi = cs + (so + (int64_t)k * K + r0) * S + s0 + c;
+      if (k == 0) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const bool ok = (mask >> i) & 1u;
-        const float *p0 = !ok ? dummy : k == 0 ? fs + (rows_sm[r0 + i] >> 1) * S + s0 + c : lo + (int64_t)i * S;
-        const float *p1 = ok && has_hi ? hi + (int64_t)i * S : dummy;
-        x0[i] = *p0;
-        x1[i] = *p1;
+        for (int i = 0; i < 8; ++i)
+          x0[i] = *(((mask >> i) & 1u) ? fs + (rows_sm[r0 + i] >> 1) * S + s0 + c : dummy);
+      } else {
+        const float *lo = cs + (so + (int64_t)(k - 1) * K + r0) * S + s0 + c;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x0[i] = *(((mask >> i) & 1u) ? lo + (int64_t)i * S : dummy);
       }
-      if (!has_hi) mask |= 1u << 8;   // upper level is zero
+      if (has_hi) {
+        const float *hi = cs + (so + (int64_t)k * K + r0) * S + s0 + c;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x1[i] = *(((mask >> i) & 1u) ? hi + (int64_t)i * S : dummy);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x1[i] = 0.f;
+        mask |= 1u << 8;   // upper level is zero
+      }
     } else {
       const float *f1 = Fk + (int64_t)r0 * S + c;
 #pragma unroll
@@ -195,6 +203,106 @@ __device__ __forceinline__ void tcs_epilogue(const StepArgs<float> &a, const Spl
   }
 }
 
+// Epilogue through shared memory (k_tc_split, whose A and B buffers are free once its products
+// are done): the accumulator tile (K rows, NT sources) goes TMEM -> tile (row pitch NT + 4
+// floats: conflict-free 16-byte stores from lanes over rows), then the global traffic runs with
+// lanes over sources, coalesced along each row and four 16-byte vectors per thread in flight:
+// flux -> F scratch rows (and the face flux buffer for k = 0), acceleration -> leapfrog of the
+// hidden layer.  Same per-element arithmetic as tcs_epilogue.
+template <int NT, bool FLUX>
+__device__ __forceinline__ void tcs_epilogue_staged(const StepArgs<float> &a, const SplitArgs<float> &p,
+                                                    unsigned tmem, int k, int K, int s0, int ns, int64_t f_row,
+                                                    const int64_t *rows_sm, int64_t so, const float *cs, float *cso,
+                                                    float *tile) {
+  constexpr int LD = NT + 4;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3, half = warp >> 2;
+  const int r = 32 * q + lane;
+  const unsigned lane_addr = (unsigned)(32 * q) << 16;
+  constexpr int CH = NT / 2;
+  const int c0 = half * CH;
+  constexpr int U = CH >= 32 ? 4 : CH / 8;
+  fence_async_smem();   // the tile overwrites operands the tensor cores have finished reading
+  for (int cb = 0; cb < CH; cb += 8 * U) {
+    float acc[U][8];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      __syncwarp();
+      tc_ld8(tmem + lane_addr + (unsigned)(c0 + cb + 8 * u), acc[u]);
+    }
+    if (r < K) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float4 *d = reinterpret_cast<float4 *>(tile + r * LD + c0 + cb + 8 * u);
+        d[0] = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+        d[1] = make_float4(acc[u][4], acc[u][5], acc[u][6], acc[u][7]);
+      }
+    }
+  }
+  __syncthreads();
+  const int S = a.S;
+  const float tau2 = a.tau2;
+  if ((S % 4) == 0 && ns == NT) {
+    constexpr int VR = NT / 4;   // 16-byte vectors per row
+    constexpr int B4 = 4;        // vectors per thread in flight
+    const int total = K * VR;
+    for (int i0 = tid; i0 < total; i0 += B4 * kTcsThreads) {
+      if (FLUX) {
+#pragma unroll
+        for (int b = 0; b < B4; ++b) {
+          const int i = i0 + b * kTcsThreads;
+          if (i < total) {
+            const int rr = i / VR, v = i - rr * VR;
+            const float4 x = reinterpret_cast<const float4 *>(tile + rr * LD)[v];
+            reinterpret_cast<float4 *>(p.F + (f_row + rr) * S + s0)[v] = x;
+            if (k == 0) reinterpret_cast<float4 *>(a.flux + rows_sm[rr] * S + s0)[v] = x;
+          }
+        }
+      } else {
+        float4 nw[B4], od[B4];
+        int64_t at[B4];
+#pragma unroll
+        for (int b = 0; b < B4; ++b) {
+          const int i = i0 + b * kTcsThreads;
+          const bool ok = i < total;
+          const int rr = ok ? i / VR : 0, v = i - rr * VR;
+          at[b] = ok ? (so + (int64_t)(k - 1) * K + rr) * S + s0 + 4 * v : -1;
+          nw[b] = *reinterpret_cast<const float4 *>(ok ? cs + at[b] : cs);
+          od[b] = *reinterpret_cast<const float4 *>(ok ? cso + at[b] : cso);
+        }
+#pragma unroll
+        for (int b = 0; b < B4; ++b) {
+          const int i = i0 + b * kTcsThreads;
+          if (at[b] < 0) continue;
+          const int rr = i / VR, v = i - rr * VR;
+          const float4 x = reinterpret_cast<const float4 *>(tile + rr * LD)[v];
+          float4 o = od[b];
+          const float4 n = nw[b];
+          o.x = 2.f * n.x - o.x + tau2 * x.x;
+          o.y = 2.f * n.y - o.y + tau2 * x.y;
+          o.z = 2.f * n.z - o.z + tau2 * x.z;
+          o.w = 2.f * n.w - o.w + tau2 * x.w;
+          *reinterpret_cast<float4 *>(cso + at[b]) = o;
+        }
+      }
+    }
+  } else {
+    // ragged source tile or rows not 16-byte aligned: one element per thread and step
+    for (int i = tid; i < K * NT; i += kTcsThreads) {
+      const int rr = i / NT, c = i - rr * NT;
+      if (c >= ns) continue;
+      const float x = tile[rr * LD + c];
+      if (FLUX) {
+        p.F[(f_row + rr) * S + s0 + c] = x;
+        if (k == 0) a.flux[rows_sm[rr] * S + s0 + c] = x;
+      } else {
+        const int64_t at = (so + (int64_t)(k - 1) * K + rr) * S + s0 + c;
+        cso[at] = 2.f * cs[at] - cso[at] + tau2 * x;
+      }
+    }
+  }
+}
+
 template <int NT, bool FLUX>
 __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<float> a, const SplitArgs<float> p,
                                                              const TcArgs t, const int cur) {
@@ -293,7 +401,8 @@ __global__ void __launch_bounds__(kTcsThreads, 2) k_tc_split(const StepArgs<floa
   const bool go = ok_sm != 0;
   tc_fence_after();
   if (go) {
-    tcs_epilogue<NT, FLUX>(a, p, tmem, k, K, s0, ns, f_row, rows_sm, so, cs, cso);
+    tcs_epilogue_staged<NT, FLUX>(a, p, tmem, k, K, s0, ns, f_row, rows_sm, so, cs, cso,
+                                  reinterpret_cast<float *>(smem));
   } else if (tid == 0) {
     atomicExch(t.err, 1);
     // the A copies must land, and issued products finish, before shared memory and TMEM go away
