@@ -90,8 +90,8 @@ __device__ __forceinline__ void fma2(float &d0, float &d1, float a, float b0, fl
 
 // acc[s] = sum_c G[c*K] * X[c*ST + s] for the thread's output row (G already offset by the row).
 // The column stream of G is software-pipelined in registers: the next kChunk loads are issued
-// before the current kChunk values are consumed, and the chunk after that is prefetched into L2,
-// so each register load waits on L2 rather than on HBM.
+// before the current kChunk values are consumed; the caller has bulk-prefetched the whole matrix
+// into L2, so each register load waits on L2 rather than on HBM.
 template <typename T, int ST>
 __device__ __forceinline__ void row_times_block(const T *__restrict__ G, int K, const T *__restrict__ X,
                                                 T (&acc)[ST]) {
