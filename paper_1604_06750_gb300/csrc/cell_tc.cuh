@@ -196,17 +196,39 @@ __device__ __forceinline__ void tc_stage_layers(const float *fs, const float *cs
 #pragma unroll
     for (int i = 0; i < 8; ++i) mask |= (r0 + i < K && c < ns) ? 1u << i : 0u;
     const bool has_hi = k + 1 < m;
-    const float *lo = cs + (so + (int64_t)(k - 1) * K + r0) * S + s0 + c;
-    const float *hi = cs + (so + (int64_t)k * K + r0) * S + s0 + c;
+    const bool all = mask == 0xFFu;   // whole group inside the block: no address selects
+    if (k == 0) {
+      if (all) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const bool ok = (mask >> i) & 1u;
-      const float *p0 = !ok ? dummy : k == 0 ? fs + (rows[r0 + i] >> 1) * S + s0 + c : lo + (int64_t)i * S;
-      const float *p1 = ok && has_hi ? hi + (int64_t)i * S : dummy;
-      x0[i] = *p0;
-      x1[i] = *p1;
+        for (int i = 0; i < 8; ++i) x0[i] = fs[(rows[r0 + i] >> 1) * S + s0 + c];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x0[i] = *(((mask >> i) & 1u) ? fs + (rows[r0 + i] >> 1) * S + s0 + c : dummy);
+      }
+    } else {
+      const float *lo = cs + (so + (int64_t)(k - 1) * K + r0) * S + s0 + c;
+      if (all) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x0[i] = lo[(int64_t)i * S];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x0[i] = *(((mask >> i) & 1u) ? lo + (int64_t)i * S : dummy);
+      }
     }
-    if (!has_hi) mask |= 1u << 8;   // upper level is zero
+    if (has_hi) {
+      const float *hi = cs + (so + (int64_t)k * K + r0) * S + s0 + c;
+      if (all) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x1[i] = hi[(int64_t)i * S];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x1[i] = *(((mask >> i) & 1u) ? hi + (int64_t)i * S : dummy);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x1[i] = 0.f;
+      mask |= 1u << 8;   // upper level is zero
+    }
     kb = k;
     off = (int)core_off(c, r0, Kp);
     return true;

@@ -48,23 +48,36 @@ __device__ __forceinline__ void tcs_stage_b(const StepArgs<float> &a, const floa
     mask = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) mask |= (r0 + i < K && c < ns) ? 1u << i : 0u;
+    // 8 rows from base with row stride S: unmasked when the whole group is inside the block
+    // (the common case, no address selects), else masked elements read the safe address
+    const bool all = mask == 0xFFu;
+    auto rows8 = [&](float (&x)[8], const float *base) {
+      if (all) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = base[(int64_t)i * S];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = *(((mask >> i) & 1u) ? base + (int64_t)i * S : dummy);
+      }
+    };
     if (FLUX) {
       // lower level U^k (face rows for k = 0) and upper level U^{k+1} (zero past the last layer);
       // k and the upper layer's presence are uniform over the CTA
       const bool has_hi = k + 1 < m;
       if (k == 0) {
+        if (all) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          x0[i] = *(((mask >> i) & 1u) ? fs + (rows_sm[r0 + i] >> 1) * S + s0 + c : dummy);
+          for (int i = 0; i < 8; ++i) x0[i] = fs[(rows_sm[r0 + i] >> 1) * S + s0 + c];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            x0[i] = *(((mask >> i) & 1u) ? fs + (rows_sm[r0 + i] >> 1) * S + s0 + c : dummy);
+        }
       } else {
-        const float *lo = cs + (so + (int64_t)(k - 1) * K + r0) * S + s0 + c;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) x0[i] = *(((mask >> i) & 1u) ? lo + (int64_t)i * S : dummy);
+        rows8(x0, cs + (so + (int64_t)(k - 1) * K + r0) * S + s0 + c);
       }
       if (has_hi) {
-        const float *hi = cs + (so + (int64_t)k * K + r0) * S + s0 + c;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) x1[i] = *(((mask >> i) & 1u) ? hi + (int64_t)i * S : dummy);
+        rows8(x1, cs + (so + (int64_t)k * K + r0) * S + s0 + c);
       } else {
 #pragma unroll
         for (int i = 0; i < 8; ++i) x1[i] = 0.f;
@@ -72,12 +85,8 @@ __device__ __forceinline__ void tcs_stage_b(const StepArgs<float> &a, const floa
       }
     } else {
       const float *f1 = Fk + (int64_t)r0 * S + c;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const bool ok = (mask >> i) & 1u;
-        x1[i] = *(ok ? f1 + (int64_t)i * S : dummy);
-        x0[i] = *(ok ? f1 + (int64_t)(i - K) * S : dummy);
-      }
+      rows8(x1, f1);
+      rows8(x0, f1 - (int64_t)K * S);
     }
     off = (int)core_off(c, r0, Kp);
     return true;
