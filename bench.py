@@ -13,6 +13,7 @@ off-line build time, per-kernel roofline, the oracle timed on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
     python bench.py --profile N [--sched K]   # same workload, N eager time steps, for ncu captures
+    python bench.py --accuracy                # ROM vs fine grid at equal accuracy, cells of one wavelength
 
 The step schedule (graph-captured kernels with the plain or TMA-streamed cell kernel, or the
 persistent time-block kernel) is picked by the library's autotuner before the timed region.
@@ -632,6 +633,85 @@ def run_surrogate(args):
     print(json.dumps(out))
 
 
+def run_accuracy(args):
+    """ROM against the fine grid at equal receiver accuracy, at the operating point of the paper's
+    experiments (Section 7: cells about one minimum wavelength across, m = 4).
+
+    The 3D layered recipe on an n^3 grid of 16^3-voxel cells, band limit with a minimum wavelength
+    of one cell edge, 8 surface sources, fine-grid CFL step for both.  For each face-mode count:
+    GPU off-line build, FP32 and FP64 ROM stepping (Appendix D corners, graph schedule), receiver
+    rel-L2 against the same GPU's FP64 fine-grid leapfrog, and ms per time step of the FP32 ROM
+    beside the FP32 fine grid.  One JSON line."""
+    import torch
+    import paper_1604_06750_gb300 as P
+    from paper_1604_06750_gb300 import build as B
+    B.build()
+    P.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    modes = [int(x) for x in args.acc_modes.split(",")]
+    wl = synth.workload_3d_layers(args.acc_n, 16, m=4, n_modes=modes[0], n_src=8, n_steps=args.acc_steps,
+                                  band="cell")
+    L = P.Operator(wl.grid, wl.sigma, wl.rho)
+    LP = P.Partition(L, wl.cell, np.concatenate([wl.src_nodes, wl.rcv_nodes]).astype(np.int32))
+    lam = L.lambda_max(1e-7)
+    tau = wl.cfl_fraction * 2.0 / math.sqrt(lam)
+    s = -(2 * math.pi * wl.f_max) ** 2
+    nst, S, R = wl.n_steps, len(wl.src_nodes), len(wl.rcv_nodes)
+    wd = torch.tensor(synth.ricker(np.arange(nst) * tau, wl.f_peak), device=dev)
+
+    def run(obj, dtype, reps):
+        tr = torch.zeros((nst, R, S), device=dev, dtype=dtype)
+        obj.reset()
+        obj.step(nst, wd, tr, use_graph=True)              # warm-up, captures the graph
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            obj.reset()
+            obj.step(nst, wd, tr, use_graph=True)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return tr.double().cpu().numpy(), statistics.mean(ts)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    ref, t_f64 = run(P.FineSim(L, P.FP64, tau, wl.src_nodes, wl.rcv_nodes), torch.float64, 1)
+    f32, t_f32 = run(P.FineSim(L, P.FP32, tau, wl.src_nodes, wl.rcv_nodes), torch.float32, 3)
+    rows = []
+    for nm in modes:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            LR = P.Rom.build(LP, 4, nm, s, cg_tol=1e-13)
+        except P.MssError as ex:        # e.g. a coefficient block that is not SPD: reported, not fatal
+            rows.append({"face_modes": nm, "error": str(ex)})
+            continue
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        LR.set_io_nodes(LP, wl.src_nodes, wl.rcv_nodes)
+        cm, cfp, cf, fM, _, _, _, _ = LR.export()
+        Ks = [int(sum(fM[cf[cfp[c]:cfp[c + 1]]])) for c in range(len(cm))]
+        r32, t32 = run(P.Sim(LR, P.FP32, tau, corner_correction=True), torch.float32, 3)
+        r64, t64 = run(P.Sim(LR, P.FP64, tau, corner_correction=True), torch.float64, 1)
+        rows.append({"face_modes": nm, "K_max": max(Ks), "offline_s": t_build,
+                     "rel_l2_rom_fp64_vs_fine_fp64": rel(r64, ref), "rel_l2_rom_fp32_vs_fine_fp64": rel(r32, ref),
+                     "rom_fp32_ms_per_time_step": 1e3 * t32 / nst, "rom_fp64_ms_per_time_step": 1e3 * t64 / nst,
+                     "fine_fp32_over_rom_fp32_time": t_f32 / t32})
+        del LR
+    ncells = int(LP.info()[0])
+    out = {"mode": "accuracy", "workload": "3d_layers_%d band=cell: %d^3 voxels, %d cells of 16^3, m=4, %d sources, "
+                                          "%d receivers, %d steps" % (args.acc_n, args.acc_n, ncells, S, R, nst),
+           "f_peak": wl.f_peak, "f_max": wl.f_max, "tau": tau,
+           "fine_fp32_ms_per_time_step": 1e3 * t_f32 / nst, "fine_fp64_ms_per_time_step": 1e3 * t_f64 / nst,
+           "rel_l2_fine_fp32_vs_fine_fp64": rel(f32, ref), "roms": rows}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -650,7 +730,15 @@ def main():
     ap.add_argument("--train-media", type=int, default=24)
     ap.add_argument("--train-iters", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--accuracy", action="store_true",
+                    help="ROM vs fine grid at equal receiver accuracy over face-mode counts (JSON line)")
+    ap.add_argument("--acc-n", type=int, default=64, help="voxels per edge of --accuracy")
+    ap.add_argument("--acc-modes", default="15,28,45", help="face-mode counts of --accuracy")
+    ap.add_argument("--acc-steps", type=int, default=3000)
     args = ap.parse_args()
+    if args.accuracy:
+        run_accuracy(args)
+        return
     if args.surrogate:
         run_surrogate(args)
         return
