@@ -15,6 +15,9 @@ Readings (where the paper is silent, garbled or inconsistent):
   modes of the face's node grid, Euclidean-orthonormal by construction (S_f^T S_f = I),
   ordered by (a/n1)^2 + (b/n2)^2 then (a, b); these are the Neumann modes of a
   uniform face and do not depend on the medium.  I/O faces keep S_f = I.
+  The paper's exact frequency-limited Gramian (Eq. trgr, from the propagative eigenpairs
+  of the whole pencil) is ``face_gramians`` / ``gramian_bases``; it checks that reading
+  and can replace it through ``build_rom(..., bases=...)``.
 * Krylov subspace (Eq. npks): the pencil form with K = (A+sB)^{-1} B and the
   zero-power block B^{-1} P S (Remark Sinsubspace), i.e. the block Krylov space
   span{B^{-1}C, K B^{-1}C, ..., K^{m-1} B^{-1}C}, C = P^Gamma S; note K B^{-1} C =
@@ -82,6 +85,72 @@ def face_basis(face, n_modes: int) -> np.ndarray:
         return dct_modes(shape[0])[:, [o[0] for o in order]]
     p1, p2 = dct_modes(shape[0]), dct_modes(shape[1])
     return np.stack([np.kron(p1[:, a], p2[:, b]) for (a, b) in order], axis=1)
+
+
+def propagative_modes(A: sp.spmatrix, Bd: np.ndarray, lam_max: float, dense_limit: int = 6000):
+    """Eigenpairs of the pencil below the band limit (Eq. specdec): -A z_l = lam_l B z_l with
+    lam_l <= lam_max (eigenvalues of -B^{-1}A, reading R16) and z_l^T B z_l = 1.
+
+    Dense symmetric-definite eigensolver up to ``dense_limit`` unknowns; above it, shift-invert
+    Lanczos (ARPACK) on B^{-1/2}(-A)B^{-1/2} about zero, with the number of requested pairs doubled
+    until one of them lies above the band.  Returns (lam ascending, Z as columns).
+    """
+    N = A.shape[0]
+    if N <= dense_limit:
+        lam, Z = sla.eigh(-A.toarray(), np.diag(Bd), subset_by_value=(-np.inf, lam_max))
+        return lam, Z
+    bh = 1.0 / np.sqrt(Bd)
+    Ms = (sp.diags(bh) @ (-A) @ sp.diags(bh)).tocsc()
+    k = 64
+    while True:
+        k = min(k, N - 2)
+        lam, W = spla.eigsh(Ms, k=k, sigma=0.0, which="LM")
+        order = np.argsort(lam)
+        lam, W = lam[order], W[:, order]
+        if lam[-1] > lam_max or k >= N - 2:
+            keep = lam <= lam_max
+            return lam[keep], bh[:, None] * W[:, keep]
+        k *= 2
+
+
+def face_gramians(part, modes) -> List[Optional[np.ndarray]]:
+    """Frequency-limited Gramians of Eq. trgr, one per interior face (None for I/O faces).
+
+    G_f = sum over the given propagative modes of v_l v_l^T, v_l = z_l restricted to the face's
+    nodes in face order (a hanging copy of a corner-set node takes the node's value);
+    ``modes`` = (lam, Z) from ``propagative_modes``.
+    """
+    Z = modes[1]
+    out: List[Optional[np.ndarray]] = []
+    for f in part.faces:
+        if f.kind == "io":
+            out.append(None)
+            continue
+        V = Z[np.asarray(f.parents, dtype=np.int64), :]
+        out.append(V @ V.T)
+    return out
+
+
+def gramian_bases(part, lam_max: float, n_modes: int, modes=None) -> List[np.ndarray]:
+    """S_f from the frequency-limited Gramian of Eq. trgr, the paper's own boundary basis.
+
+    S_f = the eigenvectors of G_f (``face_gramians``) of the ``n_modes`` largest eigenvalues,
+    S_f^T S_f = I.  G_f has rank at most the number of propagative modes, so columns beyond it
+    span part of its null space.  z_l are the B-normalised eigenvectors of the original pencil
+    with lam_l <= lam_max (``propagative_modes``, or ``modes`` = (lam, Z) given).  I/O faces
+    keep S_f = I.
+    """
+    if modes is None:
+        modes = propagative_modes(part.op.A, part.op.B, lam_max)
+    out = []
+    for f, G in zip(part.faces, face_gramians(part, modes)):
+        if G is None:
+            out.append(np.eye(len(f.nodes)))
+            continue
+        w, Q = np.linalg.eigh(G)
+        M = min(n_modes, len(f.nodes))
+        out.append(Q[:, ::-1][:, :M].copy())
+    return out
 
 
 # --------------------------------------------------------------------------- Krylov ROM (Eq. npks, tfprj)
@@ -255,9 +324,13 @@ def face_masses(part, bases, cell_roms: Dict[int, CellRom]) -> List[np.ndarray]:
     return out
 
 
-def build_rom(part, m, n_modes: int, s: float, keep=False) -> Rom:
-    """All cells (m scalar or per cell) -> topology, coefficients and face bases."""
-    bases = [face_basis(f, n_modes) for f in part.faces]
+def build_rom(part, m, n_modes: int, s: float, keep=False, bases=None) -> Rom:
+    """All cells (m scalar or per cell) -> topology, coefficients and face bases.
+
+    ``bases``: per-face S_f to use instead of the DCT modes of ``face_basis`` (for example
+    ``gramian_bases``)."""
+    if bases is None:
+        bases = [face_basis(f, n_modes) for f in part.faces]
     ms = [int(m)] * len(part.cells) if np.isscalar(m) else [int(x) for x in m]
     cells = {c.id: build_cell_rom(part, c.id, bases, ms[c.id], s, keep) for c in part.cells}
     fm = face_masses(part, bases, cells)
