@@ -155,6 +155,21 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------- ranks
+def whole_job_rate(units_per_rank: float, seconds: float, world: int, dist=None, device=None):
+    """Throughput of the whole job: the units all ranks processed over the slowest rank's time.
+
+    Every rank runs its own replica (no data-path collective); the only exchange is this max over
+    ranks of the timed seconds (an all-reduce on ``device``: the GPU under NCCL, the CPU under
+    gloo).  Collective: all ranks must call it.  Returns (rate, slowest seconds)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+    return world * units_per_rank / seconds, seconds
+
+
 # ----------------------------------------------------------------------------- native
 def _kernel_model(rom_info, topo_K, topo_m, n_src, es):
     """Algorithmic bytes and flops of one cell-kernel launch (one time step, all cells)."""
@@ -268,12 +283,7 @@ def run_native(args):
     if dist:
         dist.barrier()
     ck = clocks.stop()
-    t_step = statistics.mean(times)
-    if dist:
-        t = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = world * units / t_step
+    value, t_step = whole_job_rate(units, statistics.mean(times), world, dist, dev)
     tr32 = tr.double().cpu().numpy()
     # ---- per-kernel timing (eager, CUDA events on the launching stream)
     # per-kernel events need separate launches: profile the graph schedule with the same cell body
@@ -377,8 +387,8 @@ def run_native(args):
         a = time.perf_counter()
         host_tr = sim.run_host(w)
         e2e_times.append(time.perf_counter() - a)
-    e2e = {"value": world * units / statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": int(w.nbytes),
-           "d2h_bytes_per_step": int(host_tr.nbytes)}
+    e2e = {"value": whole_job_rate(units, statistics.mean(e2e_times), world, dist, dev)[0], "unit": UNIT,
+           "h2d_bytes_per_step": int(w.nbytes), "d2h_bytes_per_step": int(host_tr.nbytes)}
     # ---- oracle on the host cores, bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1:
