@@ -1,0 +1,76 @@
+"""The library's host-side off-line pieces against the oracle, without a GPU.
+
+``mss_rom_skeleton`` runs the parts of the off-line stage that live in host C++: topology, DCT
+face bases (Section 4.1, reading R6), the exact Markov block Gamma-hat^1 = S^T P^T B^{-1} P S
+of every cell (Remark Sinsubspace) and the face masses of Eq. bdrytstep.  The Krylov and
+Lanczos steps run on the GPU and are left out.  Each piece is compared with the oracle's full
+build on the same partition.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fine, partition, rom
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1604_06750_gb300 as pkg
+    from paper_1604_06750_gb300 import build
+    build.build()
+    pkg.lib()
+    return pkg
+
+
+def _cases():
+    yield "2d", synth.workload_2d_layers(32, 8, m=3, n_modes=4, n_steps=10)
+    yield "3d", synth.workload_3d_layers(16, 8, m=3, n_modes=6, n_src=2, n_steps=10)
+
+
+@pytest.mark.parametrize("name,wl", list(_cases()))
+def test_skeleton_matches_oracle(P, name, wl):
+    op = fine.FineOperator(wl.grid, wl.sigma, wl.rho)
+    io_list = [tuple(int(x) for x in p) for p in list(wl.src_nodes) + list(wl.rcv_nodes)]
+    part = partition.Partition(op, wl.sigma, wl.rho, wl.cell, io_nodes=io_list)
+    s = -rom.omega_max(wl.f_max) ** 2
+    R = rom.build_rom(part, wl.m, wl.n_modes, s)
+    L = P.Operator(wl.grid, wl.sigma, wl.rho)
+    LP = P.Partition(L, wl.cell, np.concatenate([wl.src_nodes, wl.rcv_nodes]).astype(np.int32))
+    SK = P.Rom.skeleton(LP, wl.m, wl.n_modes, s)
+    cm, cfp, cf, fM, fc, g, gh, fm = SK.export()
+    topo = R.topology
+    assert list(cm) == list(topo.cell_m)
+    assert list(fM) == list(topo.face_M)
+    for c in range(topo.n_cells):
+        assert list(cf[cfp[c]:cfp[c + 1]]) == topo.cell_faces[c]
+    # Gamma-hat^1 of every cell is exact and block-diagonal over the cell's faces
+    o = 0
+    for c in range(topo.n_cells):
+        K = int(topo.cell_K()[c])
+        blk = gh[o:o + K * K].reshape(K, K)
+        ref = R.coeffs.gamma_hat[c][0]
+        assert np.linalg.norm(blk - ref) <= TOL * np.linalg.norm(ref), c
+        r0 = 0
+        for f in topo.cell_faces[c]:
+            M = int(topo.face_M[f])
+            off = blk[r0:r0 + M].copy()
+            off[:, r0:r0 + M] = 0.0
+            assert np.abs(off).max() <= TOL * np.abs(blk).max()
+            r0 += M
+        # Gamma^k and Gamma-hat^(k >= 2) are left for the exact or learned construction
+        assert not np.any(g[o:o + int(cm[c]) * K * K])
+        assert not np.any(gh[o + K * K:o + int(cm[c]) * K * K])
+        o += int(cm[c]) * K * K
+    o = 0
+    for f, M in enumerate(topo.face_M):
+        blk = fm[o:o + M * M].reshape(M, M)
+        assert np.linalg.norm(blk - R.coeffs.face_mass[f]) <= TOL * np.linalg.norm(R.coeffs.face_mass[f])
+        o += M * M
+    bases = SK.face_bases()
+    o = 0
+    for B in R.bases:
+        assert np.allclose(bases[o:o + B.size].reshape(B.shape), B, rtol=0, atol=1e-14)
+        o += B.size
+    assert o == bases.size
