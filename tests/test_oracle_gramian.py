@@ -80,3 +80,43 @@ def test_dense_and_shift_invert_eigensolvers_agree():
     # same B-orthogonal projector onto the propagative subspace (eigenvector signs are free)
     assert np.allclose(Zd @ Zd.T, Zs @ Zs.T, atol=1e-9 * np.abs(Zd @ Zd.T).max())
     assert np.allclose(Zd.T @ (op.B[:, None] * Zd), np.eye(ld.size), atol=1e-10)
+
+
+def _gramian_pin_error(modes_fn=None):
+    """Largest relative deviation of the oracle's face Gramians from the closed form (rho = 2)."""
+    n, cell, rho, sigma = 12, 4, 2.0, 3.0
+    grid, op, part = _uniform_box(n, cell, rho, sigma)
+    lam_max = _band_between_levels(n, grid.h, sigma / rho, 9)
+    Zc = _closed_form(grid, op, sigma, rho, lam_max)
+    modes = (modes_fn or rom.propagative_modes)(op.A, op.B, lam_max)
+    G = rom.face_gramians(part, modes)
+    err = 0.0
+    for f, Gf in zip(part.faces, G):
+        idx = np.asarray(f.parents)
+        Gc = Zc[idx] @ Zc[idx].T
+        err = max(err, np.abs(Gf - Gc).max() / np.abs(Gc).max())
+    return err
+
+
+def test_gramian_pin_catches_planted_mistakes():
+    assert _gramian_pin_error() < 1e-12
+
+    def euclidean_modes(A, Bd, lam_max):
+        # eigenvectors normalised in the Euclidean instead of the B inner product
+        lam, Z = rom.propagative_modes(A, Bd, lam_max)
+        return lam, Z / np.linalg.norm(Z, axis=0)
+
+    def generalised_sign(A, Bd, lam_max):
+        # eigenvalues of B^{-1}A instead of -B^{-1}A (reading R16 ignored): every mode passes
+        import scipy.linalg as sla
+        lam, Z = sla.eigh(A.toarray(), np.diag(Bd))
+        keep = lam <= lam_max
+        return lam[keep], Z[:, keep]
+
+    def one_mode_short(A, Bd, lam_max):
+        lam, Z = rom.propagative_modes(A, Bd, lam_max)
+        return lam[:-1], Z[:, :-1]
+
+    assert _gramian_pin_error(euclidean_modes) > 1e-3
+    assert _gramian_pin_error(one_mode_short) > 1e-3
+    assert _gramian_pin_error(generalised_sign) > 1e-3
