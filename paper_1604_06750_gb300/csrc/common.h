@@ -8,9 +8,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mss.h"
 
 namespace mss {
+
+// Scoped NVTX range around an entry point (off-line stages, time blocks, autotuning), so that a
+// profiler's timeline shows them by name; a no-op when no tool is attached.
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 // An error carrying a status code; caught at the C ABI boundary.
 struct Error : std::runtime_error {

@@ -246,6 +246,7 @@ mss_status mss_fine_reset(mss_fine *f, void *stream) {
 mss_status mss_fine_step(mss_fine *f, int64_t n_steps, const double *waveform, void *traces, int32_t use_graph,
                          void *stream) {
   return guard([&] {
+    const Range nvtx_range("mss_fine_step");
     MSS_REQUIRE(f && waveform && traces && n_steps >= 0, MSS_ERR_INVALID_ARG, "bad argument");
     if (n_steps == 0) return;
     if (f->prec == MSS_FP64) fine_step<double>(*f, n_steps, waveform, traces, use_graph, (cudaStream_t)stream);

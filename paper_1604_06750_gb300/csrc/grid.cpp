@@ -535,6 +535,7 @@ extern "C" {
 
 mss_status mss_assemble(const mss_grid *g, const double *sigma, const double *rho, mss_operator **out) {
   return guard([&] {
+    const Range nvtx_range("mss_assemble");
     MSS_REQUIRE(g && sigma && rho && out, MSS_ERR_INVALID_ARG, "null argument");
     auto h = std::make_unique<mss_operator>();
     assemble(h->o, *g, sigma, rho);
@@ -588,6 +589,7 @@ void mss_operator_destroy(mss_operator *op) { delete op; }
 mss_status mss_partition_create(const mss_operator *op, const double *sigma, const double *rho, const int32_t *cell,
                                 int32_t n_io, const int32_t *io_nodes, mss_partition **out) {
   return guard([&] {
+    const Range nvtx_range("mss_partition_create");
     MSS_REQUIRE(op && sigma && rho && cell && out && n_io >= 0 && (n_io == 0 || io_nodes), MSS_ERR_INVALID_ARG,
                 "null argument");
     auto h = std::make_unique<mss_partition>();

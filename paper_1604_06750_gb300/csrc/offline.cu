@@ -1132,6 +1132,7 @@ extern "C" {
 
 mss_status mss_rom_skeleton(const mss_partition *p, const mss_rom_params *prm, const int32_t *cell_m, mss_rom **out) {
   return guard([&] {
+    const Range nvtx_range("mss_rom_skeleton");
     MSS_REQUIRE(p && prm && out, MSS_ERR_INVALID_ARG, "null argument");
     auto h = std::make_unique<mss_rom>();
     Partition &P = const_cast<Partition &>(p->p);
@@ -1149,6 +1150,7 @@ mss_status mss_rom_skeleton(const mss_partition *p, const mss_rom_params *prm, c
 
 mss_status mss_rom_rebuild_cells(mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells, void *stream) {
   return guard([&] {
+    const Range nvtx_range("mss_rom_rebuild_cells");
     MSS_REQUIRE(r && p && n >= 0 && (n == 0 || cells), MSS_ERR_INVALID_ARG, "bad argument");
     Rom &R = r->r;
     MSS_REQUIRE(R.source == &p->p, MSS_ERR_STATE, "ROM was not built from this partition");
@@ -1247,6 +1249,7 @@ mss_status mss_surrogate_unpack(mss_rom *r, const mss_partition *p, int32_t n, c
 mss_status mss_surrogate_screen(const mss_rom *r, const mss_partition *p, int32_t n, const int32_t *cells, double *err,
                                 void *stream) {
   return guard([&] {
+    const Range nvtx_range("mss_surrogate_screen");
     MSS_REQUIRE(r && p && n >= 1 && cells && err, MSS_ERR_INVALID_ARG, "bad argument");
     const Rom &R = r->r;
     MSS_REQUIRE(R.source == &p->p, MSS_ERR_STATE, "ROM was not built from this partition");
@@ -1264,6 +1267,7 @@ mss_status mss_surrogate_infer(mss_surrogate *sur, mss_rom *r, const mss_partiti
                                int32_t slot_modes, int32_t io_slots, double tol, double *err, int32_t *fallback,
                                void *stream) {
   return guard([&] {
+    const Range nvtx_range("mss_surrogate_infer");
     MSS_REQUIRE(sur && r && p && n >= 1 && cells && err && fallback && tol > 0, MSS_ERR_INVALID_ARG, "bad argument");
     Rom &R = r->r;
     MSS_REQUIRE(R.source == &p->p, MSS_ERR_STATE, "ROM was not built from this partition");
@@ -1321,6 +1325,7 @@ using namespace mss;
 extern "C" mss_status mss_build_roms(const mss_partition *p, const mss_rom_params *prm, const int32_t *cell_m, void *stream,
                                      mss_rom **out) {
   return guard([&] {
+    const Range nvtx_range("mss_build_roms");
     MSS_REQUIRE(p && prm && out, MSS_ERR_INVALID_ARG, "null argument");
     auto h = std::make_unique<mss_rom>();
     build_roms(p->p, *prm, cell_m, (cudaStream_t)stream, h->r);

@@ -1512,6 +1512,7 @@ mss_status mss_step_noalloc(mss_step_buffers *b, int64_t n_steps, const double *
 
 mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32_t corner_correction, mss_sim **out) {
   return guard([&] {
+    const Range nvtx_range("mss_sim_create");
     MSS_REQUIRE(r && out, MSS_ERR_INVALID_ARG, "null argument");
     auto s = std::make_unique<mss_sim>();
     sim_create(*s, r->r, precision, tau, corner_correction);
@@ -1550,6 +1551,7 @@ mss_status mss_sim_reset(mss_sim *s, void *stream) {
 mss_status mss_step(mss_sim *s, int64_t n_steps, const double *waveform, void *traces, int32_t use_graph,
                     void *stream) {
   return guard([&] {
+    const Range nvtx_range("mss_step");
     MSS_REQUIRE(s && waveform && traces && n_steps >= 0, MSS_ERR_INVALID_ARG, "bad argument");
     if (n_steps == 0) return;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1561,6 +1563,7 @@ mss_status mss_step(mss_sim *s, int64_t n_steps, const double *waveform, void *t
 mss_status mss_step_profile(mss_sim *s, int64_t n_steps, const double *waveform, void *traces, double ms[3],
                             void *stream) {
   return guard([&] {
+    const Range nvtx_range("mss_step_profile");
     MSS_REQUIRE(s && waveform && traces && ms && n_steps > 0, MSS_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     if (s->prec == MSS_FP64) profile_dispatch<double>(*s, n_steps, waveform, traces, ms, st);
@@ -1648,6 +1651,7 @@ mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *avail
 
 mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *ms, int32_t *chosen) {
   return guard([&] {
+    const Range nvtx_range("mss_sim_autotune");
     MSS_REQUIRE(s && n_steps >= 2, MSS_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     const int n = n_steps + (n_steps & 1);   // even: the time-level parity returns, graphs are reused
@@ -1771,6 +1775,7 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
 
 mss_status mss_run_host(mss_sim *s, int64_t n_steps, const double *waveform_host, void *traces_host, void *stream) {
   return guard([&] {
+    const Range nvtx_range("mss_run_host");
     MSS_REQUIRE(s && waveform_host && traces_host && n_steps > 0, MSS_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t es = s->prec == MSS_FP64 ? 8 : 4;

@@ -21,6 +21,7 @@ using namespace mss;
 extern "C" mss_status mss_sim_check_stability(mss_sim *s, int32_t n_steps, uint64_t seed, double max_growth,
                                               double *growth, void *stream) {
   return guard([&] {
+    const Range nvtx_range("mss_sim_check_stability");
     MSS_REQUIRE(s && n_steps >= 1 && max_growth > 1.0, MSS_ERR_INVALID_ARG, "bad argument");
     int64_t info[8];
     mss_status e = mss_sim_info(s, info);

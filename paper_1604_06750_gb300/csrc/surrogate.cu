@@ -543,6 +543,7 @@ mss_status mss_surrogate_backward(mss_surrogate *s, int32_t batch, const float *
 mss_status mss_surrogate_train_step(mss_surrogate *s, int32_t batch, const float *x, const float *feat,
                                     const float *target, const float *mask, float lr, float *loss, void *stream) {
   return guard([&] {
+    const Range nvtx_range("mss_surrogate_train_step");
     MSS_REQUIRE(s && batch >= 1 && x && target && (s->nfeat == 0 || feat) && lr > 0, MSS_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     sur_alloc_batch(*s, batch);
