@@ -111,10 +111,23 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- oracle timing
+def _oracle_stepper(topo, co, gt, qt):
+    """The oracle's ROM leapfrog for host timing, prepared for one topology: the plain C loops
+    (OpenMP, all host threads; coefficients marshalled before the clock starts) when gcc could
+    build them, else the NumPy restatement.  Returns (run(w, tau, n_steps), label, threads)."""
+    try:
+        from oracle import c_leapfrog
+        lf = c_leapfrog.RomLeapfrog(topo, co, gt, qt)
+        return lf.run, "C, OpenMP", c_leapfrog.threads()
+    except (OSError, RuntimeError):
+        from oracle import online
+        return (lambda w, tau, n: online.rom_leapfrog(topo, co, gt, qt, w, tau, n)), "NumPy", 1
+
+
 def oracle_rate(n_src: int, n_steps_sample: int):
     """The oracle's ROM leapfrog on the workload's cell/face shapes (random SPD coefficients of
     the same sizes; the timing does not depend on the values), all cells and sources, a bounded
-    number of time steps.  Returns (rate in source·cell-steps/s, seconds, cells)."""
+    number of time steps.  Returns (rate in source·cell-steps/s, seconds, cells, label, threads)."""
     from oracle import online
     io_cells = [(c, 2) for c in range(7 * 64, 8 * 64)]           # one 2-node I/O face per top cell
     topo = synth.box_topology((8, 8, 8), modes=WORKLOAD["n_modes"], m=WORKLOAD["m"], io_cells=io_cells, seed=7)
@@ -123,10 +136,21 @@ def oracle_rate(n_src: int, n_steps_sample: int):
     gt = online.dense_io(topo, src, n_src, "src")
     qt = online.dense_io(topo, rcv, 8, "rcv")
     w = synth.ricker(np.arange(n_steps_sample) * 0.05, 1.0)
+    step, label, threads = _oracle_stepper(topo, co, gt, qt)
     t0 = time.perf_counter()
-    online.rom_leapfrog(topo, co, gt, qt, w, 0.05, n_steps_sample)
+    step(w, 0.05, n_steps_sample)
     dt = time.perf_counter() - t0
-    return topo.n_cells * n_src * n_steps_sample / dt, dt, topo.n_cells
+    return topo.n_cells * n_src * n_steps_sample / dt, dt, topo.n_cells, label, threads
+
+
+def oracle_baseline(n_src: int, target_s: float = 10.0):
+    """cpu_baseline entry: a 20-step probe, then a sample sized to about ``target_s`` seconds."""
+    rate, dt, nc, label, threads = oracle_rate(n_src, 20)
+    steps = int(min(5000, max(20, target_s / max(dt / 20, 1e-9))))
+    rate, dt, nc, label, threads = oracle_rate(n_src, steps)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "seconds": dt,
+            "sample": "all %d cells x %d sources x %d time steps (%s oracle loops, random SPD coefficients of "
+                      "the workload's block sizes)" % (nc, n_src, steps, label)}
 
 
 def run_reference(args):
@@ -140,17 +164,17 @@ def run_reference(args):
     for _ in range(args.warmup):
         oracle_rate(n_src, 5)
     for _ in range(args.steps):
-        rate, dt, nc = oracle_rate(n_src, sample)
+        rate, dt, nc, label, cores = oracle_rate(n_src, sample)
         times.append(dt)
     units = nc * n_src * sample
     value = units / statistics.mean(times)
-    cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(wl, {"precision": "fp64 (oracle, numpy)"}),
+            "config": _config(wl, {"precision": "fp64 (oracle, %s)" % label}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "all %d cells x %d sources x %d time steps per bench step" % (nc, n_src, sample)},
+                             "sample": "all %d cells x %d sources x %d time steps per bench step (%s oracle loops)"
+                                       % (nc, n_src, sample, label)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -392,10 +416,7 @@ def run_native(args):
     # ---- oracle on the host cores, bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1:
-        rate, dt, nc = oracle_rate(S, 100)
-        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "seconds": dt,
-               "sample": "all %d cells x %d sources x 100 time steps (numpy, random SPD coefficients of the "
-                         "workload's block sizes)" % (nc, S)}
+        cpu = oracle_baseline(S)
     if rank != 0:
         if dist:
             dist.destroy_process_group()

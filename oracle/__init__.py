@@ -23,6 +23,9 @@ Modules
                Eqs. intrtstep_td, bdrytstep, solatrec) and its discrete energy.
 ``freq``       frequency-domain coupled ROM (Algorithm alg2red) and transfer
                functions of cells and skeleton.
+``c_leapfrog`` the ROM and fine-grid leapfrog loops again in plain C with OpenMP
+               (``c/leapfrog.c``), checked against ``online`` / ``fine``; the
+               host-core timing path of the bench's CPU baseline.
 
 Pins: ``tests/test_oracle_*.py`` check every function against closed forms the
 paper prints, invariants it states, and brute force on tiny inputs.
