@@ -15,10 +15,12 @@ Modules
 ``fine``       fine-grid assembly (Section 1) and the fine leapfrog.
 ``partition``  coarse cells, operator splitting (Section 2, Eq. splitN_c),
                corner-set removal (Section 3, Appendix B), I/O faces.
-``rom``        face bases (Section 4.1), rational Krylov ROM (Section 4.2,
+``rom``        face bases (Section 4.1; DCT reading and the frequency-limited
+               Gramian of Eq. trgr), rational Krylov ROM (Section 4.2,
                Eq. npks/tfprj), block Lanczos (Appendix C, Eq. NtDtri),
                S-fraction coefficients (Eq. GammaTrans), face masses
-               (Remark Sinsubspace, Eq. bdrytstep), projected sources/receivers.
+               (Remark Sinsubspace, Eq. bdrytstep), projected sources/receivers,
+               the per-cell layer-count rule of the dipping-layer workload.
 ``online``     on-line leapfrog of the coupled ROM (Algorithm alg1red stage 2,
                Eqs. intrtstep_td, bdrytstep, solatrec) and its discrete energy.
 ``freq``       frequency-domain coupled ROM (Algorithm alg2red) and transfer

@@ -295,6 +295,34 @@ def cell_input_matrix(part, cid: int, bases: List[np.ndarray]) -> np.ndarray:
     return C
 
 
+def layer_count_rule(part, cid: int, bases: List[np.ndarray], s: float, omega_max: float,
+                     m_range=(3, 6), tol: float = 1e-4, n_freq: int = 8):
+    """Per-cell number of S-fraction layers (reading R22 of the 256^3 dipping-layer workload):
+    the smallest m in ``m_range`` whose ROM transfer function (Eq. tfprj) is within ``tol`` of the
+    largest m's at ``n_freq`` test frequencies.
+
+    Test points: z_j = -w_j^2 + i w_j omega_max / 10, w_j = j omega_max / n_freq (j = 1..n_freq),
+    damped frequencies that keep clear of the real-axis poles.  Error: the largest
+    ||F~^m(z_j) - F~^mmax(z_j)||_F / ||F~^mmax(z_j)||_F.  The block Krylov spaces are nested (each
+    block is B-orthogonalised against the earlier ones), so A^m and S^m of every m are leading
+    blocks of the largest m's.  Returns (m, error at m, errors of every m in the range).
+    """
+    lo, hi = int(m_range[0]), int(m_range[1])
+    cell = part.build_cell(cid)
+    C = cell_input_matrix(part, cid, bases)
+    K = C.shape[1]
+    _, Am, Sm = krylov_rom(cell.A, cell.B, C, hi, s)
+    zs = [-(w * w) + 1j * w * omega_max / 10.0 for w in omega_max * np.arange(1, n_freq + 1) / n_freq]
+    ref = [Sm.T @ np.linalg.solve(Am + z * np.eye(Am.shape[0]), Sm) for z in zs]
+    errs = {}
+    for m in range(lo, hi + 1):
+        n = m * K
+        errs[m] = max(float(np.linalg.norm(Sm[:n].T @ np.linalg.solve(Am[:n, :n] + z * np.eye(n), Sm[:n]) - R)
+                            / np.linalg.norm(R)) for z, R in zip(zs, ref))
+    m = next(k for k in range(lo, hi + 1) if errs[k] <= tol)
+    return m, errs[m], errs
+
+
 def build_cell_rom(part, cid: int, bases: List[np.ndarray], m: int, s: float, keep=False) -> CellRom:
     c = part.build_cell(cid)
     C = cell_input_matrix(part, cid, bases)
