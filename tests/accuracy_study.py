@@ -10,6 +10,7 @@ and prints the receiver relative L2 error.
     python tests/accuracy_study.py --n 64 --band nyquist --modes 15 --m 6
     python tests/accuracy_study.py --n 64 --band nyquist --modes 15 --m 8 --clamp-last
     python tests/accuracy_study.py --n 32 --band cell --modes 6 10 --basis gramian
+    python tests/accuracy_study.py --workload 2d --modes 2 3 4 --basis gramian
     python tests/accuracy_study.py --n 64 --band cell --modes 45 --sources 8 --fp32 plain fp64-last chol-last
 
 ``--clamp-last`` sets the near-zero eigenvalues of the last coefficient to zero so that builds
@@ -114,7 +115,9 @@ def rel(a, b):
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--n", type=int, default=32, help="voxels per edge (16^3-voxel cells)")
+    ap.add_argument("--workload", choices=["3d", "2d"], default="3d",
+                    help="3d: layered 3D recipe with 16^3-voxel cells; 2d: the 64^2 layered 2D workload")
+    ap.add_argument("--n", type=int, default=32, help="voxels per edge of the 3D recipe (16^3-voxel cells)")
     ap.add_argument("--band", choices=["cell", "nyquist"], default="cell")
     ap.add_argument("--modes", type=int, nargs="+", default=[15])
     ap.add_argument("--m", type=int, default=4)
@@ -124,8 +127,13 @@ def main():
     ap.add_argument("--clamp-last", action="store_true")
     ap.add_argument("--fp32", nargs="*", default=[], choices=["plain", "fp64-last", "chol-last"])
     a = ap.parse_args()
-    nst = a.steps or (1500 if a.n <= 32 else 3000)
-    wl = synth.workload_3d_layers(a.n, 16, m=a.m, n_modes=a.modes[0], n_src=a.sources, n_steps=nst, band=a.band)
+    if a.workload == "2d":
+        nst = a.steps or 2000
+        wl = synth.workload_2d_layers(64, 8, m=a.m, n_modes=a.modes[0], n_steps=nst)
+    else:
+        nst = a.steps or (1500 if a.n <= 32 else 3000)
+        wl = synth.workload_3d_layers(a.n, 16, m=a.m, n_modes=a.modes[0], n_src=a.sources, n_steps=nst,
+                                      band=a.band)
     op = fine.FineOperator(wl.grid, wl.sigma, wl.rho)
     io = [tuple(int(x) for x in p) for p in list(wl.src_nodes) + list(wl.rcv_nodes)]
     part = partition.Partition(op, wl.sigma, wl.rho, wl.cell, io_nodes=io)
@@ -150,8 +158,9 @@ def main():
         qt = [x.T for x in rom.project_io(part, R.bases, part.prime_vectors(wl.rcv_nodes))]
         corners = online.corner_rows(part.corner_groups(), R.bases)
         tr = online.rom_leapfrog(R.topology, R.coeffs, gt, qt, w, tau, nst, corners=corners)
-        line = "n=%d band=%s basis=%s modes=%d m=%d sources=%d steps=%d: rel-L2 ROM FP64 vs fine %.4e" % (
-            a.n, a.band, a.basis, nm, a.m, a.sources, nst, rel(tr, ref))
+        line = "%s basis=%s modes=%d m=%d sources=%d steps=%d: rel-L2 ROM FP64 vs fine %.4e" % (
+            wl.name + ("" if a.workload == "2d" else " band=" + a.band), a.basis, nm, a.m, len(wl.src_nodes), nst,
+            rel(tr, ref))
         for v in a.fp32:
             t32 = rom_leapfrog_fp32(R, gt, qt, w, tau, nst, corners, v)
             line += "; FP32 %s: vs ROM FP64 %.3e, vs fine %.3e" % (v, rel(t32, tr), rel(t32, ref))
