@@ -121,7 +121,7 @@ def _oracle_stepper(topo, co, gt, qt):
         return lf.run, "C, OpenMP", c_leapfrog.threads()
     except (OSError, RuntimeError):
         from oracle import online
-        return (lambda w, tau, n: online.rom_leapfrog(topo, co, gt, qt, w, tau, n)), "NumPy", 1
+        return (lambda w, tau, n: online.rom_leapfrog(topo, co, gt, qt, w, tau, n)), "NumPy", os.cpu_count()
 
 
 def oracle_rate(n_src: int, n_steps_sample: int):
