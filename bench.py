@@ -665,8 +665,9 @@ def run_surrogate(args):
 
 
 def run_accuracy(args):
-    """ROM against the fine grid at equal receiver accuracy, at the operating point of the paper's
-    experiments (Section 7: cells about one minimum wavelength across, m = 4).
+    """ROM against the fine grid at equal receiver accuracy, by default at the operating point of
+    the paper's experiments (Section 7: cells about one minimum wavelength across, m = 4);
+    ``--acc-band nyquist --acc-m 6`` measures the 1/10-Nyquist band with more layers.
 
     The 3D layered recipe on an n^3 grid of 16^3-voxel cells, band limit with a minimum wavelength
     of one cell edge, 8 surface sources, fine-grid CFL step for both.  For each face-mode count:
@@ -681,8 +682,8 @@ def run_accuracy(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     modes = [int(x) for x in args.acc_modes.split(",")]
-    wl = synth.workload_3d_layers(args.acc_n, 16, m=4, n_modes=modes[0], n_src=8, n_steps=args.acc_steps,
-                                  band="cell")
+    wl = synth.workload_3d_layers(args.acc_n, 16, m=args.acc_m, n_modes=modes[0], n_src=8, n_steps=args.acc_steps,
+                                  band=args.acc_band)
     L = P.Operator(wl.grid, wl.sigma, wl.rho)
     LP = P.Partition(L, wl.cell, np.concatenate([wl.src_nodes, wl.rcv_nodes]).astype(np.int32))
     lam = L.lambda_max(1e-7)
@@ -718,7 +719,7 @@ def run_accuracy(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         try:
-            LR = P.Rom.build(LP, 4, nm, s, cg_tol=1e-13)
+            LR = P.Rom.build(LP, args.acc_m, nm, s, cg_tol=1e-13)
         except P.MssError as ex:        # e.g. a coefficient block that is not SPD: reported, not fatal
             rows.append({"face_modes": nm, "error": str(ex)})
             continue
@@ -735,8 +736,9 @@ def run_accuracy(args):
                      "fine_fp32_over_rom_fp32_time": t_f32 / t32})
         del LR
     ncells = int(LP.info()[0])
-    out = {"mode": "accuracy", "workload": "3d_layers_%d band=cell: %d^3 voxels, %d cells of 16^3, m=4, %d sources, "
-                                          "%d receivers, %d steps" % (args.acc_n, args.acc_n, ncells, S, R, nst),
+    out = {"mode": "accuracy", "workload": "3d_layers_%d band=%s: %d^3 voxels, %d cells of 16^3, m=%d, %d sources, "
+                                          "%d receivers, %d steps" % (args.acc_n, args.acc_band, args.acc_n, ncells,
+                                                                      args.acc_m, S, R, nst),
            "f_peak": wl.f_peak, "f_max": wl.f_max, "tau": tau,
            "fine_fp32_ms_per_time_step": 1e3 * t_f32 / nst, "fine_fp64_ms_per_time_step": 1e3 * t_f64 / nst,
            "rel_l2_fine_fp32_vs_fine_fp64": rel(f32, ref), "roms": rows}
@@ -766,6 +768,9 @@ def main():
     ap.add_argument("--acc-n", type=int, default=64, help="voxels per edge of --accuracy")
     ap.add_argument("--acc-modes", default="15,28,45", help="face-mode counts of --accuracy")
     ap.add_argument("--acc-steps", type=int, default=3000)
+    ap.add_argument("--acc-m", type=int, default=4, help="S-fraction layers of --accuracy")
+    ap.add_argument("--acc-band", default="cell", choices=["cell", "nyquist"],
+                    help="band of --accuracy: one minimum wavelength per cell, or peak at 1/10 grid Nyquist")
     args = ap.parse_args()
     if args.accuracy:
         run_accuracy(args)
