@@ -417,6 +417,11 @@ def run_native(args):
     cpu = None
     if rank == 0 and world == 1:
         cpu = oracle_baseline(S)
+    # ---- CFL check of the bench's tau through the sim's own kernels (not timed; state restored)
+    try:
+        stability = {"growth_over_300_source_free_steps": sim.check_stability(300, seed=1), "tau": tau}
+    except P.MssError as ex:
+        stability = {"error": str(ex), "tau": tau}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -446,6 +451,7 @@ def run_native(args):
             "speedup_vs_fine_grid": tfine / t_step,
             "receiver_rel_l2": {"fp32_vs_fp64_rom": rel(tr32, ref64), "rom_fp64_vs_fine_fp32": rel(ref64, fine_tr)},
             "offline_s": {"assemble_partition_cfl": t1 - t0, "gpu_rom_build": t2 - t1},
+            "stability": stability,
             "tau": tau}
     print(json.dumps(line))
     if dist:
