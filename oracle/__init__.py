@@ -25,6 +25,8 @@ Modules
                Eqs. intrtstep_td, bdrytstep, solatrec) and its discrete energy.
 ``freq``       frequency-domain coupled ROM (Algorithm alg2red) and transfer
                functions of cells and skeleton.
+``elastic``    VTI elastic fine-grid pencil (Q1 elements, lumped mass, Thomsen's
+               parameters), the first step of the elastic workload (Section 7).
 ``c_leapfrog`` the ROM and fine-grid leapfrog loops again in plain C with OpenMP
                (``c/leapfrog.c``), checked against ``online`` / ``fine``; the
                host-core timing path of the bench's CPU baseline.
