@@ -189,6 +189,16 @@ mss_status mss_rom_export(const mss_rom *r, int32_t *cell_m, int32_t *cell_face_
 /* Face bases S_f (K_f x M_f, row-major, concatenated over faces) of a ROM built by
  * mss_build_roms; sizes: sum K_f M_f. */
 mss_status mss_rom_face_bases(const mss_rom *r, int64_t *count, double *bases);
+/* Caller-supplied face bases S_f in place of the DCT modes, for example the frequency-limited
+ * Gramian basis of Eq. trgr (Section 4.1).  They apply to every later mss_build_roms /
+ * mss_rom_skeleton / mss_rom_rebuild_cells of p, which ignore n_modes for those faces.
+ * face_M[f] = M_f columns of face f (1 <= M_f <= K_f, K_f its node count from
+ * mss_partition_faces), or 0 to keep the DCT modes there.  bases holds, face by face, the
+ * faces with M_f > 0 as K_f x M_f row-major blocks in the face's node order (host buffer, copied).
+ * n_faces must be the partition's face count; n_faces = 0 clears the bases.
+ * Errors: INVALID_ARG (count, sizes, or columns not orthonormal to 1e-10). */
+mss_status mss_partition_set_face_bases(mss_partition *p, int32_t n_faces, const int32_t *face_M,
+                                        const double *bases);
 
 /* Projected inputs/outputs (Eq. BEINCr g~_f = S_f^T g|_f, Eq. solatrec q~_f = S_f^T q|_f) from
  * point sources/receivers at fine-grid nodes with weights (NULL = 1); a node of the corner set

@@ -83,6 +83,7 @@ _SIGS = [
     ("mss_partition_info", C.c_int32, [_P, _P]),
     ("mss_partition_faces", C.c_int32, [_P, _P, _P, _P, _P, _P, _P]),
     ("mss_partition_cell", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
+    ("mss_partition_set_face_bases", C.c_int32, [_P, C.c_int32, _P, _P]),
     ("mss_partition_destroy", None, [_P]),
     ("mss_build_roms", C.c_int32, [_P, _P, _P, _P, _P]),
     ("mss_rom_import", C.c_int32, [_P, _P]),
@@ -267,6 +268,17 @@ class Partition(_Handle):
         _check(lib().mss_partition_faces(self._h, _ptr(kind), _ptr(cells), _ptr(shape), _ptr(ptr), _ptr(nodes),
                                          _ptr(par)))
         return kind, cells.reshape(F, 2), shape.reshape(F, 2), ptr, nodes, par
+
+    def set_face_bases(self, bases) -> None:
+        """Caller-supplied face bases (mss_partition_set_face_bases): one K_f x M_f array per face,
+        or None for a face that keeps the DCT modes; ``bases=None`` clears them."""
+        if bases is None:
+            _check(lib().mss_partition_set_face_bases(self._h, 0, None, None))
+            return
+        fM = np.array([0 if b is None else np.asarray(b).shape[1] for b in bases], np.int32)
+        flat = [np.ascontiguousarray(b, dtype=np.float64).ravel() for b in bases if b is not None]
+        data = np.concatenate(flat) if flat else np.zeros(1)
+        _check(lib().mss_partition_set_face_bases(self._h, int(len(bases)), _ptr(fM), _ptr(data)))
 
     def cell(self, c: int):
         cnt = np.zeros(4, np.int64)

@@ -112,6 +112,10 @@ struct Partition {
   std::vector<int64_t> corner_set;    // unknowns with > 1 face
   int64_t Np = 0;
   std::vector<int64_t> prime_parent;
+  // face bases set by the caller (mss_partition_set_face_bases): per face K_f x M_f row-major, or
+  // empty where the DCT reading applies
+  std::vector<std::vector<double>> user_bases;
+  std::vector<int> user_M;
 
   int faces_of(int64_t u, const int32_t **list) const {
     *list = nf_face.data() + nf_ptr[u];

@@ -756,7 +756,12 @@ static void rom_topology(Partition &P, const mss_rom_params &prm, const int32_t 
   for (int f = 0; f < nf; ++f) {
     std::vector<double> S;
     int M = 0;
-    face_basis(P.faces[f], prm.n_modes, S, M);
+    if (f < (int)P.user_bases.size() && !P.user_bases[f].empty()) {
+      S = P.user_bases[f];
+      M = P.user_M[f];
+    } else {
+      face_basis(P.faces[f], prm.n_modes, S, M);
+    }
     R.face_M[f] = M;
     R.face_K[f] = (int32_t)P.faces[f].nodes.size();
     R.bases.insert(R.bases.end(), S.begin(), S.end());

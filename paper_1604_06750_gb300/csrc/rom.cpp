@@ -203,6 +203,42 @@ mss_status mss_rom_face_bases(const mss_rom *r, int64_t *count, double *bases) {
   });
 }
 
+mss_status mss_partition_set_face_bases(mss_partition *p, int32_t n_faces, const int32_t *face_M,
+                                        const double *bases) {
+  return guard([&] {
+    MSS_REQUIRE(p, MSS_ERR_INVALID_ARG, "null argument");
+    Partition &P = p->p;
+    if (n_faces == 0) {
+      P.user_bases.clear();
+      P.user_M.clear();
+      return;
+    }
+    const int nf = (int)P.faces.size();
+    MSS_REQUIRE(n_faces == nf && face_M && bases, MSS_ERR_INVALID_ARG, "need face_M and bases for every face");
+    std::vector<std::vector<double>> ub(nf);
+    std::vector<int> um(nf, 0);
+    size_t o = 0;
+    for (int f = 0; f < nf; ++f) {
+      const int K = (int)P.faces[f].nodes.size(), M = face_M[f];
+      MSS_REQUIRE(M >= 0 && M <= K, MSS_ERR_INVALID_ARG, "face_M[f] must lie in 0..K_f");
+      if (M == 0) continue;
+      const double *S = bases + o;
+      o += (size_t)K * M;
+      for (int a = 0; a < M; ++a)
+        for (int b = 0; b <= a; ++b) {
+          double g = 0.0;
+          for (int r = 0; r < K; ++r) g += S[(size_t)r * M + a] * S[(size_t)r * M + b];
+          MSS_REQUIRE(std::abs(g - (a == b ? 1.0 : 0.0)) <= 1e-10, MSS_ERR_INVALID_ARG,
+                      "face basis columns are not orthonormal");
+        }
+      ub[f].assign(S, S + (size_t)K * M);
+      um[f] = M;
+    }
+    P.user_bases.swap(ub);
+    P.user_M.swap(um);
+  });
+}
+
 mss_status mss_rom_set_io(mss_rom *r, int32_t n_src, int32_t n_src_entries, const int32_t *src_face,
                           const int32_t *src_index, const double *src_vals, int32_t n_rcv, int32_t n_rcv_entries,
                           const int32_t *rcv_face, const int32_t *rcv_index, const double *rcv_vals) {

@@ -74,3 +74,48 @@ def test_skeleton_matches_oracle(P, name, wl):
         assert np.allclose(bases[o:o + B.size].reshape(B.shape), B, rtol=0, atol=1e-14)
         o += B.size
     assert o == bases.size
+
+
+def test_caller_face_bases_match_oracle(P):
+    """mss_partition_set_face_bases: the paper's Gramian basis (Eq. trgr), computed by the oracle,
+    passed to the library; the skeleton's Gamma-hat^1, face masses and bases follow it."""
+    wl = synth.workload_2d_layers(32, 8, m=3, n_modes=4, n_steps=10)
+    op = fine.FineOperator(wl.grid, wl.sigma, wl.rho)
+    io_list = [tuple(int(x) for x in p) for p in list(wl.src_nodes) + list(wl.rcv_nodes)]
+    part = partition.Partition(op, wl.sigma, wl.rho, wl.cell, io_nodes=io_list)
+    s = -rom.omega_max(wl.f_max) ** 2
+    gb = rom.gramian_bases(part, -s, 3)
+    given = [None if f.kind == "io" else gb[f.id] for f in part.faces]   # I/O faces keep the default
+    R = rom.build_rom(part, wl.m, wl.n_modes, s, bases=[rom.face_basis(f, 4) if b is None else b
+                                                        for f, b in zip(part.faces, given)])
+    L = P.Operator(wl.grid, wl.sigma, wl.rho)
+    LP = P.Partition(L, wl.cell, np.concatenate([wl.src_nodes, wl.rcv_nodes]).astype(np.int32))
+    LP.set_face_bases(given)
+    SK = P.Rom.skeleton(LP, wl.m, wl.n_modes, s)
+    cm, cfp, cf, fM, fc, g, gh, fm = SK.export()
+    assert list(fM) == list(R.topology.face_M)
+    o = 0
+    for c in range(R.topology.n_cells):
+        K = int(R.topology.cell_K()[c])
+        ref = R.coeffs.gamma_hat[c][0]
+        assert np.linalg.norm(gh[o:o + K * K].reshape(K, K) - ref) <= TOL * np.linalg.norm(ref)
+        o += int(cm[c]) * K * K
+    o = 0
+    for f, M in enumerate(fM):
+        ref = R.coeffs.face_mass[f]
+        assert np.linalg.norm(fm[o:o + M * M].reshape(M, M) - ref) <= TOL * np.linalg.norm(ref)
+        o += M * M
+    bases = SK.face_bases()
+    o = 0
+    for B in R.bases:
+        assert np.allclose(bases[o:o + B.size].reshape(B.shape), B, rtol=0, atol=1e-14)
+        o += B.size
+    # clearing restores the DCT reading; bad input is refused
+    LP.set_face_bases(None)
+    assert list(P.Rom.skeleton(LP, wl.m, wl.n_modes, s).export()[3]) == [4 if f.kind != "io" else len(f.nodes)
+                                                                        for f in part.faces]
+    bad = [None if b is None else 2.0 * b for b in given]
+    with pytest.raises(P.MssError):
+        LP.set_face_bases(bad)
+    with pytest.raises(P.MssError):
+        LP.set_face_bases(given[:-1])
