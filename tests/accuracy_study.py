@@ -10,6 +10,7 @@ and prints the receiver relative L2 error.
     python tests/accuracy_study.py --n 64 --band nyquist --modes 15 --m 6
     python tests/accuracy_study.py --n 64 --band nyquist --modes 15 --m 8 --clamp-last
     python tests/accuracy_study.py --n 32 --band cell --modes 6 10 --basis gramian
+    python tests/accuracy_study.py --n 64 --band cell --modes 15 28 45 --basis gramian --eig chebyshev
     python tests/accuracy_study.py --workload 2d --modes 2 3 4 --basis gramian
     python tests/accuracy_study.py --n 64 --band cell --modes 45 --sources 8 --fp32 plain fp64-last chol-last
 
@@ -26,6 +27,7 @@ import sys
 import time
 
 import numpy as np
+import scipy.sparse as sp
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -55,6 +57,32 @@ def clamped_gamma_trans(alphas, betas):
             G = np.linalg.solve(G.T @ Gk, betas[k + 1].T)
         Gprev = Gk
     return gam, gh
+
+
+def chebyshev_modes(A, Bd, lam_cut: float, p: int = 200, deg: int = 150, iters: int = 15, seed: int = 0):
+    """Approximate propagative eigenpairs (lam <= lam_cut) of the pencil for grids where shift-invert
+    Lanczos is too slow: subspace iteration on B^{-1/2}(-A)B^{-1/2} with a degree-``deg`` Chebyshev
+    filter that damps [lam_cut, lam_max], Rayleigh-Ritz after each pass.  Modes near the cut
+    converge slowest; the residuals are printed.  Returns (lam, Z) with Z^T B Z = I."""
+    bh = 1.0 / np.sqrt(Bd)
+    M = (sp.diags(bh) @ (-A) @ sp.diags(bh)).tocsr()
+    lmax = 1.05 * fine.lambda_max(A, Bd)
+    e, c = (lmax - lam_cut) / 2, (lmax + lam_cut) / 2
+    X = np.linalg.qr(np.random.default_rng(seed).standard_normal((M.shape[0], p)))[0]
+    for it in range(iters):
+        Y0, Y1 = X, (M @ X - c * X) / e
+        for _ in range(2, deg + 1):
+            Y0, Y1 = Y1, 2 * (M @ Y1 - c * Y1) / e - Y0
+        X = np.linalg.qr(Y1)[0]
+        H = X.T @ (M @ X)
+        w, V = np.linalg.eigh(0.5 * (H + H.T))
+        X = X @ V
+        res = np.linalg.norm(M @ X - X * w, axis=0)
+        keep = w <= lam_cut
+        print("chebyshev pass %d: %d modes below the cut, largest residual %.2e (cut %.3g)"
+              % (it, int(keep.sum()), res[keep].max() if keep.any() else 0.0, lam_cut), flush=True)
+    keep = w <= lam_cut
+    return w[keep], bh[:, None] * X[:, keep]
 
 
 def rom_leapfrog_fp32(R, gt, qt, w, tau, n_steps, corners, last="plain"):
@@ -124,6 +152,8 @@ def main():
     ap.add_argument("--sources", type=int, default=2)
     ap.add_argument("--steps", type=int, default=0, help="time steps (default: 1500 at n=32, 3000 else)")
     ap.add_argument("--basis", choices=["dct", "gramian"], default="dct")
+    ap.add_argument("--eig", choices=["lanczos", "chebyshev"], default="lanczos",
+                    help="eigensolver of the Gramian basis (chebyshev: approximate, for 64^3 and up)")
     ap.add_argument("--clamp-last", action="store_true")
     ap.add_argument("--fp32", nargs="*", default=[], choices=["plain", "fp64-last", "chol-last"])
     a = ap.parse_args()
@@ -149,7 +179,10 @@ def main():
     ref = fine.fine_leapfrog(op.A.tocsr(), op.B, g, q, w, tau, nst)
     if a.clamp_last:
         rom.gamma_trans = clamped_gamma_trans
-    modes = rom.propagative_modes(op.A, op.B, lam) if a.basis == "gramian" else None
+    modes = None
+    if a.basis == "gramian":
+        modes = (chebyshev_modes(op.A, op.B, lam) if a.eig == "chebyshev"
+                 else rom.propagative_modes(op.A, op.B, lam))
     for nm in a.modes:
         t0 = time.perf_counter()
         bases = rom.gramian_bases(part, lam, nm, modes=modes) if modes is not None else None
