@@ -85,6 +85,32 @@ def chebyshev_modes(A, Bd, lam_cut: float, p: int = 200, deg: int = 150, iters: 
     return w[keep], bh[:, None] * X[:, keep]
 
 
+def hybrid_bases(part, modes, n_modes: int, rel_tol: float = 1e-8):
+    """Face bases that start with the range of the face's Gramian (eigenvalues above rel_tol of the
+    largest, at most n_modes) and continue with the DCT modes orthogonalised against it (the DCT
+    order of ``rom.face_basis``), n_modes columns in all.  I/O faces keep S_f = I."""
+    out = []
+    for f, G in zip(part.faces, rom.face_gramians(part, modes)):
+        if G is None:
+            out.append(np.eye(len(f.nodes)))
+            continue
+        w, Q = np.linalg.eigh(G)
+        w, Q = w[::-1], Q[:, ::-1]
+        M = min(n_modes, len(f.nodes))
+        cols = [Q[:, j] for j in range(min(M, int(np.sum(w > rel_tol * w[0]))))]
+        for d in rom.face_basis(f, len(f.nodes)).T:
+            if len(cols) >= M:
+                break
+            for _ in range(2):
+                for c in cols:
+                    d = d - (c @ d) * c
+            nd = np.linalg.norm(d)
+            if nd > 1e-6:
+                cols.append(d / nd)
+        out.append(np.stack(cols, axis=1))
+    return out
+
+
 def rom_leapfrog_fp32(R, gt, qt, w, tau, n_steps, corners, last="plain"):
     """The oracle's ROM leapfrog with every array in float32; ``last`` is how the last flux
     product Gamma^m (U^{m+1} - U^m) is formed: "plain", "fp64-last" or "chol-last"."""
@@ -151,7 +177,7 @@ def main():
     ap.add_argument("--m", type=int, default=4)
     ap.add_argument("--sources", type=int, default=2)
     ap.add_argument("--steps", type=int, default=0, help="time steps (default: 1500 at n=32, 3000 else)")
-    ap.add_argument("--basis", choices=["dct", "gramian"], default="dct")
+    ap.add_argument("--basis", choices=["dct", "gramian", "hybrid"], default="dct")
     ap.add_argument("--eig", choices=["lanczos", "chebyshev"], default="lanczos",
                     help="eigensolver of the Gramian basis (chebyshev: approximate, for 64^3 and up)")
     ap.add_argument("--clamp-last", action="store_true")
@@ -180,12 +206,16 @@ def main():
     if a.clamp_last:
         rom.gamma_trans = clamped_gamma_trans
     modes = None
-    if a.basis == "gramian":
+    if a.basis in ("gramian", "hybrid"):
         modes = (chebyshev_modes(op.A, op.B, lam) if a.eig == "chebyshev"
                  else rom.propagative_modes(op.A, op.B, lam))
     for nm in a.modes:
         t0 = time.perf_counter()
-        bases = rom.gramian_bases(part, lam, nm, modes=modes) if modes is not None else None
+        bases = None
+        if a.basis == "gramian":
+            bases = rom.gramian_bases(part, lam, nm, modes=modes)
+        elif a.basis == "hybrid":
+            bases = hybrid_bases(part, modes, nm)
         R = rom.build_rom(part, a.m, nm, -lam, bases=bases)
         gt = rom.project_io(part, R.bases, part.prime_vectors(wl.src_nodes))
         qt = [x.T for x in rom.project_io(part, R.bases, part.prime_vectors(wl.rcv_nodes))]
