@@ -326,7 +326,8 @@ def run_native(args):
         peaks = json.load(open(pk))
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12             # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12            # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
     cell_s = ms[0] / 1e3
     achieved_gbs = algo_bytes / cell_s / 1e9
     achieved_tf = algo_flops / cell_s / 1e12

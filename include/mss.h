@@ -488,16 +488,20 @@ typedef struct mss_step_buffers {
   void *face_state[2], *cell_state_buf[2];
 } mss_step_buffers;
 
-/* n_steps of the on-line step (Algorithm alg1red stage 2 without the Appendix D correction),
- * launched eagerly on `stream` with the flux exchange in the library's fixed scratch array.
+/* n_steps of the same step as mss_step without the corner correction, launched eagerly on
+ * `stream` with the flux exchange in the library's fixed scratch array.
  * waveform: device FP64, n_steps samples; traces: device [n_steps][R][S] of the precision.
  * Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).  The first call on a
  * device looks up the scratch array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call on a device shares the
+ * current; make that first call before any stream capture.  The address is cached for the rest
+ * of the process: after cudaDeviceReset on a device, do not call this entry point on it again
+ * (the cached address would be stale).  Every call on a device shares the
  * one scratch array and leaves its contents behind (the step writes every flux slot before it
  * reads it, so nothing needs clearing); calls that overlap on the GPU (different streams, or
  * different threads) race on it and must be serialised by the caller.
- * The four state buffers must be 16-byte aligned (vector loads).
+ * The four state buffers must be 16-byte aligned (vector loads).  face_rows must equal FR, the
+ * sum of face_M: the kernels index the scratch through face_row and row_face_row, so a smaller
+ * face_rows passes the size check below and then writes past the end of the scratch array.
  * Errors: INVALID_ARG (null pointers, counts, precision, alignment), INVALID_ARG if 2 FR S x
  * element size exceeds MSS_NOALLOC_SCRATCH_BYTES, CUDA. */
 mss_status mss_step_noalloc(mss_step_buffers *b, int64_t n_steps, const double *waveform, void *traces,

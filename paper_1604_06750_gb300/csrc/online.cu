@@ -1372,7 +1372,9 @@ static void state_io(mss_sim &s, double *now, double *old, const double *inow, c
 // ------------------------------------------------------------------ stepping without allocation
 // The flux exchange of the allocation-free step lives in this fixed file-scope array; host code
 // must not pass the symbol itself to a kernel (in host code it names a host-side stand-in), so
-// its device address is looked up once per device and cached.
+// its device address is looked up once per device and cached.  The cache is not invalidated:
+// after cudaDeviceReset on a device the cached address is stale, so a process that resets a
+// device must not call the allocation-free step on it again.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MSS_NOALLOC_SCRATCH_BYTES];
 
 namespace mss {
@@ -1498,10 +1500,15 @@ mss_status mss_step_noalloc(mss_step_buffers *b, int64_t n_steps, const double *
     for (const void *q : {b->face_state[0], b->face_state[1], b->cell_state_buf[0], b->cell_state_buf[1]})
       MSS_REQUIRE(((uintptr_t)q & 15) == 0, MSS_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     const size_t es = b->precision == MSS_FP64 ? 8 : 4;
-    const size_t need = (size_t)b->face_rows * 2 * (size_t)b->n_src * es;
-    MSS_REQUIRE(need <= MSS_NOALLOC_SCRATCH_BYTES, MSS_ERR_INVALID_ARG,
-                "flux exchange needs " + std::to_string(need) + " bytes, above the fixed scratch of " +
-                    std::to_string((size_t)MSS_NOALLOC_SCRATCH_BYTES) + " bytes");
+    // rows the fixed scratch can hold for this source count; compared without forming the
+    // product face_rows * 2 * n_src * es, which could wrap around for a huge face_rows
+    const size_t row_bytes = 2 * (size_t)b->n_src * es;
+    const size_t max_rows = (size_t)MSS_NOALLOC_SCRATCH_BYTES / row_bytes;
+    MSS_REQUIRE((uint64_t)b->face_rows <= (uint64_t)max_rows, MSS_ERR_INVALID_ARG,
+                "flux exchange of " + std::to_string(b->face_rows) + " face rows x " + std::to_string(b->n_src) +
+                    " sources needs more than the fixed scratch of " +
+                    std::to_string((size_t)MSS_NOALLOC_SCRATCH_BYTES) + " bytes (at most " +
+                    std::to_string(max_rows) + " face rows)");
     if (n_steps == 0) return;
     void *scratch = noalloc_scratch();
     cudaStream_t st = (cudaStream_t)stream;
