@@ -234,12 +234,22 @@ typedef struct mss_sim mss_sim;
  * trace sample n = sum_f q~_f^T u~_f at step n (before it is advanced).
  * precision: MSS_FP64, MSS_FP32 (state, coefficients and arithmetic), MSS_FP32_TC or MSS_BF16_TC
  * (FP32 state, tensor-core cell products; traces are float).
- * corner_correction: 0/1.  Needs I/O set on the ROM (n_src >= 1).
+ * flags: MSS_SIM_CORNERS (the Appendix D correction; 1 keeps its old meaning) | MSS_SIM_FACTOR_LAST
+ * (MSS_FP32 only: the last coefficient is applied as F^m = L (L^T D^m), L the lower Cholesky factor
+ * of Gamma^m computed in FP64 at creation, pivots at or below 1e-13 of its largest diagonal entry
+ * raised to that floor; stored as one K x K matrix W = L + L^T - diag(L), so the coefficient bytes
+ * do not change.  Rounding the entries of a nearly singular Gamma^m -- a cell without a Dirichlet
+ * node, whose constant mode makes it semidefinite, Eq. intrtstep_td with Lemma lemStil -- to FP32
+ * can make it indefinite; a rounded factor keeps L L^T semidefinite.  Schedules GRAPH and PERSIST.
+ * COEF_NOT_SPD if a Gamma^m is indefinite beyond -1e-8 of its scale).  Needs I/O set on the ROM
+ * (n_src >= 1).
  * The sim copies what it needs from the ROM (the ROM may be destroyed afterwards).
- * Errors: INVALID_ARG, STATE (ROM without I/O), CFL (tau <= 0), CUDA, OOM, TIMEOUT (a tensor-core
+ * Errors: INVALID_ARG (unknown flags), STATE (ROM without I/O), CFL (tau <= 0), COEF_NOT_SPD, CUDA,
+ * OOM, TIMEOUT (a tensor-core
  * kernel's bounded wait gave up; reported by the next mss_step / mss_sim_info call). */
-mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32_t corner_correction,
-                          mss_sim **out);
+#define MSS_SIM_CORNERS 1
+#define MSS_SIM_FACTOR_LAST 2
+mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32_t flags, mss_sim **out);
 /* info: [0] sources, [1] receivers, [2] precision, [3] steps taken, [4] state values per level,
  *       [5] device bytes held, [6] kernels launched per step, [7] source tile. */
 mss_status mss_sim_info(const mss_sim *s, int64_t info[8]);

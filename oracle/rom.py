@@ -32,6 +32,8 @@ Readings (where the paper is silent, garbled or inconsistent):
       Gamma^k = -G_k^{-T} alpha_k G_k^{-1} - Gamma^{k-1},
       G_{k+1} = (G_k^T Gamma^k)^{-1} beta_{k+1}^T,
   with beta from QR (positive diagonal).
+* The last coefficient Gamma^m may be positive semidefinite (floating cells: the constant
+  mode); it is accepted through a Cholesky factor with floored pivots (``psd_cholesky``).
 """
 from __future__ import annotations
 
@@ -235,8 +237,47 @@ def block_lanczos(Am: np.ndarray, Sm: np.ndarray, m: int):
 
 
 # --------------------------------------------------------------------------- S-fraction coefficients (Eq. GammaTrans)
+PSD_FLOOR = 1e-13      # pivot floor of the last coefficient, relative to its largest diagonal entry
+PSD_NEG_TOL = 1e-8     # most negative pivot still read as rounding of a semidefinite matrix
+
+
+def psd_cholesky(M: np.ndarray, floor: float = PSD_FLOOR, neg_tol: float = PSD_NEG_TOL):
+    """Lower factor L of a positive semidefinite M, L L^T = M + E (reading R24).
+
+    Column-by-column Cholesky in which a pivot d_j <= floor * s (s = max_i M_ii) is raised to
+    floor * s; a pivot below -neg_tol * s means M is indefinite beyond rounding (COEF_NOT_SPD).
+    E is then diagonal with 0 <= E_jj <= (floor + neg_tol) s, and L L^T is checked to stay that
+    close to M (a floored pivot met early could otherwise amplify rounding).  Returns (L, number
+    of floored pivots).
+    """
+    n = M.shape[0]
+    s = float(np.max(np.diag(M)))
+    if not s > 0:
+        raise RomError("last coefficient has no positive diagonal")
+    L = np.zeros_like(M)
+    floored = 0
+    for j in range(n):
+        d = M[j, j] - L[j, :j] @ L[j, :j]
+        if d <= floor * s:
+            if d < -neg_tol * s:
+                raise RomError("last coefficient is indefinite (pivot %.3e of scale %.3e)" % (d, s))
+            d = floor * s
+            floored += 1
+        L[j, j] = np.sqrt(d)
+        L[j + 1:, j] = (M[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    if floored and np.max(np.abs(L @ L.T - M)) > 10.0 * (floor + neg_tol) * s:
+        raise RomError("semidefinite factor of the last coefficient lost accuracy")
+    return L, floored
+
+
 def gamma_trans(alphas: List[np.ndarray], betas: List[np.ndarray]):
-    """Gamma^k, Gamma-hat^k (k = 1..m) from the block Lanczos coefficients (module readings)."""
+    """Gamma^k, Gamma-hat^k (k = 1..m) from the block Lanczos coefficients (module readings).
+
+    Gamma^1..Gamma^{m-1} and every Gamma-hat^k must be SPD.  The last coefficient Gamma^m may be
+    positive semidefinite (reading R24): a cell with no Dirichlet node has the constant as a null
+    vector of A_i, which the Krylov space nearly contains, so Gamma^m has an eigenvalue at the
+    level of rounding.  It is factored by ``psd_cholesky``; if a pivot had to be floored, Gamma^m
+    is replaced by L L^T (exactly semidefinite, within 1e-8 of the computed matrix)."""
     m = len(alphas)
     G = betas[0].T.copy()
     Gprev = np.zeros_like(G)
@@ -247,7 +288,12 @@ def gamma_trans(alphas: List[np.ndarray], betas: List[np.ndarray]):
         Gk = -Gi.T @ alphas[k] @ Gi - Gprev
         Gk = 0.5 * (Gk + Gk.T)
         Gh = 0.5 * (Gh + Gh.T)
-        for M, nm in ((Gk, "Gamma"), (Gh, "Gamma-hat")):
+        if k + 1 == m:
+            L, floored = psd_cholesky(Gk)
+            if floored:
+                Gk = L @ L.T
+                Gk = 0.5 * (Gk + Gk.T)
+        for M, nm in (((Gk, "Gamma"),) if k + 1 < m else ()) + ((Gh, "Gamma-hat"),):
             try:
                 np.linalg.cholesky(M)
             except np.linalg.LinAlgError:

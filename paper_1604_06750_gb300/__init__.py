@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libmss.so")
 FP64, FP32, FP32_TC, BF16_TC = 0, 1, 2, 3
 SCHED_GRAPH, SCHED_GRAPH_STREAM, SCHED_PERSIST, SCHED_PERSIST_STREAM, SCHED_GRAPH_SPLIT = 0, 1, 2, 3, 4
 SCHED_COUNT = 5
+SIM_CORNERS, SIM_FACTOR_LAST = 1, 2
 DEBUG_GRID_EXTRA_ARRIVALS, DEBUG_TC_EXTRA_TX = 1, 2
 DIRICHLET, NEUMANN = 0, 1
 
@@ -453,10 +454,11 @@ class Sim(_Handle):
 
     _destroy = "mss_sim_destroy"
 
-    def __init__(self, rom: Rom, precision: int, tau: float, corner_correction: bool = False):
+    def __init__(self, rom: Rom, precision: int, tau: float, corner_correction: bool = False,
+                 factor_last: bool = False):
         super().__init__()
-        _check(lib().mss_sim_create(rom._h, int(precision), C.c_double(tau), int(bool(corner_correction)),
-                                    C.byref(self._h)))
+        flags = (SIM_CORNERS if corner_correction else 0) | (SIM_FACTOR_LAST if factor_last else 0)
+        _check(lib().mss_sim_create(rom._h, int(precision), C.c_double(tau), flags, C.byref(self._h)))
         self.precision = precision
         i = self.info()
         self.n_src, self.n_rcv, self.state_size = int(i[0]), int(i[1]), int(i[4])

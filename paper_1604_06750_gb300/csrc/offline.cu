@@ -27,6 +27,11 @@ namespace mss {
 namespace {
 
 constexpr int kThreads = 256;
+// The last S-fraction coefficient may be positive semidefinite (a cell without a Dirichlet node keeps
+// the constant mode): pivot floor of its Cholesky factor and the most negative pivot still taken as
+// rounding, both relative to its largest diagonal entry.
+constexpr double kPsdFloor = 1e-13;
+constexpr double kPsdNegTol = 1e-8;
 
 __device__ __forceinline__ int cell_of_row(const int64_t *row0, int nc, int64_t r) {
   int lo = 0, hi = nc - 1;
@@ -259,6 +264,50 @@ __device__ bool bchol(double *A, int lda, int n, double tol) {
   return ok != 0;
 }
 
+// Cholesky factor of a positive semidefinite matrix (the last S-fraction coefficient of a cell that
+// holds no Dirichlet node, where the constant mode makes it singular up to rounding): as bchol, but a
+// pivot d <= floor_rel * s (s = largest diagonal entry) is raised to floor_rel * s, and a pivot below
+// -neg_rel * s means the matrix is indefinite.  Returns the number of raised pivots, or -1 if
+// indefinite (or without a positive diagonal).  A holds L in its lower part, upper part cleared.
+__device__ int bchol_psd(double *A, int lda, int n, double floor_rel, double neg_rel) {
+  __shared__ int floored;
+  __shared__ double scale;
+  if (threadIdx.x == 0) {
+    double sc = 0;
+    for (int i = 0; i < n; ++i) sc = fmax(sc, A[(int64_t)i * lda + i]);
+    scale = sc;
+    floored = sc > 0 ? 0 : -1;
+  }
+  __syncthreads();
+  if (floored < 0) return -1;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = A[(int64_t)j * lda + j];
+      if (!(d > floor_rel * scale)) {
+        if (!(d >= -neg_rel * scale)) floored = -1;
+        else if (floored >= 0) ++floored;
+        d = floor_rel * scale;
+      }
+      A[(int64_t)j * lda + j] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = A[(int64_t)j * lda + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * lda + j] /= piv;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < (n - j - 1) * (n - j - 1); idx += blockDim.x) {
+      const int i = j + 1 + idx / (n - j - 1), k = j + 1 + idx % (n - j - 1);
+      if (k <= i) A[(int64_t)i * lda + k] -= A[(int64_t)i * lda + j] * A[(int64_t)k * lda + j];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, k = idx - i * n;
+    if (k > i) A[(int64_t)i * lda + k] = 0.0;
+  }
+  __syncthreads();
+  return floored;
+}
+
 // Linv = L^{-1} for lower-triangular L (columns solved in parallel).
 __device__ void btrinv_lower(double *Linv, int ldi, const double *L, int ldl, int n) {
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -445,10 +494,36 @@ __global__ void k_lanczos_gamma(const double *Am, const int64_t *am_off, const d
     if (!binverse(k1, K, k2, K, K)) { if (threadIdx.x == 0) atomicExch(status, MSS_ERR_COEF_NOT_SPD); return; }
     bgemm(Gm, K, k2, K, false, beta, K, true, K, K, K, 1.0, 0.0);
   }
-  // SPD checks of all coefficients (Eq. S-fraction: symmetric positive definite)
+  // SPD checks of all coefficients (Eq. S-fraction: symmetric positive definite), except that the
+  // last Gamma^m may be positive semidefinite: it is factored with floored pivots and, if a pivot
+  // was raised, replaced by L L^T, which must stay within 10 (floor + neg) s of it elementwise.
   for (int k = 0; k < m; ++k) {
-    bcopy(k1, K, G + (int64_t)k * K * K, K, K, K, 1.0);
-    if (!bchol(k1, K, K, 0.0)) { if (threadIdx.x == 0) atomicExch(status, MSS_ERR_COEF_NOT_SPD); return; }
+    double *Gk = G + (int64_t)k * K * K;
+    bcopy(k1, K, Gk, K, K, K, 1.0);
+    if (k + 1 < m) {
+      if (!bchol(k1, K, K, 0.0)) { if (threadIdx.x == 0) atomicExch(status, MSS_ERR_COEF_NOT_SPD); return; }
+    } else {
+      const int fl = bchol_psd(k1, K, K, kPsdFloor, kPsdNegTol);
+      if (fl < 0) { if (threadIdx.x == 0) atomicExch(status, MSS_ERR_COEF_NOT_SPD); return; }
+      if (fl > 0) {
+        bgemm(k2, K, k1, K, false, k1, K, true, K, K, K, 1.0, 0.0);      // L L^T
+        bsym(k2, K, K);
+        __shared__ double gap, gsc;
+        if (threadIdx.x == 0) {
+          double g = 0, sc = 0;
+          for (int i = 0; i < K; ++i) sc = fmax(sc, Gk[(int64_t)i * K + i]);
+          for (int i = 0; i < K * K; ++i) g = fmax(g, fabs(k2[i] - Gk[i]));
+          gap = g;
+          gsc = sc;
+        }
+        __syncthreads();
+        if (!(gap <= 10.0 * (kPsdFloor + kPsdNegTol) * gsc)) {
+          if (threadIdx.x == 0) atomicExch(status, MSS_ERR_COEF_NOT_SPD);
+          return;
+        }
+        bcopy(Gk, K, k2, K, K, K, 1.0);
+      }
+    }
     bcopy(k1, K, H + (int64_t)k * K * K, K, K, K, 1.0);
     if (!bchol(k1, K, K, 0.0)) { if (threadIdx.x == 0) atomicExch(status, MSS_ERR_COEF_NOT_SPD); return; }
   }

@@ -24,6 +24,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <thread>
 #include <type_traits>
 
 #include "cuda_util.h"
@@ -57,6 +58,9 @@ struct StepArgs {
   const T *coef, *minv, *src_val, *rcv_val, *cg_rows, *cg_w, *fm_rows;
   T *fstate0, *fstate1, *cstate0, *cstate1, *flux, *uhat;
   int S, n_cells, n_faces, n_rcv, corners, n_cfaces;
+  // 1: the block of Gamma^m in coef holds W = L + L^T - diag(L), L the lower Cholesky factor of
+  // Gamma^m, and F^m = L (L^T D^m) is formed from it in two triangular passes
+  int factor_last;
   T tau2;
 };
 
@@ -122,6 +126,36 @@ __device__ __forceinline__ void row_times_block(const T *__restrict__ G, int K, 
   }
 }
 
+// acc[s] += sum_{c0 <= c < c1} G[c*K] * X[c*ST + s]: the same register-pipelined column stream as
+// row_times_block over a column range (one triangle of a factored coefficient), accumulating.
+template <typename T, int ST>
+__device__ __forceinline__ void row_times_range(const T *__restrict__ G, int K, const T *__restrict__ X, int c0,
+                                                int c1, T (&acc)[ST]) {
+  T g[kChunk], gn[kChunk];
+#pragma unroll
+  for (int j = 0; j < kChunk; ++j) g[j] = c0 + j < c1 ? __ldg(G + (size_t)(c0 + j) * K) : T(0);
+  for (int cb = c0; cb < c1; cb += kChunk) {
+    const int cn = cb + kChunk;
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) gn[j] = (cn + j < c1) ? __ldg(G + (size_t)(cn + j) * K) : T(0);
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+      if (cb + j < c1) {
+        const T *x = X + (cb + j) * ST;
+        if constexpr (std::is_same<T, float>::value && ST % 2 == 0) {
+#pragma unroll
+          for (int s = 0; s < ST; s += 2) fma2(acc[s], acc[s + 1], g[j], x[s], x[s + 1]);
+        } else {
+#pragma unroll
+          for (int s = 0; s < ST; ++s) acc[s] += g[j] * x[s];
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) g[j] = gn[j];
+  }
+}
+
 // 16-byte vector type of T (4 floats or 2 doubles)
 template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
@@ -138,7 +172,9 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
   const int ns = min(ST, a.S - s0);
   T *X = reinterpret_cast<T *>(smem_raw);        // U (layers 1..m, [k][r][s]), then F^k
   T *D = X + (size_t)m * K * ST;                 // U^{k+1} - U^k, then F^k - F^{k-1}
-  int64_t *rows = reinterpret_cast<int64_t *>(D + (size_t)m * K * ST);   // K boundary rows: face row*2+side
+  T *Y = D + (size_t)m * K * ST;                 // factored last coefficient: L^T D^m (even length)
+  const size_t ylen = a.factor_last ? (((size_t)K * ST + 1) & ~(size_t)1) : 0;
+  int64_t *rows = reinterpret_cast<int64_t *>(Y + ylen);   // K boundary rows: face row*2+side
   const T *fs = cur ? a.fstate1 : a.fstate0;
   const T *cs = cur ? a.cstate1 : a.cstate0;
   T *cso = cur ? a.cstate0 : a.cstate1;
@@ -180,14 +216,58 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
   __syncthreads();
   // fluxes F^k = Gamma^k D^k into X (U is not needed any more: the "now" level is re-read below)
   const T *G = a.coef + a.cell_coef[cell];
-  for (int it = threadIdx.x; it < m * K; it += blockDim.x) {
-    const int k = it / K, r = it - k * K;
-    T acc[ST];
-    row_times_block<T, ST>(G + (size_t)k * K * K + r, K, D + (size_t)k * K * ST, acc);
+  if (!a.factor_last) {
+    for (int it = threadIdx.x; it < m * K; it += blockDim.x) {
+      const int k = it / K, r = it - k * K;
+      T acc[ST];
+      row_times_block<T, ST>(G + (size_t)k * K * K + r, K, D + (size_t)k * K * ST, acc);
 #pragma unroll
-    for (int s = 0; s < ST; ++s) X[(size_t)k * K * ST + r * ST + s] = acc[s];
+      for (int s = 0; s < ST; ++s) X[(size_t)k * K * ST + r * ST + s] = acc[s];
+    }
+    __syncthreads();
+  } else {
+    // F^1..F^{m-1} as above; F^m = L (L^T D^m) with W = L + L^T - diag(L) read column by column:
+    // y_r = sum_{c >= r} W[c][r] D^m_c (L^T), then F^m_r = sum_{c <= r} W[c][r] y_c (L).  Rows r
+    // and K-1-r share an item, so every item streams K+1 coefficients of the triangle pair.
+    const T *W = G + (size_t)(m - 1) * K * K;
+    const T *Dm = D + (size_t)(m - 1) * K * ST;
+    const int full = (m - 1) * K, pairs = (K + 1) / 2;
+    for (int it = threadIdx.x; it < full + pairs; it += blockDim.x) {
+      if (it < full) {
+        const int k = it / K, r = it - k * K;
+        T acc[ST];
+        row_times_block<T, ST>(G + (size_t)k * K * K + r, K, D + (size_t)k * K * ST, acc);
+#pragma unroll
+        for (int s = 0; s < ST; ++s) X[(size_t)k * K * ST + r * ST + s] = acc[s];
+      } else {
+        const int p = it - full;
+        for (int h = 0; h < 2; ++h) {
+          const int r = h ? K - 1 - p : p;
+          if (h && r == p) break;
+          T acc[ST];
+#pragma unroll
+          for (int s = 0; s < ST; ++s) acc[s] = T(0);
+          row_times_range<T, ST>(W + r, K, Dm, r, K, acc);
+#pragma unroll
+          for (int s = 0; s < ST; ++s) Y[r * ST + s] = acc[s];
+        }
+      }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < pairs; p += blockDim.x) {
+      for (int h = 0; h < 2; ++h) {
+        const int r = h ? K - 1 - p : p;
+        if (h && r == p) break;
+        T acc[ST];
+#pragma unroll
+        for (int s = 0; s < ST; ++s) acc[s] = T(0);
+        row_times_range<T, ST>(W + r, K, Y, 0, r + 1, acc);
+#pragma unroll
+        for (int s = 0; s < ST; ++s) X[(size_t)(m - 1) * K * ST + r * ST + s] = acc[s];
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // exchange: this cell's F^1 on each of its faces; E^k = F^k - F^{k-1} into D
   if (vec) {
     constexpr int NV = ST >= VN ? ST / VN : 1;
@@ -524,6 +604,7 @@ struct mss_sim {
   mss::TcArgs tca{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
+  int factor_last = 0;                         // FP32: Gamma^m applied as L (L^T .)
   int64_t face_rows = 0, cell_rows = 0;
   int64_t steps = 0;
   int cur = 0;
@@ -605,6 +686,7 @@ static StepArgs<T> make_args(const mss_sim &s) {
   a.n_rcv = s.n_rcv;
   a.corners = s.corners;
   a.n_cfaces = s.n_cfaces;
+  a.factor_last = s.factor_last;
   a.tau2 = (T)(s.tau * s.tau);
   return a;
 }
@@ -991,13 +1073,46 @@ static void build_tc_blob(const Rom &R, std::vector<uint16_t> &blob, std::vector
   }
 }
 
+// Shared memory of the CUDA-core cell kernel: U and D (m K ST values each), the factored last
+// coefficient's intermediate (K ST values, rounded up to even), and the K boundary-row indices.
+static size_t cell_smem_bytes(int max_m, int max_K, int ST, size_t es, int factor_last) {
+  const size_t y = factor_last ? (((size_t)max_K * ST + 1) & ~(size_t)1) : 0;
+  return (2 * (size_t)max_m * max_K * ST + y) * es + 8 * (size_t)max_K;
+}
+
+// Lower Cholesky factor of a positive semidefinite n x n matrix (row-major, FP64): pivots at or
+// below 1e-13 of the largest diagonal entry are raised to that floor; a pivot below -1e-8 of it
+// means the matrix is indefinite (returns false).
+static bool psd_cholesky_host(const double *M, int n, std::vector<double> &L) {
+  double sc = 0;
+  for (int i = 0; i < n; ++i) sc = std::max(sc, M[(size_t)i * n + i]);
+  if (!(sc > 0)) return false;
+  L.assign((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = M[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(d > 1e-13 * sc)) {
+      if (!(d >= -1e-8 * sc)) return false;
+      d = 1e-13 * sc;
+    }
+    const double piv = std::sqrt(d);
+    L[(size_t)j * n + j] = piv;
+    for (int i = j + 1; i < n; ++i) {
+      double v = M[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = v / piv;
+    }
+  }
+  return true;
+}
+
 // Sizes that depend on the CUDA-core source tile ST (every per-column result is independent of
 // the tiling, so changing ST leaves the arithmetic of each source unchanged).
 static void apply_tile(mss_sim &s, int ST) {
   const size_t es = s.prec == MSS_FP64 ? 8 : 4;
   s.ST = ST;
   s.tiles = (s.n_src + ST - 1) / ST;
-  s.cell_smem = 2 * (size_t)s.max_m * s.max_K * ST * es + 8 * (size_t)s.max_K;
+  s.cell_smem = cell_smem_bytes(s.max_m, s.max_K, ST, es, s.factor_last);
   s.corner_smem = std::max<size_t>(16, (size_t)s.max_nm * (ST + s.max_M) * es);
   s.face_smem = std::max<size_t>(16, (2 * (size_t)s.max_M * ST + (size_t)s.max_M * s.max_M +
                                       (s.corners ? (size_t)s.max_nm * s.max_M : 0)) * es);
@@ -1022,7 +1137,12 @@ static void apply_tcs_nt(mss_sim &s, int nt) {
   s.tcp_slots = std::max(1, std::min(per, 2)) * sms;
 }
 
-static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corners) {
+static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags) {
+  MSS_REQUIRE((flags & ~(MSS_SIM_CORNERS | MSS_SIM_FACTOR_LAST)) == 0, MSS_ERR_INVALID_ARG, "unknown sim flags");
+  const int corners = flags & MSS_SIM_CORNERS;
+  MSS_REQUIRE(!(flags & MSS_SIM_FACTOR_LAST) || prec == MSS_FP32, MSS_ERR_INVALID_ARG,
+              "the factored last coefficient is an option of MSS_FP32");
+  s.factor_last = (flags & MSS_SIM_FACTOR_LAST) ? 1 : 0;
   MSS_REQUIRE(prec == MSS_FP64 || prec == MSS_FP32 || prec == MSS_FP32_TC || prec == MSS_BF16_TC, MSS_ERR_INVALID_ARG,
               "precision must be MSS_FP64, MSS_FP32, MSS_FP32_TC or MSS_BF16_TC");
   MSS_REQUIRE(tau > 0 && std::isfinite(tau), MSS_ERR_CFL, "tau must be positive");
@@ -1047,7 +1167,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   s.max_M = *std::max_element(R.face_M.begin(), R.face_M.end());
   int dev_smem = 0;
   MSS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s.device));
-  auto cell_smem = [&](int st) { return 2 * (size_t)s.max_m * s.max_K * st * es + 8 * (size_t)s.max_K; };
+  auto cell_smem = [&](int st) { return cell_smem_bytes(s.max_m, s.max_K, st, es, s.factor_last); };
   while (s.ST > 1 && cell_smem(s.ST) > (size_t)dev_smem) s.ST /= 2;
   s.cell_smem = cell_smem(s.ST);
   MSS_REQUIRE(s.cell_smem <= (size_t)dev_smem, MSS_ERR_INVALID_ARG, "cell too large for shared memory");
@@ -1153,6 +1273,30 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
     }
   }
   s.cell_rows = srows;
+  if (s.factor_last) {
+    // Gamma^m of every cell -> W = L + L^T - diag(L), L its (floored) lower Cholesky factor;
+    // cells are independent, factored on the host threads
+    const int nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<int> bad(nt, -1);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+      pool.emplace_back([&, t] {
+        std::vector<double> L;
+        for (int c = t; c < R.n_cells; c += nt) {
+          const int K = R.cell_K[c], m = R.cell_m[c];
+          double *Wc = coef.data() + cell_coef[c] + (size_t)(m - 1) * K * K;
+          if (!psd_cholesky_host(Wc, K, L)) {
+            if (bad[t] < 0) bad[t] = c;
+            continue;
+          }
+          for (int i = 0; i < K; ++i)
+            for (int j = 0; j < K; ++j) Wc[(size_t)i * K + j] = i >= j ? L[(size_t)i * K + j] : L[(size_t)j * K + i];
+        }
+      });
+    for (auto &th : pool) th.join();
+    for (int b : bad)
+      MSS_REQUIRE(b < 0, MSS_ERR_COEF_NOT_SPD, "last coefficient of cell " + std::to_string(b) + " is indefinite");
+  }
   {
     // split cell phase: one item per (cell, matrix) and an F scratch block of m K rows per cell
     std::vector<int2> fi, ai;
@@ -1174,7 +1318,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int corne
   }
   // streamed cell kernel: FP32 CUDA-core path with 16-source tiles and K_i <= 128; the same
   // matrices as coef, each row padded to Kq = K rounded up to 4 floats (16-byte rows)
-  if (prec == MSS_FP32 && !s.tc && s.ST == kStreamST && s.max_K <= 128) {
+  if (prec == MSS_FP32 && !s.tc && !s.factor_last && s.ST == kStreamST && s.max_K <= 128) {
     const size_t need = (size_t)kStreamSlots * kStreamChunk + 64 + 2 * (size_t)s.max_m * s.max_K * kStreamST * 4 +
                         8 * (size_t)s.max_K;
     if (need <= (size_t)dev_smem) {
@@ -1517,12 +1661,12 @@ mss_status mss_step_noalloc(mss_step_buffers *b, int64_t n_steps, const double *
   });
 }
 
-mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32_t corner_correction, mss_sim **out) {
+mss_status mss_sim_create(const mss_rom *r, int32_t precision, double tau, int32_t flags, mss_sim **out) {
   return guard([&] {
     const Range nvtx_range("mss_sim_create");
     MSS_REQUIRE(r && out, MSS_ERR_INVALID_ARG, "null argument");
     auto s = std::make_unique<mss_sim>();
-    sim_create(*s, r->r, precision, tau, corner_correction);
+    sim_create(*s, r->r, precision, tau, flags);
     sim_reset(*s, 0);
     MSS_CUDA(cudaStreamSynchronize(0));
     *out = s.release();
@@ -1579,6 +1723,7 @@ mss_status mss_step_profile(mss_sim *s, int64_t n_steps, const double *waveform,
 }
 
 static bool sched_allowed(const mss_sim &s, int sched) {
+  if (s.factor_last) return sched == MSS_SCHED_GRAPH || sched == MSS_SCHED_PERSIST;
   switch (sched) {
     case MSS_SCHED_GRAPH: return true;
     case MSS_SCHED_GRAPH_STREAM: return s.stream_ok;
