@@ -218,6 +218,14 @@ mss_status mss_rom_set_io(mss_rom *r, int32_t n_src, int32_t n_src_entries, cons
  * mss_build_roms; this call replaces it (n_groups = 0 clears it). */
 mss_status mss_rom_set_corners(mss_rom *r, int32_t n_groups, const int32_t *group_ptr, const int32_t *face,
                                const double *rows, const double *weight);
+/* Host copies of a ROM's projected I/O (Eq. BEINCr g~_f = S_f^T g|_f, Eq. solatrec q~_f = S_f^T q|_f)
+ * and Appendix D data, in the layouts of mss_rom_set_io and mss_rom_set_corners.
+ * counts (host, [9]): sources, source entries, source values, receivers, receiver entries,
+ * receiver values, corner groups, corner members, corner row values.  Any array may be NULL
+ * (counts only); otherwise it must hold its count (group_ptr: groups + 1).  Errors: INVALID_ARG. */
+mss_status mss_rom_export_io(const mss_rom *r, int64_t counts[9], int32_t *src_face, int32_t *src_index,
+                             double *src_vals, int32_t *rcv_face, int32_t *rcv_index, double *rcv_vals,
+                             int32_t *group_ptr, int32_t *member_face, double *member_rows, double *member_weight);
 void mss_rom_destroy(mss_rom *r);
 
 /* ------------------------------------------------------------------------- */

@@ -94,6 +94,7 @@ _SIGS = [
     ("mss_rom_set_io_nodes", C.c_int32, [_P, _P, C.c_int32, _P, _P, C.c_int32, _P, _P]),
     ("mss_rom_set_io", C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_int32, C.c_int32, _P, _P, _P]),
     ("mss_rom_set_corners", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P]),
+    ("mss_rom_export_io", C.c_int32, [_P] * 12),
     ("mss_rom_destroy", None, [_P]),
     ("mss_sim_create", C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, _P]),
     ("mss_sim_info", C.c_int32, [_P, _P]),
@@ -438,6 +439,35 @@ class Rom(_Handle):
         rf, ri, rv = pack(rcv_entries)
         _check(lib().mss_rom_set_io(self._h, int(n_src), len(src_entries), _ptr(sf), _ptr(si), _ptr(sv), int(n_rcv),
                                     len(rcv_entries), _ptr(rf), _ptr(ri), _ptr(rv)))
+
+    def export_io(self):
+        """mss_rom_export_io: (sources, receivers, corner groups) as lists of (face, index, values[M_f])
+        entries and of groups of (face, row values[M_f], weight)."""
+        n = np.zeros(9, np.int64)
+        _check(lib().mss_rom_export_io(self._h, _ptr(n), *([None] * 10)))
+        sf, si, sv = np.zeros(n[1], np.int32), np.zeros(n[1], np.int32), np.zeros(n[2])
+        rf, ri, rv = np.zeros(n[4], np.int32), np.zeros(n[4], np.int32), np.zeros(n[5])
+        gp, mf, mr, mw = np.zeros(n[6] + 1, np.int32), np.zeros(n[7], np.int32), np.zeros(n[8]), np.zeros(n[7])
+        _check(lib().mss_rom_export_io(self._h, _ptr(n), _ptr(sf), _ptr(si), _ptr(sv), _ptr(rf), _ptr(ri), _ptr(rv),
+                                       _ptr(gp), _ptr(mf), _ptr(mr), _ptr(mw)))
+        fM = self.export()[3]
+
+        def entries(face, idx, vals):
+            out, o = [], 0
+            for f, j in zip(face, idx):
+                out.append((int(f), int(j), vals[o:o + fM[f]].copy()))
+                o += int(fM[f])
+            return out
+
+        groups, o = [], 0
+        for g in range(int(n[6])):
+            grp = []
+            for e in range(int(gp[g]), int(gp[g + 1])):
+                f = int(mf[e])
+                grp.append((f, mr[o:o + fM[f]].copy(), float(mw[e])))
+                o += int(fM[f])
+            groups.append(grp)
+        return entries(sf, si, sv), entries(rf, ri, rv), groups
 
     def set_corners(self, groups):
         """groups: list of lists of (face, row values[M_f], weight)."""

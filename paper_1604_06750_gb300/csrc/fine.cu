@@ -60,6 +60,84 @@ __global__ void __launch_bounds__(kFineThreads) k_fine(const FineArgs<T> a, cons
   }
 }
 
+// 16-byte vector of T over sources (4 floats or 2 doubles).
+template <typename T> struct FineVec;
+template <> struct FineVec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct FineVec<double> { using type = double2; static constexpr int n = 2; };
+
+// Same step with one thread per (node, vector of VN sources) when S is a multiple of VN: 16-byte
+// loads and stores of the state, the node's coefficients read once per vector instead of once per
+// source, and 32-bit index arithmetic whenever the thread count allows.  Every element takes the
+// same operations in the same order as k_fine.
+template <typename T>
+__global__ void __launch_bounds__(kFineThreads) k_fine_v(const FineArgs<T> a, const int cur, const double *w,
+                                                         T *traces) {
+  using V = typename FineVec<T>::type;
+  constexpr int VN = FineVec<T>::n;
+  const int nv = a.S / VN;
+  const int64_t total = a.nodes * nv;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const T *u = cur ? a.u1 : a.u0;
+  T *uo = cur ? a.u0 : a.u1;
+  if (i < total) {
+    int64_t p;
+    int v;
+    if (total <= 0xffffffffLL) {
+      const unsigned ii = (unsigned)i, pp = ii / (unsigned)nv;
+      p = pp;
+      v = (int)(ii - pp * (unsigned)nv);
+    } else {
+      p = i / nv;
+      v = (int)(i - p * nv);
+    }
+    const T bi = a.binv[p];
+    if (bi == T(0)) return;   // removed node: stays zero
+    const int S = a.S;
+    const int64_t off = p * S + (int64_t)v * VN;
+    const V uc = *reinterpret_cast<const V *>(u + off);
+    const T *ue = reinterpret_cast<const T *>(&uc);
+    const T dg = a.diag[p];
+    T lap[VN];
+#pragma unroll
+    for (int e = 0; e < VN; ++e) lap[e] = dg * ue[e];
+    const T *cp[3] = {a.cp0, a.cp1, a.cp2};
+    const int64_t st[3] = {a.s0, a.s1, a.s2};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if (ax >= a.d) break;
+      const int64_t q = p + st[ax], r = p - st[ax];
+      if (q < a.nodes) {
+        const T c = cp[ax][p];
+        const V x = *reinterpret_cast<const V *>(u + off + st[ax] * S);
+        const T *xe = reinterpret_cast<const T *>(&x);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) lap[e] += c * xe[e];
+      }
+      if (r >= 0) {
+        const T c = cp[ax][r];
+        const V x = *reinterpret_cast<const V *>(u + off - st[ax] * S);
+        const T *xe = reinterpret_cast<const T *>(&x);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) lap[e] += c * xe[e];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < VN; ++e)
+      if (a.src_node[v * VN + e] == p) lap[e] -= (T)(*w);
+    V o = *reinterpret_cast<const V *>(uo + off);
+    T *oe = reinterpret_cast<T *>(&o);
+#pragma unroll
+    for (int e = 0; e < VN; ++e) oe[e] = T(2) * ue[e] - oe[e] + a.tau2 * bi * lap[e];
+    *reinterpret_cast<V *>(uo + off) = o;
+  } else {
+    const int64_t j = i - ((total + kFineThreads - 1) / kFineThreads) * kFineThreads;
+    if (j < 0 || j >= (int64_t)a.R * a.S) return;
+    const int64_t r = j / a.S;
+    const int s = (int)(j - r * a.S);
+    traces[j] = u[a.rcv_node[r] * a.S + s];
+  }
+}
+
 struct FineGraphKey {
   int64_t n;
   const void *w, *t;
@@ -118,11 +196,14 @@ static FineArgs<T> fine_args(const mss_fine &f) {
 template <typename T>
 static void fine_launch(mss_fine &f, int64_t n, const double *w, T *traces, cudaStream_t st) {
   const FineArgs<T> a = fine_args<T>(f);
-  const int64_t total = f.nodes * f.S;
+  constexpr int VN = FineVec<T>::n;
+  const bool vec = f.S % VN == 0;
+  const int64_t total = f.nodes * (vec ? f.S / VN : f.S);
   const int64_t nb = (total + kFineThreads - 1) / kFineThreads + ((int64_t)f.R * f.S + kFineThreads - 1) / kFineThreads;
   int cur = f.cur;
   for (int64_t j = 0; j < n; ++j) {
-    k_fine<T><<<(unsigned)nb, kFineThreads, 0, st>>>(a, cur, w + j, traces + j * (int64_t)f.R * f.S);
+    if (vec) k_fine_v<T><<<(unsigned)nb, kFineThreads, 0, st>>>(a, cur, w + j, traces + j * (int64_t)f.R * f.S);
+    else k_fine<T><<<(unsigned)nb, kFineThreads, 0, st>>>(a, cur, w + j, traces + j * (int64_t)f.R * f.S);
     cur ^= 1;
   }
   MSS_CUDA(cudaGetLastError());

@@ -373,6 +373,33 @@ mss_status mss_rom_set_corners(mss_rom *r, int32_t n_groups, const int32_t *grou
   });
 }
 
+mss_status mss_rom_export_io(const mss_rom *r, int64_t counts[9], int32_t *src_face, int32_t *src_index,
+                             double *src_vals, int32_t *rcv_face, int32_t *rcv_index, double *rcv_vals,
+                             int32_t *group_ptr, int32_t *member_face, double *member_rows, double *member_weight) {
+  return guard([&] {
+    MSS_REQUIRE(r && counts, MSS_ERR_INVALID_ARG, "null argument");
+    const Rom &R = r->r;
+    const int64_t ng = R.cg_ptr.empty() ? 0 : (int64_t)R.cg_ptr.size() - 1;
+    const int64_t c[9] = {R.n_src, (int64_t)R.src_face.size(), (int64_t)R.src_vals.size(), R.n_rcv,
+                          (int64_t)R.rcv_face.size(), (int64_t)R.rcv_vals.size(), ng, (int64_t)R.cg_face.size(),
+                          (int64_t)R.cg_rows.size()};
+    std::copy(c, c + 9, counts);
+    auto put = [](auto *dst, const auto &v) {
+      if (dst) std::copy(v.begin(), v.end(), dst);
+    };
+    put(src_face, R.src_face);
+    put(src_index, R.src_index);
+    put(src_vals, R.src_vals);
+    put(rcv_face, R.rcv_face);
+    put(rcv_index, R.rcv_index);
+    put(rcv_vals, R.rcv_vals);
+    put(group_ptr, R.cg_ptr);
+    put(member_face, R.cg_face);
+    put(member_rows, R.cg_rows);
+    put(member_weight, R.cg_weight);
+  });
+}
+
 void mss_rom_destroy(mss_rom *r) { delete r; }
 
 }  // extern "C"

@@ -77,23 +77,53 @@ def test_build_roms_matches_oracle(P, name, wl):
         o += B.size
 
 
-def test_io_projection_and_corners_match_oracle(P):
-    wl = synth.workload_2d_layers(32, 8, m=3, n_modes=4, n_steps=100)
+@pytest.mark.parametrize("name,wl", [("2d_16cells", synth.workload_2d_layers(32, 8, m=3, n_modes=4, n_steps=10)),
+                                     ("3d_8cells", synth.workload_3d_layers(16, 8, m=3, n_modes=6, n_src=2,
+                                                                           n_steps=10))])
+def test_io_projection_and_corners_match_oracle(P, name, wl):
+    """g~_f = S_f^T g|_f, q~_f = S_f^T q|_f (Eqs. BEINCr, solatrec; corner-set nodes spread over their
+    hanging copies by b_{k_f}/b_k) and the Appendix D rows of the GPU-built ROM, entry by entry
+    against the oracle's projections of the same nodes."""
     op, part, io, _ = _setup(wl)
     s = -rom.omega_max(wl.f_max) ** 2
     L = P.Operator(wl.grid, wl.sigma, wl.rho)
     LP = P.Partition(L, wl.cell, io)
     LR = P.Rom.build(LP, wl.m, wl.n_modes, s)
-    info = LR.info()
-    cg = part.corner_groups()
-    assert info[7] == len(cg)
-    bases = [rom.face_basis(f, wl.n_modes) for f in part.faces]
-    gp = part.prime_vectors(wl.src_nodes)
-    gt = rom.project_io(part, bases, gp)
     LR.set_io_nodes(LP, wl.src_nodes, wl.rcv_nodes)
-    # run one step with a unit waveform and compare the face response through the traces is
-    # indirect; instead compare against the oracle's projections via a full FP64 run below.
-    assert sum(np.count_nonzero(np.abs(x) > 0) for x in gt) > 0
+    src, rcv, groups = LR.export_io()
+    bases = [rom.face_basis(f, wl.n_modes) for f in part.faces]
+    nS, nR = len(wl.src_nodes), len(wl.rcv_nodes)
+    gt = rom.project_io(part, bases, part.prime_vectors(wl.src_nodes))
+    qt = rom.project_io(part, bases, part.prime_vectors(wl.rcv_nodes))
+    got_g = online.dense_io(_topo(LR), src, nS, "src")
+    got_q = online.dense_io(_topo(LR), rcv, nR, "rcv")
+    scale_g = max(np.max(np.abs(x)) for x in gt)
+    scale_q = max(np.max(np.abs(x)) for x in qt)
+    assert scale_g > 0 and scale_q > 0
+    for f in range(len(part.faces)):
+        assert np.max(np.abs(got_g[f] - gt[f]), initial=0.0) <= 1e-13 * scale_g, f
+        assert np.max(np.abs(got_q[f].T - qt[f]), initial=0.0) <= 1e-13 * scale_q, f
+    ref = online.corner_rows(part.corner_groups(), bases)
+    assert len(groups) == len(ref) and LR.info()[7] == len(ref)
+
+    def canon(gs):
+        out = []
+        for g in gs:
+            out.append(sorted((int(f), tuple(np.round(np.asarray(r), 12)), round(float(w), 12)) for (f, r, w) in g))
+        return sorted(out)
+
+    a, b = canon(groups), canon(ref)
+    for ga, gb in zip(a, b):
+        assert [m[0] for m in ga] == [m[0] for m in gb]
+        for ma, mb in zip(ga, gb):
+            assert np.max(np.abs(np.asarray(ma[1]) - np.asarray(mb[1]))) <= 1e-12
+            assert abs(ma[2] - mb[2]) <= 1e-12
+
+
+def _topo(LR):
+    cm, cfp, cf, fM, fc, _, _, _ = LR.export()
+    return synth.RomTopology(np.asarray(cm, np.int64), [list(cf[cfp[c]:cfp[c + 1]]) for c in range(len(cm))],
+                             np.asarray(fM, np.int64), [[int(x) for x in r if x >= 0] for r in fc])
 
 
 @pytest.mark.parametrize("corners", [False, True])

@@ -200,7 +200,10 @@ def test_full_size_launch_sampled_sources(P):
 
 
 @pytest.mark.parametrize("prec_tol", [(0, 1e-12), (1, 2e-5)])
-def test_fine_grid_gpu_parity(P, prec_tol):
+@pytest.mark.parametrize("n_src", [3, 4, 8])
+def test_fine_grid_gpu_parity(P, prec_tol, n_src):
+    """Scalar kernel (3 sources) and the vector kernel over sources (4 and 8: multiples of the
+    16-byte vector width in both precisions)."""
     prec, tol = prec_tol
     n = (10, 12, 14)
     g = synth.Grid(n=n, h=1.0 / 14, bc=(("D", "N"), ("D", "D"), ("N", "D")))
@@ -209,11 +212,11 @@ def test_fine_grid_gpu_parity(P, prec_tol):
     op = fine.FineOperator(g, s, r)
     lam = fine.lambda_max(op.A, op.B)
     tau = 0.5 * fine.tau_critical(lam)
-    srcn = [(10, 3, 4), (5, 6, 7), (2, 2, 9)]
+    srcn = [(10, 3, 4), (5, 6, 7), (2, 2, 9), (7, 10, 2), (3, 9, 12), (9, 1, 1), (6, 6, 6), (1, 11, 5)][:n_src]
     rcvn = [(10, 8, 8), (4, 4, 4), (7, 1, 13), (10, 3, 4)]
     nst = 200
     w = synth.ricker(np.arange(nst) * tau, 0.05 / tau)
-    G = np.zeros((op.N, 3))
+    G = np.zeros((op.N, n_src))
     Q = np.zeros((4, op.N))
     for j, p in enumerate(srcn):
         G[op.node_unknown(p), j] = 1
@@ -223,7 +226,7 @@ def test_fine_grid_gpu_parity(P, prec_tol):
     L = P.Operator(g, s, r)
     fs = P.FineSim(L, prec, tau, srcn, rcvn)
     wd = torch.tensor(w, device="cuda")
-    tr = torch.zeros((nst, 4, 3), device="cuda", dtype=torch.float64 if prec == 0 else torch.float32)
+    tr = torch.zeros((nst, 4, n_src), device="cuda", dtype=torch.float64 if prec == 0 else torch.float32)
     fs.step(nst, wd, tr)
     torch.cuda.synchronize()
     assert _rel(tr.cpu().numpy().astype(np.float64), ref) <= tol
