@@ -200,10 +200,22 @@ mss_status mss_rom_face_bases(const mss_rom *r, int64_t *count, double *bases);
 mss_status mss_partition_set_face_bases(mss_partition *p, int32_t n_faces, const int32_t *face_M,
                                         const double *bases);
 
+/* Receivers inside cells through the Galerkin lift (Remark MFEM: the ROM is a Galerkin method, the
+ * cell's fine state is approximately V x, x its projected state).  nodes (host, n x dim) must lie
+ * strictly inside a cell: on no face and not an I/O node of mss_partition_create.  The next
+ * mss_build_roms / mss_rom_rebuild_cells of p computes, per node and cell layer k, the weights
+ * w_k = G_k^{-T} Q_k^T V^T e_node (Q_k the block Lanczos vectors of Eq. NtDtri, G_k the change of
+ * variables of Eq. GammaTrans), and mss_rom_set_io_nodes then reads a receiver at such a node as
+ * sum_k w_k . U^k (layer 1 = the cell's face state, layers 2..m its hidden state), so the node
+ * needs no I/O face.  n = 0 clears the list.  Errors: INVALID_ARG (a node outside the grid, on a
+ * Dirichlet wall, on a face or an I/O node). */
+mss_status mss_partition_set_lift_nodes(mss_partition *p, int32_t n, const int32_t *nodes);
+
 /* Projected inputs/outputs (Eq. BEINCr g~_f = S_f^T g|_f, Eq. solatrec q~_f = S_f^T q|_f) from
  * point sources/receivers at fine-grid nodes with weights (NULL = 1); a node of the corner set
- * is spread over its hanging copies with weights b_{k_f}/b_k.  Needs a ROM built by
- * mss_build_roms from the same partition.  Replaces any previous I/O of the ROM. */
+ * is spread over its hanging copies with weights b_{k_f}/b_k; a receiver at a lift node of the build
+ * (mss_partition_set_lift_nodes) is read through its lift.  Needs a ROM built by mss_build_roms from
+ * the same partition.  Replaces any previous I/O of the ROM. */
 mss_status mss_rom_set_io_nodes(mss_rom *r, const mss_partition *p, int32_t n_src, const int32_t *src_nodes,
                                 const double *src_w, int32_t n_rcv, const int32_t *rcv_nodes,
                                 const double *rcv_w);
@@ -221,7 +233,8 @@ mss_status mss_rom_set_corners(mss_rom *r, int32_t n_groups, const int32_t *grou
 /* Host copies of a ROM's projected I/O (Eq. BEINCr g~_f = S_f^T g|_f, Eq. solatrec q~_f = S_f^T q|_f)
  * and Appendix D data, in the layouts of mss_rom_set_io and mss_rom_set_corners.
  * counts (host, [9]): sources, source entries, source values, receivers, receiver entries,
- * receiver values, corner groups, corner members, corner row values.  Any array may be NULL
+ * receiver values, corner groups, corner members, corner row values (receiver entries on hidden
+ * layers, from lifted receivers, are not part of this export).  Any array may be NULL
  * (counts only); otherwise it must hold its count (group_ptr: groups + 1).  Errors: INVALID_ARG. */
 mss_status mss_rom_export_io(const mss_rom *r, int64_t counts[9], int32_t *src_face, int32_t *src_index,
                              double *src_vals, int32_t *rcv_face, int32_t *rcv_index, double *rcv_vals,

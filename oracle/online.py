@@ -74,13 +74,16 @@ def corner_rows(corner_groups, bases):
 
 
 def rom_leapfrog(topo, coeffs, gt: List[np.ndarray], qt: List[np.ndarray], w: np.ndarray, tau: float,
-                 n_steps: int, state: Optional[tuple] = None, return_state: bool = False, corners=None):
+                 n_steps: int, state: Optional[tuple] = None, return_state: bool = False, corners=None,
+                 lifted=None):
     """Leapfrog of the coupled ROM.  gt[f]: (M_f, S); qt[f]: (R, M_f); w: waveform samples.
 
     ``state`` = ((faces_now, cells_now), (faces_old, cells_old)) or None for zero.
     ``corners``: optional Appendix D correction data (see corner_correct), applied to
     every new face level.
-    Returns traces (n_steps, R, S) (and the final two levels if asked).
+    ``lifted``: optional receivers inside cells, a list of (cell i, weights (m_i, K_i)) read as
+    sum_k w_k^T U^k_i (``rom.receiver_lift``); their traces follow the R face receivers.
+    Returns traces (n_steps, R + len(lifted), S) (and the final two levels if asked).
     """
     S = gt[0].shape[1] if len(gt) else 1
     R = qt[0].shape[0] if len(qt) else 0
@@ -97,11 +100,15 @@ def rom_leapfrog(topo, coeffs, gt: List[np.ndarray], qt: List[np.ndarray], w: np
         fo = [np.array(x, dtype=np.float64) for x in fo]
         cu = [[np.array(x, dtype=np.float64) for x in c] for c in cu]
         co = [[np.array(x, dtype=np.float64) for x in c] for c in co]
-    out = np.zeros((n_steps, R, S))
+    lifted = lifted or []
+    out = np.zeros((n_steps, R + len(lifted), S))
     t2 = tau * tau
     for n in range(n_steps):
         for f in range(topo.n_faces):
-            out[n] += qt[f] @ fu[f]
+            out[n, :R] += qt[f] @ fu[f]
+        for j, (i, wts) in enumerate(lifted):
+            U = [np.concatenate([fu[f] for f in topo.cell_faces[i]], axis=0)] + list(cu[i])
+            out[n, R + j] = sum(wts[k] @ U[k] for k in range(len(U)))
         flux_sum = [np.zeros((int(M), S)) for M in topo.face_M]
         new_cells = []
         for i in range(topo.n_cells):

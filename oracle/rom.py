@@ -203,11 +203,12 @@ def _qr_pos(W: np.ndarray):
     return Q * sgn, sgn[:, None] * R
 
 
-def block_lanczos(Am: np.ndarray, Sm: np.ndarray, m: int):
+def block_lanczos(Am: np.ndarray, Sm: np.ndarray, m: int, return_q: bool = False):
     """Block tridiagonal form T = Q^T A^m Q, R = Q^T S^m = [beta_1, 0, ..]^T (Eq. NtDtri).
 
     Returns (alpha[0..m-1], beta[0..m-1]) with alpha[k] = alpha_{k+1}, beta[k] = beta_{k+1};
     A^m Q_k = Q_{k-1} beta_k^T + Q_k alpha_k + Q_{k+1} beta_{k+1}; full reorthogonalisation.
+    With ``return_q`` also the Lanczos blocks Q_1..Q_m.
     """
     K = Sm.shape[1]
     Q1, b1 = _qr_pos(Sm)
@@ -233,6 +234,8 @@ def block_lanczos(Am: np.ndarray, Sm: np.ndarray, m: int):
             raise RomError("block Lanczos breakdown")
         Qs.append(Qn)
         betas.append(bn)
+    if return_q:
+        return alphas, betas, Qs
     return alphas, betas
 
 
@@ -270,7 +273,7 @@ def psd_cholesky(M: np.ndarray, floor: float = PSD_FLOOR, neg_tol: float = PSD_N
     return L, floored
 
 
-def gamma_trans(alphas: List[np.ndarray], betas: List[np.ndarray]):
+def gamma_trans(alphas: List[np.ndarray], betas: List[np.ndarray], return_g: bool = False):
     """Gamma^k, Gamma-hat^k (k = 1..m) from the block Lanczos coefficients (module readings).
 
     Gamma^1..Gamma^{m-1} and every Gamma-hat^k must be SPD.  The last coefficient Gamma^m may be
@@ -281,8 +284,9 @@ def gamma_trans(alphas: List[np.ndarray], betas: List[np.ndarray]):
     m = len(alphas)
     G = betas[0].T.copy()
     Gprev = np.zeros_like(G)
-    gam, gh = [], []
+    gam, gh, Gs = [], [], []
     for k in range(m):
+        Gs.append(G.copy())
         Gh = G @ G.T
         Gi = np.linalg.inv(G)
         Gk = -Gi.T @ alphas[k] @ Gi - Gprev
@@ -303,6 +307,8 @@ def gamma_trans(alphas: List[np.ndarray], betas: List[np.ndarray]):
         if k + 1 < m:
             G = np.linalg.solve(G.T @ Gk, betas[k + 1].T)
         Gprev = Gk
+    if return_g:
+        return gam, gh, Gs
     return gam, gh
 
 
@@ -378,6 +384,27 @@ def build_cell_rom(part, cid: int, bases: List[np.ndarray], m: int, s: float, ke
     if keep:
         return CellRom(gam, gh, V, Am, Sm, C)
     return CellRom(gam, gh)
+
+
+def receiver_lift(cr: CellRom, rows: Sequence[int]) -> np.ndarray:
+    """Weights that read fine-grid values inside a cell off its S-fraction state (Remark MFEM:
+    the ROM is a Galerkin method, u_i ~ V x with x the projected state).
+
+    In the Lanczos basis x = sum_k Q_k z_k (Eq. NtDtri, mass I), and the S-fraction variables of
+    Eq. GammaTrans are U^k = G_k z_k (their mass is (Gamma-hat^k)^{-1} = G_k^{-T} G_k^{-1}), so the
+    value at cell-local node n is sum_k w_k^T U^k with w_k = G_k^{-T} Q_k^T V^T e_n; U^1 is the cell's
+    face state.  ``cr`` must come from ``build_cell_rom(..., keep=True)``.  Returns (len(rows), m, K).
+    """
+    m = len(cr.gamma)
+    K = cr.Sm.shape[1]
+    al, be, Q = block_lanczos(cr.Am, cr.Sm, m, return_q=True)
+    _, _, Gs = gamma_trans(al, be, return_g=True)
+    out = np.zeros((len(rows), m, K))
+    for j, n in enumerate(rows):
+        v = cr.V[int(n), :]
+        for k in range(m):
+            out[j, k] = np.linalg.solve(Gs[k].T, Q[k].T @ v)
+    return out
 
 
 def face_masses(part, bases, cell_roms: Dict[int, CellRom]) -> List[np.ndarray]:

@@ -95,6 +95,7 @@ _SIGS = [
     ("mss_rom_set_io", C.c_int32, [_P, C.c_int32, C.c_int32, _P, _P, _P, C.c_int32, C.c_int32, _P, _P, _P]),
     ("mss_rom_set_corners", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P]),
     ("mss_rom_export_io", C.c_int32, [_P] * 12),
+    ("mss_partition_set_lift_nodes", C.c_int32, [_P, C.c_int32, _P]),
     ("mss_rom_destroy", None, [_P]),
     ("mss_sim_create", C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, _P]),
     ("mss_sim_info", C.c_int32, [_P, _P]),
@@ -270,6 +271,11 @@ class Partition(_Handle):
         _check(lib().mss_partition_faces(self._h, _ptr(kind), _ptr(cells), _ptr(shape), _ptr(ptr), _ptr(nodes),
                                          _ptr(par)))
         return kind, cells.reshape(F, 2), shape.reshape(F, 2), ptr, nodes, par
+
+    def set_lift_nodes(self, nodes) -> None:
+        """mss_partition_set_lift_nodes: receivers inside cells read through the Galerkin lift."""
+        a = _arr(np.zeros((0, 1)) if nodes is None or len(nodes) == 0 else nodes, np.int32)
+        _check(lib().mss_partition_set_lift_nodes(self._h, int(a.shape[0]) if a.size else 0, _ptr(a)))
 
     def set_face_bases(self, bases) -> None:
         """Caller-supplied face bases (mss_partition_set_face_bases): one K_f x M_f array per face,

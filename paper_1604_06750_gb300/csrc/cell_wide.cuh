@@ -1,0 +1,273 @@
+// Wide streamed cell kernel: the cell phase for large boundary dimensions (K_i up to 512), FP32 on
+// the CUDA cores, 16-source tiles, the coefficient stream staged by TMA.
+//
+// At the paper's operating point (cells about one wavelength across, K~ = 180-294, Section 7) a
+// cell's 2m-1 coefficient matrices hold about 2 MB per step, more than the L2 share of the CTAs
+// resident at once, so the stream is moved by the copy engine, not by thread loads: one thread
+// issues 1-D bulk copies (cp.async.bulk) of whole stored rows into a ring of four 16 KB
+// shared-memory slots, each guarded by an mbarrier with a transaction count, and 512 threads
+// consume them.  Thread (g, r0): g = tid / 256 picks 8 of the 16 sources, r0 = tid % 256 picks the
+// output rows r0 and r0 + 256.  Row j of a stored symmetric matrix is also its column j, so
+//   acc[i][e] += G[j][r0 + 256 i] * D[j][8 g + e]
+// reads the slot without bank conflicts and D as a broadcast.
+//
+// Factored last coefficient (Gamma^m = L L^T, the stored matrix W = L + L^T - diag(L) with its rows
+// in descending order): F^m = L (L^T D^m) in one pass over the stream.  Rows j arrive from K-1 down
+// to 0.  In each ring segment, y_r += W[j][r] D^m_j for r <= j (the L^T product; y_j is complete
+// once row j has passed), the segment's complete y_j go to shared memory, and after a barrier
+// F_r += W[j][r] y_j for r >= j (the L product) reuses the same rows from the slot.  Per element
+// this is the same sequence of fused multiply-adds as the plain cell kernel's descending
+// triangular passes, so both give identical bits.
+//
+// Every wait is bounded (globaltimer); on timeout the CTA records an error, waits (bounded) for
+// its own copies in flight and returns.
+#pragma once
+
+namespace mss {
+
+constexpr int kWideThreads = 512;
+constexpr int kWideSlots = 256;     // row slots: a thread owns rows r0 and r0 + kWideSlots
+constexpr int kWideRows = 2;        // rows per thread, so K_i <= kWideSlots * kWideRows
+constexpr int kWideCP = 8;          // sources per thread (two 8-source groups per 16-source tile)
+
+// Shared memory of the wide kernel: ring and its barriers, U/F (X) and D/E (D) as m K 16 floats
+// each, the factored product's y (K 16 floats), the K boundary-row indices.
+inline size_t wide_smem_bytes(int max_m, int max_K, int factor_last) {
+  return (size_t)kStreamSlots * kStreamChunk + 64 +
+         (2 * (size_t)max_m * max_K * kStreamST + (factor_last ? (size_t)max_K * kStreamST : 0)) * 4 +
+         8 * (size_t)max_K;
+}
+
+__device__ __forceinline__ void fma8(float (&acc)[kWideCP], float gv, const float4 d0, const float4 d1) {
+  fma2(acc[0], acc[1], gv, d0.x, d0.y);
+  fma2(acc[2], acc[3], gv, d0.z, d0.w);
+  fma2(acc[4], acc[5], gv, d1.x, d1.y);
+  fma2(acc[6], acc[7], gv, d1.z, d1.w);
+}
+
+// One (cell, 16-source tile) of the cell phase.  gc: chunks this CTA has consumed so far; returns
+// false if a wait timed out (error recorded, copies drained).
+__device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, const int cur, const int cell,
+                               const int tile, unsigned char *smem, unsigned &gc) {
+  constexpr int ST = kStreamST, CP = kWideCP;
+  const int s0 = tile * ST;
+  const int K = a.cell_K[cell], m = a.cell_m[cell], Kq = t.Kq[cell];
+  const int ns = min(ST, a.S - s0);
+  const int S = a.S;
+  const int tid = threadIdx.x;
+  const bool fac = a.factor_last != 0;
+  unsigned char *ring = smem;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStreamSlots * kStreamChunk);
+  float *X = reinterpret_cast<float *>(smem + kStreamSlots * kStreamChunk + 64);
+  float *D = X + (size_t)m * K * ST;
+  float *Ys = D + (size_t)m * K * ST;
+  int64_t *rows = reinterpret_cast<int64_t *>(Ys + (fac ? (size_t)K * ST : 0));
+  const float *fs = cur ? a.fstate1 : a.fstate0;
+  const float *cs = cur ? a.cstate1 : a.cstate0;
+  float *cso = cur ? a.cstate0 : a.cstate1;
+  const int64_t rp = a.cell_row[cell], so = a.cell_state[cell];
+  const int row_bytes = Kq * 4;
+  const int CR = kStreamChunk / row_bytes;
+  const int total_rows = (2 * m - 1) * K;
+  const int nch = (total_rows + CR - 1) / CR;
+  const unsigned gc0 = gc;
+  const float *src = t.coef + t.coef_off[cell];
+  auto issue = [&](int c) {   // thread 0 only
+    const unsigned g = gc0 + (unsigned)c, slot = g % kStreamSlots;
+    const int r0 = c * CR, nr = min(CR, total_rows - r0);
+    const unsigned bytes = (unsigned)(nr * row_bytes);
+    fence_async_smem();
+    mbar_expect_tx(smem_u32(full + slot), bytes);
+    bulk_g2s(smem_u32(ring + (size_t)slot * kStreamChunk), src + (size_t)r0 * Kq, bytes, smem_u32(full + slot));
+  };
+  if (tid == 0)
+    for (int c = 0; c < min(nch, kStreamSlots); ++c) issue(c);
+  // operands: U (face rows gathered, then interior layers), then D^k = U^{k+1} - U^k
+  for (int r = tid; r < K; r += blockDim.x) rows[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
+  __syncthreads();
+  const bool vec = (ns == ST) && (S % 4 == 0);
+  if (vec) {
+    for (int i = tid; i < K * (ST / 4); i += blockDim.x) {
+      const int r = i / (ST / 4), v = i - r * (ST / 4);
+      reinterpret_cast<float4 *>(X)[i] = *reinterpret_cast<const float4 *>(fs + (rows[r] >> 1) * S + s0 + v * 4);
+    }
+    for (int i = tid; i < (m - 1) * K * (ST / 4); i += blockDim.x) {
+      const int r = i / (ST / 4), v = i - r * (ST / 4);
+      reinterpret_cast<float4 *>(X + (size_t)K * ST)[i] = *reinterpret_cast<const float4 *>(cs + (so + r) * S + s0 + v * 4);
+    }
+  } else {
+    for (int i = tid; i < K * ST; i += blockDim.x) {
+      const int r = i / ST, s = i - r * ST;
+      X[i] = s < ns ? fs[(rows[r] >> 1) * S + s0 + s] : 0.f;
+    }
+    for (int i = tid; i < (m - 1) * K * ST; i += blockDim.x) {
+      const int r = i / ST, s = i - r * ST;
+      X[(size_t)K * ST + i] = s < ns ? cs[(so + r) * S + s0 + s] : 0.f;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < m * K * ST; i += blockDim.x) {
+    const int k = i / (K * ST);
+    D[i] = (k + 1 < m ? X[i + (size_t)K * ST] : 0.f) - X[i];
+  }
+  __syncthreads();
+  const int r0 = tid & (kWideSlots - 1), g = tid / kWideSlots;
+  int rr[kWideRows];
+  bool act[kWideRows];
+#pragma unroll
+  for (int i = 0; i < kWideRows; ++i) {
+    rr[i] = r0 + i * kWideSlots;
+    act[i] = rr[i] < K;
+  }
+  const float tau2 = a.tau2;
+  auto fail = [&](int c) {
+    if (tid == 0) atomicExch(t.err, 1);
+    stream_drain(full, gc0 + (unsigned)c, gc0 + (unsigned)min(nch, c + kStreamSlots));
+    gc = gc0 + (unsigned)nch;   // bookkeeping only; the caller stops
+  };
+  int c = 0;                                      // chunk being read
+  if (!stream_wait(full, gc0, t.err)) {
+    fail(0);
+    return false;
+  }
+  for (int q = 0; q < 2 * m - 1; ++q) {
+    if (q == m) {
+      // all fluxes are in X: publish F^1, then E^k = F^k - F^{k-1} into D
+      __syncthreads();
+      if (vec) {
+        for (int i = tid; i < K * (ST / 4); i += blockDim.x) {
+          const int r = i / (ST / 4), v = i - r * (ST / 4);
+          *reinterpret_cast<float4 *>(a.flux + rows[r] * S + s0 + v * 4) = reinterpret_cast<const float4 *>(X)[i];
+        }
+      } else {
+        for (int i = tid; i < K * ST; i += blockDim.x) {
+          const int r = i / ST, s = i - r * ST;
+          if (s < ns) a.flux[rows[r] * S + s0 + s] = X[i];
+        }
+      }
+      for (int i = tid; i < (m - 1) * K * ST; i += blockDim.x) {
+        const size_t jj = (size_t)K * ST + i;
+        D[jj] = X[jj] - X[jj - (size_t)K * ST];
+      }
+      __syncthreads();
+    }
+    const int layer = q < m ? q : q - m + 1;
+    const bool tri = fac && q == m - 1;           // the factored last coefficient, rows descending
+    float acc[kWideRows][CP], yv[kWideRows][CP];
+#pragma unroll
+    for (int i = 0; i < kWideRows; ++i)
+#pragma unroll
+      for (int e = 0; e < CP; ++e) acc[i][e] = yv[i][e] = 0.f;
+    const float *Dl = D + (size_t)layer * K * ST + CP * g;
+    for (int j0 = 0; j0 < K;) {
+      const int fr = q * K + j0;
+      if (fr >= (c + 1) * CR) {
+        // chunk c consumed by every thread: refill its slot, move to the next chunk
+        __syncthreads();
+        if (tid == 0 && c + kStreamSlots < nch) issue(c + kStreamSlots);
+        ++c;
+        if (!stream_wait(full, gc0 + (unsigned)c, t.err)) {
+          fail(c);
+          return false;
+        }
+      }
+      const int j1 = min(K, (c + 1) * CR - q * K);
+      const int n = j1 - j0;
+      const float *sp = reinterpret_cast<const float *>(ring + (size_t)((gc0 + c) % kStreamSlots) * kStreamChunk) +
+                        (size_t)(fr - c * CR) * Kq;
+      if (!tri) {
+        // acc[i] += G[j][r_i] D^layer_j, j = j0 .. j1-1 ascending
+#pragma unroll 2
+        for (int h = 0; h < n; ++h) {
+          const float4 *dp = reinterpret_cast<const float4 *>(Dl + (size_t)(j0 + h) * ST);
+          const float4 d0 = dp[0], d1 = dp[1];
+#pragma unroll
+          for (int i = 0; i < kWideRows; ++i)
+            if (act[i]) fma8(acc[i], sp[(size_t)h * Kq + rr[i]], d0, d1);
+        }
+      } else {
+        // stored position p holds row K-1-p: the segment covers rows jt = K-1-j0 down to jb
+        const int jt = K - 1 - j0, jb = K - j1;
+#pragma unroll 2
+        for (int h = 0; h < n; ++h) {
+          const int j = jt - h;
+          const float4 *dp = reinterpret_cast<const float4 *>(Dl + (size_t)j * ST);
+          const float4 d0 = dp[0], d1 = dp[1];
+#pragma unroll
+          for (int i = 0; i < kWideRows; ++i)
+            if (act[i] && rr[i] <= j) fma8(yv[i], sp[(size_t)h * Kq + rr[i]], d0, d1);
+        }
+        // the y of this segment's rows are complete: share them
+#pragma unroll
+        for (int i = 0; i < kWideRows; ++i)
+          if (act[i] && rr[i] >= jb && rr[i] <= jt) {
+            float4 *o = reinterpret_cast<float4 *>(Ys + (size_t)rr[i] * ST + CP * g);
+            o[0] = make_float4(yv[i][0], yv[i][1], yv[i][2], yv[i][3]);
+            o[1] = make_float4(yv[i][4], yv[i][5], yv[i][6], yv[i][7]);
+          }
+        __syncthreads();
+#pragma unroll 2
+        for (int h = 0; h < n; ++h) {
+          const int j = jt - h;
+          const float4 *yp = reinterpret_cast<const float4 *>(Ys + (size_t)j * ST + CP * g);
+          const float4 y0 = yp[0], y1 = yp[1];
+#pragma unroll
+          for (int i = 0; i < kWideRows; ++i)
+            if (act[i] && rr[i] >= j) fma8(acc[i], sp[(size_t)h * Kq + rr[i]], y0, y1);
+        }
+      }
+      j0 = j1;
+    }
+    // end of matrix q: rows of F^{q+1}, or leapfrog of U^k with Gamma-hat^k E^k
+#pragma unroll
+    for (int i = 0; i < kWideRows; ++i) {
+      if (!act[i]) continue;
+      const int r = rr[i];
+      if (q < m) {
+        float4 *o = reinterpret_cast<float4 *>(X + ((size_t)q * K + r) * ST + CP * g);
+        o[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        o[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+      } else {
+        const int k = q - m + 1;
+        const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + CP * g;
+        if (vec) {
+#pragma unroll
+          for (int h = 0; h < CP / 4; ++h) {
+            const float4 nw = *reinterpret_cast<const float4 *>(cs + base + 4 * h);
+            float4 od = *reinterpret_cast<const float4 *>(cso + base + 4 * h);
+            od.x = 2.f * nw.x - od.x + tau2 * acc[i][4 * h + 0];
+            od.y = 2.f * nw.y - od.y + tau2 * acc[i][4 * h + 1];
+            od.z = 2.f * nw.z - od.z + tau2 * acc[i][4 * h + 2];
+            od.w = 2.f * nw.w - od.w + tau2 * acc[i][4 * h + 3];
+            *reinterpret_cast<float4 *>(cso + base + 4 * h) = od;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < CP; ++e)
+            if (CP * g + e < ns) cso[base + e] = 2.f * cs[base + e] - cso[base + e] + tau2 * acc[i][e];
+        }
+      }
+    }
+  }
+  __syncthreads();   // last chunk consumed (its slot may be refilled by the next item)
+  if (m == 1) {
+    // no interior layers: publish F^1 here
+    for (int i = tid; i < K * ST; i += blockDim.x) {
+      const int r = i / ST, s = i - r * ST;
+      if (s < ns) a.flux[rows[r] * S + s0 + s] = X[i];
+    }
+  }
+  gc = gc0 + (unsigned)nch;
+  return true;
+}
+
+__global__ void __launch_bounds__(kWideThreads, 1) k_cell_w(const StepArgs<float> a, const StreamArgs t, const int cur) {
+  extern __shared__ __align__(128) unsigned char smem_w[];
+  if (*(volatile const int *)t.err) return;
+  stream_init(smem_w);
+  unsigned gc = 0;
+  const int tiles = (a.S + kStreamST - 1) / kStreamST;   // 1-D grid, tiles of a cell adjacent
+  cell_wide_item(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_w, gc);
+}
+
+}  // namespace mss

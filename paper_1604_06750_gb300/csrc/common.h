@@ -116,6 +116,11 @@ struct Partition {
   // empty where the DCT reading applies
   std::vector<std::vector<double>> user_bases;
   std::vector<int> user_M;
+  // nodes strictly inside cells whose Galerkin lift (Remark MFEM) the off-line stage computes
+  // (mss_partition_set_lift_nodes): unknown, cell, and position in the cell's node list
+  std::vector<int64_t> lift_unknown;
+  std::vector<int> lift_cell;
+  std::vector<int64_t> lift_local;
 
   int faces_of(int64_t u, const int32_t **list) const {
     *list = nf_face.data() + nf_ptr[u];
@@ -148,6 +153,15 @@ struct Rom {
   std::vector<int64_t> basis_off;
   std::vector<double> bases;
   const Partition *source = nullptr;
+  // Galerkin lift of the partition's lift nodes (built ROMs): node l of cell lift_cell[l] reads
+  // sum_k w_k . U^k with w = lift_w[lift_off[l] ..] (m_c blocks of K_c values, layer 1 first)
+  std::vector<int64_t> lift_unknown, lift_off;
+  std::vector<int> lift_cell;
+  std::vector<double> lift_w;
+  // receivers read off hidden layers (layer 2..m of a cell): receiver, cell, layer (1-based),
+  // K_c values each, concatenated
+  std::vector<int32_t> rcv_h_index, rcv_h_cell, rcv_h_layer;
+  std::vector<double> rcv_h_vals;
   mss_rom_params prm{};            // parameters of the off-line construction (built ROMs)
 
   void finalize_topology();   // validates and fills cell_K, coef_off, fmass_off

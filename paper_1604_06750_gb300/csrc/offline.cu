@@ -397,9 +397,13 @@ __global__ void k_chol_inv(double *Linv, double *G, const double *pre, const int
 
 // Block Lanczos (Appendix C) + symmetric GammaTrans on A^m (n x n, n = m K) and S^m (n x K), one
 // block per cell.  Workspace per cell: n^2 + 3 n K + 8 K^2 doubles.
+// Lift rows (optional): cell c owns rows lift_ptr[c] .. lift_ptr[c+1]-1, row l holds V^T e_n (n values,
+// the cell's Krylov basis at one interior node) and receives the lift weights w_k = G_k^{-T} Q_k^T V^T e_n,
+// k = 1..m, as m blocks of K values (Remark MFEM: the value at node n is sum_k w_k . U^k).
 __global__ void k_lanczos_gamma(const double *Am, const int64_t *am_off, const double *Sm, const int64_t *sm_off,
                                 const int32_t *Kt, const int32_t *mc, double *work, const int64_t *work_off, double *gam,
-                                double *gh, const int64_t *coef_off, int *status) {
+                                double *gh, const int64_t *coef_off, int *status, const int32_t *lift_ptr,
+                                const double *lift_v, double *lift_w, const int64_t lift_ld) {
   const int c = blockIdx.x;
   const int K = Kt[c], m = mc[c], n = m * K;
   const double *A = Am + am_off[c];
@@ -412,6 +416,7 @@ __global__ void k_lanczos_gamma(const double *Am, const int64_t *am_off, const d
   double *k1 = T + (int64_t)n * K;        // K x K scratch x 8
   double *k2 = k1 + K * K, *k3 = k2 + K * K, *k4 = k3 + K * K, *Gm = k4 + K * K, *Gp = Gm + K * K;
   double *alpha = Gp + K * K, *beta = alpha + K * K;
+  double *tl = beta + K * K;              // K: Q_k^T v of one lift row
   double *G = gam + coef_off[c], *H = gh + coef_off[c];
   __shared__ double anorm;
   __shared__ int bad;
@@ -469,6 +474,24 @@ __global__ void k_lanczos_gamma(const double *Am, const int64_t *am_off, const d
     bsym(G + (int64_t)k * K * K, K, K);
     bsym(H + (int64_t)k * K * K, K, K);
     bcopy(Gp, K, G + (int64_t)k * K * K, K, K, K, 1.0);
+    // lift weights of layer k+1: w = G_k^{-T} (Q_k^T v), with k2 = G_k^{-1} still in place
+    if (lift_ptr)
+      for (int l = lift_ptr[c]; l < lift_ptr[c + 1]; ++l) {
+        const double *v = lift_v + (int64_t)l * lift_ld;
+        for (int i = threadIdx.x; i < K; i += blockDim.x) {
+          double t = 0;
+          for (int r = 0; r < n; ++r) t += Qk[(int64_t)r * n + i] * v[r];
+          tl[i] = t;
+        }
+        __syncthreads();
+        double *wl = lift_w + (int64_t)l * lift_ld + (int64_t)k * K;
+        for (int i = threadIdx.x; i < K; i += blockDim.x) {
+          double t = 0;
+          for (int j = 0; j < K; ++j) t += k2[(int64_t)j * K + i] * tl[j];
+          wl[i] = t;
+        }
+        __syncthreads();
+      }
     if (k + 1 == m) break;
     // Wk -= Q_k alpha_k; full reorthogonalisation against Q_1..Q_k (two passes)
     bgemm(Wk, K, Qk, n, false, alpha, K, false, n, K, K, -1.0, 1.0);
@@ -744,7 +767,7 @@ static void build_chunk(const Partition &P, const std::vector<int> &cells, const
     const int64_t n = (int64_t)mc[i] * Kt[i];
     am_off[i + 1] = am_off[i] + n * n;
     sm_off[i + 1] = sm_off[i] + n * Kt[i];
-    work_off[i + 1] = work_off[i] + n * n + 3 * n * Kt[i] + 8 * (int64_t)Kt[i] * Kt[i];
+    work_off[i + 1] = work_off[i] + n * n + 3 * n * Kt[i] + 8 * (int64_t)Kt[i] * Kt[i] + Kt[i];
     coef_off[i + 1] = coef_off[i] + (int64_t)mc[i] * Kt[i] * Kt[i];
   }
   DevMem d_am, d_sm, d_work, d_gam, d_gh, d_amoff, d_smoff, d_workoff, d_coefoff;
@@ -768,10 +791,42 @@ static void build_chunk(const Partition &P, const std::vector<int> &cells, const
     k_pack_sm<<<nc, kThreads, 0, st>>>(d_sm.as<double>(), d_smoff.as<int64_t>(), V[j2].as<double>(), d_Cb.as<double>(),
                                        d_cboff.as<int64_t>(), r0, d_Kb.as<int32_t>(), kt, d_mc.as<int32_t>(), W, j2);
   }
+  // lift rows: V^T e_n of every lift node of these cells (m blocks of the node's row of V_j)
+  std::vector<int32_t> lptr(nc + 1, 0);
+  std::vector<int> lnode;                    // index into P.lift_* per lift row
+  {
+    std::vector<int> chunk_pos(P.n_cells, -1);
+    for (int i = 0; i < nc; ++i) chunk_pos[cells[i]] = i;
+    std::vector<std::vector<int>> per(nc);
+    for (size_t l = 0; l < P.lift_cell.size(); ++l)
+      if (chunk_pos[P.lift_cell[l]] >= 0) per[chunk_pos[P.lift_cell[l]]].push_back((int)l);
+    for (int i = 0; i < nc; ++i) {
+      lptr[i + 1] = lptr[i] + (int32_t)per[i].size();
+      lnode.insert(lnode.end(), per[i].begin(), per[i].end());
+    }
+  }
+  DevMem d_lptr, d_lv, d_lw;
+  int64_t lw_stride = 0;
+  for (int i = 0; i < nc; ++i) lw_stride = std::max<int64_t>(lw_stride, (int64_t)mc[i] * Kt[i]);
+  if (!lnode.empty()) {
+    // one row per lift node, padded to the longest basis of the chunk; row l uses its cell's n
+    upload(d_lptr, lptr);
+    d_lv.alloc((size_t)lnode.size() * lw_stride * 8);
+    d_lw.alloc((size_t)lnode.size() * lw_stride * 8);
+    for (int i = 0; i < nc; ++i)
+      for (int l = lptr[i]; l < lptr[i + 1]; ++l) {
+        const int64_t row = row0[i] + P.lift_local[lnode[l]];
+        for (int j = 0; j < mc[i]; ++j)
+          MSS_CUDA(cudaMemcpyAsync(d_lv.as<double>() + (int64_t)l * lw_stride + (int64_t)j * Kt[i],
+                                   V[j].as<double>() + row * W, (size_t)Kt[i] * 8, cudaMemcpyDeviceToDevice, st));
+      }
+  }
   // the per-cell Am blocks from k_gram are V_j1^T A V_j2; symmetrise is done inside the Lanczos kernel
   k_lanczos_gamma<<<nc, kThreads, 0, st>>>(d_am.as<double>(), d_amoff.as<int64_t>(), d_sm.as<double>(), d_smoff.as<int64_t>(),
                                            kt, d_mc.as<int32_t>(), d_work.as<double>(), d_workoff.as<int64_t>(),
-                                           d_gam.as<double>(), d_gh.as<double>(), d_coefoff.as<int64_t>(), status);
+                                           d_gam.as<double>(), d_gh.as<double>(), d_coefoff.as<int64_t>(), status,
+                                           lnode.empty() ? nullptr : d_lptr.as<int32_t>(), d_lv.as<double>(),
+                                           d_lw.as<double>(), lw_stride);
   MSS_CUDA(cudaGetLastError());
   MSS_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
   std::vector<double> gam(coef_off[nc]), gh(coef_off[nc]);
@@ -783,6 +838,18 @@ static void build_chunk(const Partition &P, const std::vector<int> &cells, const
     const int c = cells[i];
     std::copy(gam.begin() + coef_off[i], gam.begin() + coef_off[i + 1], R.gamma.begin() + R.coef_off[c]);
     std::copy(gh.begin() + coef_off[i], gh.begin() + coef_off[i + 1], R.gamma_hat.begin() + R.coef_off[c]);
+  }
+  if (!lnode.empty()) {
+    std::vector<double> lw((size_t)lnode.size() * lw_stride);
+    MSS_CUDA(cudaMemcpyAsync(lw.data(), d_lw.p, lw.size() * 8, cudaMemcpyDeviceToHost, st));
+    MSS_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < nc; ++i)
+      for (int l = lptr[i]; l < lptr[i + 1]; ++l) {
+        const int g = lnode[l];
+        const int64_t n = (int64_t)mc[i] * Kt[i];
+        std::copy(lw.begin() + (int64_t)l * lw_stride, lw.begin() + (int64_t)l * lw_stride + n,
+                  R.lift_w.begin() + R.lift_off[g]);
+      }
   }
 }
 
@@ -858,6 +925,13 @@ static void rom_topology(Partition &P, const mss_rom_params &prm, const int32_t 
   R.gamma_hat.assign(R.coef_off[nc], 0.0);
   Kt.assign(nc, 0);
   mv.assign(nc, 0);
+  // Galerkin lift of the partition's lift nodes: m_c K_c weights each, filled by the exact build
+  R.lift_unknown = P.lift_unknown;
+  R.lift_cell = P.lift_cell;
+  R.lift_off.assign(P.lift_cell.size() + 1, 0);
+  for (size_t l = 0; l < P.lift_cell.size(); ++l)
+    R.lift_off[l + 1] = R.lift_off[l] + (int64_t)R.cell_m[P.lift_cell[l]] * R.cell_K[P.lift_cell[l]];
+  R.lift_w.assign(R.lift_off.back(), 0.0);
   Cb.assign(nc, std::vector<double>());
   for (int c = 0; c < nc; ++c) {
     P.build_cell(c);

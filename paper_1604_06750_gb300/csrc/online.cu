@@ -46,6 +46,12 @@ struct StepArgs {
   // receivers
   const int32_t *rcv_ptr, *rcv_face;
   const int64_t *rcv_off;
+  // receivers read off hidden layers (Galerkin lift of nodes inside cells; null when none): per
+  // receiver entries rh_ptr[r]..rh_ptr[r+1]-1 of rh_cnt values at rh_val + rh_off, dotted with the
+  // current cell state rows rh_row0 .. rh_row0 + rh_cnt - 1
+  const int32_t *rh_ptr, *rh_cnt;
+  const int64_t *rh_row0, *rh_off;
+  const T *rh_val;
   // corners: members listed per face (fm_*), per corner group (grp_ptr), member data (mem_*),
   // faces that carry members (cfaces)
   const int32_t *fm_ptr, *fm_member, *mem_group, *mem_face, *grp_ptr, *cfaces;
@@ -126,22 +132,23 @@ __device__ __forceinline__ void row_times_block(const T *__restrict__ G, int K, 
   }
 }
 
-// acc[s] += sum_{c0 <= c < c1} G[c*K] * X[c*ST + s]: the same register-pipelined column stream as
-// row_times_block over a column range (one triangle of a factored coefficient), accumulating.
+// acc[s] += sum over c = c1-1 down to c0 of G[c*K] * X[c*ST + s]: the column stream of
+// row_times_block over a column range in descending order (one triangle of a factored
+// coefficient; the streamed kernels meet the rows of that matrix in the same order), accumulating.
 template <typename T, int ST>
-__device__ __forceinline__ void row_times_range(const T *__restrict__ G, int K, const T *__restrict__ X, int c0,
-                                                int c1, T (&acc)[ST]) {
+__device__ __forceinline__ void row_times_range_desc(const T *__restrict__ G, int K, const T *__restrict__ X, int c0,
+                                                     int c1, T (&acc)[ST]) {
   T g[kChunk], gn[kChunk];
 #pragma unroll
-  for (int j = 0; j < kChunk; ++j) g[j] = c0 + j < c1 ? __ldg(G + (size_t)(c0 + j) * K) : T(0);
-  for (int cb = c0; cb < c1; cb += kChunk) {
-    const int cn = cb + kChunk;
+  for (int j = 0; j < kChunk; ++j) g[j] = c1 - 1 - j >= c0 ? __ldg(G + (size_t)(c1 - 1 - j) * K) : T(0);
+  for (int cb = c1 - 1; cb >= c0; cb -= kChunk) {
+    const int cn = cb - kChunk;
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) gn[j] = (cn + j < c1) ? __ldg(G + (size_t)(cn + j) * K) : T(0);
+    for (int j = 0; j < kChunk; ++j) gn[j] = (cn - j >= c0) ? __ldg(G + (size_t)(cn - j) * K) : T(0);
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) {
-      if (cb + j < c1) {
-        const T *x = X + (cb + j) * ST;
+      if (cb - j >= c0) {
+        const T *x = X + (cb - j) * ST;
         if constexpr (std::is_same<T, float>::value && ST % 2 == 0) {
 #pragma unroll
           for (int s = 0; s < ST; s += 2) fma2(acc[s], acc[s + 1], g[j], x[s], x[s + 1]);
@@ -164,7 +171,7 @@ __device__ __forceinline__ float4 pack_vec(const float (&d)[4]) { return make_fl
 __device__ __forceinline__ double2 pack_vec(const double (&d)[2]) { return make_double2(d[0], d[1]); }
 
 // One (cell, source tile) of the cell phase with the CUDA cores; any block size.
-template <typename T, int ST>
+template <typename T, int ST, int FAC = -1>   // FAC: 0/1 fixes the factored-last flag at compile time, -1 reads it
 __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, const int cell, const int tile,
                                           unsigned char *smem_raw) {
   const int s0 = tile * ST;
@@ -173,7 +180,8 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
   T *X = reinterpret_cast<T *>(smem_raw);        // U (layers 1..m, [k][r][s]), then F^k
   T *D = X + (size_t)m * K * ST;                 // U^{k+1} - U^k, then F^k - F^{k-1}
   T *Y = D + (size_t)m * K * ST;                 // factored last coefficient: L^T D^m (even length)
-  const size_t ylen = a.factor_last ? (((size_t)K * ST + 1) & ~(size_t)1) : 0;
+  const bool fac = FAC < 0 ? a.factor_last != 0 : FAC != 0;
+  const size_t ylen = fac ? (((size_t)K * ST + 1) & ~(size_t)1) : 0;
   int64_t *rows = reinterpret_cast<int64_t *>(Y + ylen);   // K boundary rows: face row*2+side
   const T *fs = cur ? a.fstate1 : a.fstate0;
   const T *cs = cur ? a.cstate1 : a.cstate0;
@@ -216,7 +224,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
   __syncthreads();
   // fluxes F^k = Gamma^k D^k into X (U is not needed any more: the "now" level is re-read below)
   const T *G = a.coef + a.cell_coef[cell];
-  if (!a.factor_last) {
+  if (!fac) {
     for (int it = threadIdx.x; it < m * K; it += blockDim.x) {
       const int k = it / K, r = it - k * K;
       T acc[ST];
@@ -227,8 +235,9 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
     __syncthreads();
   } else {
     // F^1..F^{m-1} as above; F^m = L (L^T D^m) with W = L + L^T - diag(L) read column by column:
-    // y_r = sum_{c >= r} W[c][r] D^m_c (L^T), then F^m_r = sum_{c <= r} W[c][r] y_c (L).  Rows r
-    // and K-1-r share an item, so every item streams K+1 coefficients of the triangle pair.
+    // y_r = sum_{c >= r} W[c][r] D^m_c (L^T), then F^m_r = sum_{c <= r} W[c][r] y_c (L), both
+    // summed over c in descending order.  Rows r and K-1-r share an item, so every item streams
+    // K+1 coefficients of the triangle pair.
     const T *W = G + (size_t)(m - 1) * K * K;
     const T *Dm = D + (size_t)(m - 1) * K * ST;
     const int full = (m - 1) * K, pairs = (K + 1) / 2;
@@ -247,7 +256,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
           T acc[ST];
 #pragma unroll
           for (int s = 0; s < ST; ++s) acc[s] = T(0);
-          row_times_range<T, ST>(W + r, K, Dm, r, K, acc);
+          row_times_range_desc<T, ST>(W + r, K, Dm, r, K, acc);
 #pragma unroll
           for (int s = 0; s < ST; ++s) Y[r * ST + s] = acc[s];
         }
@@ -261,7 +270,7 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
         T acc[ST];
 #pragma unroll
         for (int s = 0; s < ST; ++s) acc[s] = T(0);
-        row_times_range<T, ST>(W + r, K, Y, 0, r + 1, acc);
+        row_times_range_desc<T, ST>(W + r, K, Y, 0, r + 1, acc);
 #pragma unroll
         for (int s = 0; s < ST; ++s) X[(size_t)(m - 1) * K * ST + r * ST + s] = acc[s];
       }
@@ -312,12 +321,14 @@ __device__ __forceinline__ void cell_item(const StepArgs<T> &a, const int cur, c
   }
 }
 
-template <typename T, int ST>
+// FAC: the factored last coefficient (a separate instantiation, so that the plain kernel keeps
+// its register budget)
+template <typename T, int ST, bool FAC = false>
 __global__ void __launch_bounds__(kCellThreads, sizeof(T) == 4 ? 4 : 2) k_cell(const StepArgs<T> a, const int cur) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // 1-D grid, source tiles of a cell adjacent so that they share its coefficients in L2
   const int tiles = (a.S + ST - 1) / ST;
-  cell_item<T, ST>(a, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_raw);
+  cell_item<T, ST, FAC ? 1 : 0>(a, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_raw);
 }
 
 // Item b of the face phase: b < n_faces is a face update, the rest are receiver blocks of
@@ -446,6 +457,14 @@ __device__ __forceinline__ void face_item(const StepArgs<T> &a, const int cur, c
       const T *q = a.rcv_val + a.rcv_off[e];
       for (int c = 0; c < M; ++c) acc += q[c] * fs[(row0 + c) * S + s0 + s];
     }
+    if (a.rh_ptr) {
+      const T *cs = cur ? a.cstate1 : a.cstate0;
+      for (int e = a.rh_ptr[r]; e < a.rh_ptr[r + 1]; ++e) {
+        const int64_t row0 = a.rh_row0[e];
+        const T *q = a.rh_val + a.rh_off[e];
+        for (int c = 0; c < a.rh_cnt[e]; ++c) acc += q[c] * cs[(row0 + c) * S + s0 + s];
+      }
+    }
     traces[(int64_t)r * S + s0 + s] = acc;
   }
 }
@@ -559,6 +578,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, co
 
 #include "cell_tc.cuh"
 #include "cell_stream.cuh"
+#include "cell_wide.cuh"
 #include "cell_split.cuh"
 #include "cell_tc_split.cuh"
 #include "cell_tc_pipe.cuh"
@@ -569,7 +589,7 @@ namespace mss {
 struct SimDev {
   DevMem cell_K, cell_m, cell_coef, cell_ghat, cell_state, cell_row, row_face_row, row_side;
   DevMem face_M, face_two, face_row, face_minv, fsrc_ptr, fsrc_index, fsrc_val;
-  DevMem rcv_ptr, rcv_face, rcv_off;
+  DevMem rcv_ptr, rcv_face, rcv_off, rh_ptr, rh_cnt, rh_row0, rh_off, rh_val;
   DevMem fm_ptr, fm_member, mem_group, mem_face, grp_ptr, mem_row, fm_roff, fm_info, fm_rows;
   DevMem coef, minv, src_val, rcv_val, cg_rows, cg_w;
   DevMem fstate[2], cstate[2], flux, uhat, cfaces, wbuf, tbuf;
@@ -601,10 +621,13 @@ struct mss_sim {
   size_t tcq_smem = 0;
   int tc_kpmax = 16, st_max = 1, dev_smem = 0;
   bool stream_blob = false;                    // streamed-kernel coefficient copy present
+  bool wide_blob = false, wide_ok = false;     // wide streamed kernel (K_i up to 512) usable
+  size_t wide_smem = 0;
   mss::TcArgs tca{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
   int factor_last = 0;                         // FP32: Gamma^m applied as L (L^T .)
+  int n_rh = 0;                                // receiver entries on hidden layers
   int64_t face_rows = 0, cell_rows = 0;
   int64_t steps = 0;
   int cur = 0;
@@ -658,6 +681,11 @@ static StepArgs<T> make_args(const mss_sim &s) {
   a.rcv_ptr = d.rcv_ptr.as<int32_t>();
   a.rcv_face = d.rcv_face.as<int32_t>();
   a.rcv_off = d.rcv_off.as<int64_t>();
+  a.rh_ptr = s.n_rh ? d.rh_ptr.as<int32_t>() : nullptr;
+  a.rh_cnt = d.rh_cnt.as<int32_t>();
+  a.rh_row0 = d.rh_row0.as<int64_t>();
+  a.rh_off = d.rh_off.as<int64_t>();
+  a.rh_val = d.rh_val.as<T>();
   a.fm_ptr = d.fm_ptr.as<int32_t>();
   a.fm_member = d.fm_member.as<int32_t>();
   a.mem_group = d.mem_group.as<int32_t>();
@@ -713,6 +741,10 @@ static void set_smem_attrs(const mss_sim &s) {
     MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
   }
   MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
+  if (s.factor_last)
+    MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
+  if (s.wide_ok)
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.wide_smem));
   if (s.stream_ok)
   {
     MSS_CUDA(cudaFuncSetAttribute(k_cell_s<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.stream_smem));
@@ -755,12 +787,14 @@ static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStr
   const dim3 gc(s.n_cells * s.tiles);
   if constexpr (std::is_same<T, float>::value && ST == kStreamST) {
     if (s.sched == MSS_SCHED_GRAPH_STREAM) {
-      if (s.stream_groups == 4) k_cell_s<4><<<gc, 512, s.stream_smem, st>>>(a, s.sca, cur);
+      if (!s.stream_ok) k_cell_w<<<gc, kWideThreads, s.wide_smem, st>>>(a, s.sca, cur);
+      else if (s.stream_groups == 4) k_cell_s<4><<<gc, 512, s.stream_smem, st>>>(a, s.sca, cur);
       else k_cell_s<2><<<gc, 256, s.stream_smem, st>>>(a, s.sca, cur);
       return;
     }
   }
-  k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
+  if (s.factor_last) k_cell<T, ST, true><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
+  else k_cell<T, ST><<<gc, kCellThreads, s.cell_smem, st>>>(a, cur);
 }
 
 template <typename T>
@@ -1118,6 +1152,7 @@ static void apply_tile(mss_sim &s, int ST) {
                                       (s.corners ? (size_t)s.max_nm * s.max_M : 0)) * es);
   s.split_smem = (size_t)s.max_K * ST * es + 8 * (size_t)s.max_K;
   s.stream_ok = s.stream_blob && ST == kStreamST;
+  s.wide_ok = s.wide_blob && ST == kStreamST;
 }
 
 // Sizes and residency of the split / pipelined tensor-core kernels with NT sources per CTA.
@@ -1316,12 +1351,17 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
     s.n_accel_items = (int)ai.size();
     s.split_smem = (size_t)s.max_K * s.ST * es + 8 * (size_t)s.max_K;
   }
-  // streamed cell kernel: FP32 CUDA-core path with 16-source tiles and K_i <= 128; the same
-  // matrices as coef, each row padded to Kq = K rounded up to 4 floats (16-byte rows)
-  if (prec == MSS_FP32 && !s.tc && !s.factor_last && s.ST == kStreamST && s.max_K <= 128) {
+  // streamed cell kernels: FP32 CUDA-core path with 16-source tiles; the same matrices as coef,
+  // each row padded to Kq = K rounded up to 4 floats (16-byte rows).  k_cell_s takes K_i <= 128
+  // (not the factored last coefficient), the wide kernel K_i <= 512; in the wide kernel's copy the
+  // factored last coefficient's rows are stored in descending order.
+  if (prec == MSS_FP32 && !s.tc && s.ST == kStreamST) {
     const size_t need = (size_t)kStreamSlots * kStreamChunk + 64 + 2 * (size_t)s.max_m * s.max_K * kStreamST * 4 +
                         8 * (size_t)s.max_K;
-    if (need <= (size_t)dev_smem) {
+    const bool narrow = !s.factor_last && s.max_K <= 128 && need <= (size_t)dev_smem;
+    const size_t wneed = wide_smem_bytes(s.max_m, s.max_K, s.factor_last);
+    const bool wide = s.max_K <= kWideSlots * kWideRows && wneed <= (size_t)dev_smem;
+    if (narrow || wide) {
       std::vector<float> blob;
       std::vector<int64_t> soff(R.n_cells);
       std::vector<int32_t> kq(R.n_cells);
@@ -1331,7 +1371,8 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
         soff[c] = (int64_t)blob.size();
         const double *src = coef.data() + cell_coef[c];
         for (int q = 0; q < 2 * m - 1; ++q)
-          for (int j = 0; j < K; ++j) {
+          for (int jj = 0; jj < K; ++jj) {
+            const int j = (s.factor_last && q == m - 1) ? K - 1 - jj : jj;
             for (int r = 0; r < K; ++r) blob.push_back((float)src[(size_t)q * K * K + (size_t)j * K + r]);
             for (int r = K; r < Kq; ++r) blob.push_back(0.f);
           }
@@ -1342,9 +1383,15 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
       s.sca.coef = s.d.sc_coef.as<float>();
       s.sca.coef_off = s.d.sc_off.as<int64_t>();
       s.sca.Kq = s.d.sc_Kq.as<int32_t>();
-      s.stream_smem = need;
-      s.stream_blob = true;
-      s.stream_ok = true;
+      if (narrow) {
+        s.stream_smem = need;
+        s.stream_blob = true;
+        s.stream_ok = true;
+      } else {
+        s.wide_smem = wneed;
+        s.wide_blob = true;
+        s.wide_ok = true;
+      }
     }
   }
   if (!s.tc) upload(s.d.tc_err, std::vector<int>(1, 0));   // error word of the bounded waits
@@ -1380,6 +1427,25 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
       }
     rcv_ptr[r + 1] = (int32_t)rcv_face.size();
   }
+  // receivers on hidden layers (lifted nodes inside cells), grouped per receiver
+  std::vector<int32_t> rh_ptr(R.n_rcv + 1, 0), rh_cnt;
+  std::vector<int64_t> rh_row0, rh_off;
+  std::vector<double> rh_val;
+  for (int r = 0; r < R.n_rcv; ++r) {
+    int64_t o = 0;
+    for (size_t e = 0; e < R.rcv_h_index.size(); ++e) {
+      const int c = R.rcv_h_cell[e], K = R.cell_K[c];
+      if (R.rcv_h_index[e] == r) {
+        rh_row0.push_back(cell_state[c] + (int64_t)(R.rcv_h_layer[e] - 2) * K);
+        rh_cnt.push_back(K);
+        rh_off.push_back((int64_t)rh_val.size());
+        rh_val.insert(rh_val.end(), R.rcv_h_vals.begin() + o, R.rcv_h_vals.begin() + o + K);
+      }
+      o += K;
+    }
+    rh_ptr[r + 1] = (int32_t)rh_row0.size();
+  }
+  s.n_rh = (int)rh_row0.size();
   // corner groups
   std::vector<int32_t> fm_ptr(R.n_faces + 1, 0), fm_member, mem_group, mem_face, grp_ptr, cfaces;
   std::vector<int64_t> mem_row, fm_roff;
@@ -1440,6 +1506,10 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
   upload(d.rcv_ptr, rcv_ptr);
   upload(d.rcv_face, rcv_face);
   upload(d.rcv_off, rcv_off);
+  upload(d.rh_ptr, rh_ptr);
+  upload(d.rh_cnt, rh_cnt);
+  upload(d.rh_row0, rh_row0);
+  upload(d.rh_off, rh_off);
   upload(d.fm_ptr, fm_ptr);
   upload(d.fm_member, fm_member);
   upload(d.mem_group, mem_group);
@@ -1457,6 +1527,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
   up(d.minv, minv);
   up(d.src_val, R.src_vals);
   up(d.rcv_val, R.rcv_vals);
+  up(d.rh_val, rh_val);
   up(d.cg_rows, s.corners ? R.cg_rows : std::vector<double>());
   up(d.cg_w, s.corners ? R.cg_weight : std::vector<double>());
   up(d.fm_rows, fm_rows);
@@ -1723,10 +1794,11 @@ mss_status mss_step_profile(mss_sim *s, int64_t n_steps, const double *waveform,
 }
 
 static bool sched_allowed(const mss_sim &s, int sched) {
-  if (s.factor_last) return sched == MSS_SCHED_GRAPH || sched == MSS_SCHED_PERSIST;
+  if (s.factor_last)
+    return sched == MSS_SCHED_GRAPH || sched == MSS_SCHED_PERSIST || (sched == MSS_SCHED_GRAPH_STREAM && s.wide_ok);
   switch (sched) {
     case MSS_SCHED_GRAPH: return true;
-    case MSS_SCHED_GRAPH_STREAM: return s.stream_ok;
+    case MSS_SCHED_GRAPH_STREAM: return s.stream_ok || s.wide_ok;
     case MSS_SCHED_PERSIST: return true;   // tensor-core precisions: pipelined split kernels
     case MSS_SCHED_PERSIST_STREAM: return s.tc ? s.tcq_nt > 0 : s.stream_ok;
     case MSS_SCHED_GRAPH_SPLIT: return s.tc ? true : s.split_smem <= 48 * 1024;

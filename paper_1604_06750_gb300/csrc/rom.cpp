@@ -239,6 +239,48 @@ mss_status mss_partition_set_face_bases(mss_partition *p, int32_t n_faces, const
   });
 }
 
+mss_status mss_partition_set_lift_nodes(mss_partition *p, int32_t n, const int32_t *nodes) {
+  return guard([&] {
+    MSS_REQUIRE(p && n >= 0 && (n == 0 || nodes), MSS_ERR_INVALID_ARG, "bad argument");
+    Partition &P = p->p;
+    const Operator &o = *P.op;
+    std::vector<int64_t> lu, ll;
+    std::vector<int> lc;
+    int64_t str[3];
+    str[o.g.dim - 1] = 1;
+    for (int a = o.g.dim - 2; a >= 0; --a) str[a] = str[a + 1] * (o.g.n[a + 1] + 1);
+    for (int32_t j = 0; j < n; ++j) {
+      int64_t pn = 0;
+      int cc[3] = {0, 0, 0};
+      for (int a = 0; a < o.g.dim; ++a) {
+        const int32_t x = nodes[(int64_t)j * o.g.dim + a];
+        MSS_REQUIRE(x >= 0 && x <= o.g.n[a], MSS_ERR_INVALID_ARG, "lift node outside the grid");
+        pn += x * str[a];
+        cc[a] = std::min(x / P.cs[a], P.nc[a] - 1);
+      }
+      const int64_t u = o.unknown[pn];
+      MSS_REQUIRE(u >= 0, MSS_ERR_INVALID_ARG, "lift node on a Dirichlet wall");
+      const int32_t *lst;
+      MSS_REQUIRE(P.faces_of(u, &lst) == 0, MSS_ERR_INVALID_ARG,
+                  "lift node on a face (skeleton or I/O node): it is read from the face state");
+      int c = 0;
+      for (int a = 0; a < o.g.dim; ++a) c = c * P.nc[a] + cc[a];
+      P.build_cell(c);
+      const Cell &C = P.cells[c];
+      const int64_t prime = P.plain_prime[u];
+      const auto it = std::find(C.nodes.begin(), C.nodes.end(), prime);
+      MSS_REQUIRE(it != C.nodes.end() && (int64_t)(it - C.nodes.begin()) >= C.K, MSS_ERR_INVALID_ARG,
+                  "lift node is not inside its cell");
+      lu.push_back(u);
+      lc.push_back(c);
+      ll.push_back((int64_t)(it - C.nodes.begin()));
+    }
+    P.lift_unknown.swap(lu);
+    P.lift_cell.swap(lc);
+    P.lift_local.swap(ll);
+  });
+}
+
 mss_status mss_rom_set_io(mss_rom *r, int32_t n_src, int32_t n_src_entries, const int32_t *src_face,
                           const int32_t *src_index, const double *src_vals, int32_t n_rcv, int32_t n_rcv_entries,
                           const int32_t *rcv_face, const int32_t *rcv_index, const double *rcv_vals) {
@@ -270,6 +312,10 @@ mss_status mss_rom_set_io(mss_rom *r, int32_t n_src, int32_t n_src_entries, cons
       rv.insert(rv.end(), rcv_vals + o, rcv_vals + o + R.face_M[rcv_face[e]]);
       o += R.face_M[rcv_face[e]];
     }
+    R.rcv_h_index.clear();
+    R.rcv_h_cell.clear();
+    R.rcv_h_layer.clear();
+    R.rcv_h_vals.clear();
     R.n_src = n_src;
     R.n_rcv = n_rcv;
     R.src_face.swap(sf);
@@ -296,8 +342,10 @@ mss_status mss_rom_set_io_nodes(mss_rom *r, const mss_partition *p, int32_t n_sr
     str[o.g.dim - 1] = 1;
     for (int a = o.g.dim - 2; a >= 0; --a) str[a] = str[a + 1] * ext[a + 1];
     // entries: for each I/O point and each of its prime copies, S_f^T e_row * weight
+    std::vector<int32_t> hi, hc, hl;
+    std::vector<double> hv;
     auto project = [&](int32_t n, const int32_t *nodes, const double *w, std::vector<int32_t> &fo,
-                       std::vector<int32_t> &io, std::vector<double> &vo) {
+                       std::vector<int32_t> &io, std::vector<double> &vo, bool lift) {
       for (int32_t j = 0; j < n; ++j) {
         int64_t pn = 0;
         for (int a = 0; a < o.g.dim; ++a) {
@@ -309,6 +357,31 @@ mss_status mss_rom_set_io_nodes(mss_rom *r, const mss_partition *p, int32_t n_sr
         MSS_REQUIRE(u >= 0, MSS_ERR_INVALID_ARG, "I/O node on a Dirichlet wall");
         const int32_t *lst;
         const int nf = P.faces_of(u, &lst);
+        if (nf == 0 && lift) {
+          // receiver inside a cell: its Galerkin lift, layer 1 as face entries, layers 2..m hidden
+          const auto it = std::find(R.lift_unknown.begin(), R.lift_unknown.end(), u);
+          MSS_REQUIRE(it != R.lift_unknown.end(), MSS_ERR_INVALID_ARG,
+                      "receiver inside a cell is neither an I/O node nor a lift node of the build");
+          const int l = (int)(it - R.lift_unknown.begin()), c = R.lift_cell[l];
+          const int K = R.cell_K[c], m = R.cell_m[c];
+          const double *wl = R.lift_w.data() + R.lift_off[l];
+          const double ww = w ? w[j] : 1.0;
+          int o = 0;
+          for (int k = R.cell_face_ptr[c]; k < R.cell_face_ptr[c + 1]; ++k) {
+            const int f = R.cell_faces[k], M = R.face_M[f];
+            fo.push_back(f);
+            io.push_back(j);
+            for (int q = 0; q < M; ++q) vo.push_back(wl[o + q] * ww);
+            o += M;
+          }
+          for (int k = 2; k <= m; ++k) {
+            hi.push_back(j);
+            hc.push_back(c);
+            hl.push_back(k);
+            for (int q = 0; q < K; ++q) hv.push_back(wl[(int64_t)(k - 1) * K + q] * ww);
+          }
+          continue;
+        }
         MSS_REQUIRE(nf >= 1, MSS_ERR_INVALID_ARG,
                     "I/O node inside a cell was not given to mss_partition_create");
         std::vector<double> wt(nf, 1.0);
@@ -333,8 +406,12 @@ mss_status mss_rom_set_io_nodes(mss_rom *r, const mss_partition *p, int32_t n_sr
     };
     std::vector<int32_t> sf, si, rf, ri;
     std::vector<double> sv, rv;
-    project(n_src, src_nodes, src_w, sf, si, sv);
-    project(n_rcv, rcv_nodes, rcv_w, rf, ri, rv);
+    project(n_src, src_nodes, src_w, sf, si, sv, false);
+    project(n_rcv, rcv_nodes, rcv_w, rf, ri, rv, true);
+    R.rcv_h_index.swap(hi);
+    R.rcv_h_cell.swap(hc);
+    R.rcv_h_layer.swap(hl);
+    R.rcv_h_vals.swap(hv);
     R.n_src = n_src;
     R.n_rcv = n_rcv;
     R.src_face.swap(sf);

@@ -80,7 +80,13 @@ def case(P):
     LR = P.Rom.import_(R.topology, R.coeffs)
     LR.set_io(len(wl.src_nodes), _entries(gt, "src"), len(wl.rcv_nodes), _entries(qt, "rcv"))
     LR.set_corners(cr)
-    return dict(LR=LR, ref=ref, w=w, tau=tau, nst=nst, n_src=len(wl.src_nodes), n_rcv=len(wl.rcv_nodes))
+    # the same coefficients with 16 random sources (16-source tiles: the streamed kernels run)
+    src16, rcv16 = synth.random_io(R.topology, 16, 8, seed=48)
+    LR16 = P.Rom.import_(R.topology, R.coeffs)
+    LR16.set_io(16, src16, 8, rcv16)
+    LR16.set_corners(cr)
+    return dict(LR=LR, ref=ref, w=w, tau=tau, nst=nst, n_src=len(wl.src_nodes), n_rcv=len(wl.rcv_nodes),
+                wide=dict(LR=LR16, w=w, tau=tau, nst=500, n_src=16, n_rcv=8))
 
 
 def _run(P, c, prec, factor_last=False, sched=None):
@@ -118,9 +124,25 @@ def test_fp32_factored_last_parity_at_k270(P, case):
 
 
 def test_factored_schedules_bit_identical(P, case):
+    """Plain cell kernel (graph), persistent kernel, and the TMA-streamed wide kernel (rows of the
+    factored coefficient met in descending order) give the same bits."""
     a = _run(P, case, P.FP32, factor_last=True, sched=P.SCHED_GRAPH)
     b = _run(P, case, P.FP32, factor_last=True, sched=P.SCHED_PERSIST)
     assert np.array_equal(a, b)
+    c16 = case["wide"]
+    outs = [_run(P, c16, P.FP32, factor_last=True, sched=k)
+            for k in (P.SCHED_GRAPH, P.SCHED_PERSIST, P.SCHED_GRAPH_STREAM)]
+    assert np.linalg.norm(outs[0]) > 0
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+
+
+def test_wide_streamed_kernel_bit_identical_unfactored(P, case):
+    c16 = case["wide"]
+    a = _run(P, c16, P.FP32, sched=P.SCHED_GRAPH)
+    c = _run(P, c16, P.FP32, sched=P.SCHED_GRAPH_STREAM)
+    assert np.linalg.norm(a) > 0
+    assert np.array_equal(a, c)
 
 
 @pytest.mark.parametrize("n_src", [3, 16, 21])
@@ -140,12 +162,23 @@ def test_factored_last_random_ragged(P, n_src):
     R = P.Rom.import_(topo, co)
     R.set_io(n_src, src, 4, rcv)
     sim = P.Sim(R, P.FP32, tau, factor_last=True)
-    assert [s for s in range(P.SCHED_COUNT) if sim.schedule()[1][s]] == [P.SCHED_GRAPH, P.SCHED_PERSIST]
+    avail = [s for s in range(P.SCHED_COUNT) if sim.schedule()[1][s]]
+    # the streamed (wide) kernel needs 16-source tiles: available from 16 sources on
+    assert avail == ([P.SCHED_GRAPH, P.SCHED_PERSIST] if n_src < 16 else
+                     [P.SCHED_GRAPH, P.SCHED_GRAPH_STREAM, P.SCHED_PERSIST])
     wd = torch.tensor(w, device="cuda")
-    tr = torch.zeros((nst, 4, n_src), device="cuda", dtype=torch.float32)
-    sim.step(nst, wd, tr)
-    torch.cuda.synchronize()
-    out = tr.cpu().numpy().astype(np.float64)
+    outs = []
+    for sched in avail:
+        sim.set_schedule(sched)
+        sim.reset()
+        tr = torch.zeros((nst, 4, n_src), device="cuda", dtype=torch.float32)
+        sim.step(nst, wd, tr)
+        torch.cuda.synchronize()
+        sim.info()
+        outs.append(tr.cpu().numpy().astype(np.float64))
+    out = outs[0]
+    for o in outs[1:]:
+        assert np.array_equal(o, out)
     # plain FP32 reaches about 2e-5 on random coefficient sets; the factored path stays there
     assert np.linalg.norm(out - ref) <= 1e-4 * np.linalg.norm(ref)
     with pytest.raises(P.MssError):
