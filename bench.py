@@ -756,11 +756,13 @@ def run_accuracy(args):
     modes = [int(x) for x in args.acc_modes.split(",")]
     wl = synth.workload_3d_layers(args.acc_n, 16, m=args.acc_m, n_modes=modes[0], n_src=args.acc_src,
                                   n_steps=args.acc_steps, band=args.acc_band)
+    if args.acc_src_centre:          # sources at the cell centres of their line (8 voxels from the faces)
+        wl.src_nodes = np.array([[args.acc_n, wl.src_nodes[0][1], 8 + 16 * j] for j in range(args.acc_n // 16)])
     L = P.Operator(wl.grid, wl.sigma, wl.rho)
     LP = P.Partition(L, wl.cell, np.concatenate([wl.src_nodes, wl.rcv_nodes]).astype(np.int32))
     lam = L.lambda_max(1e-7)
     tau = wl.cfl_fraction * 2.0 / math.sqrt(lam)
-    s = -(2 * math.pi * wl.f_max) ** 2
+    s = -args.acc_shift * (2 * math.pi * wl.f_max) ** 2
     nst, S, R = wl.n_steps, len(wl.src_nodes), len(wl.rcv_nodes)
     wd = torch.tensor(synth.ricker(np.arange(nst) * tau, wl.f_peak), device=dev)
 
@@ -800,11 +802,12 @@ def run_accuracy(args):
         LR.set_io_nodes(LP, wl.src_nodes, wl.rcv_nodes)
         cm, cfp, cf, fM, _, _, _, _ = LR.export()
         Ks = [int(sum(fM[cf[cfp[c]:cfp[c + 1]]])) for c in range(len(cm))]
-        r32, t32 = run(P.Sim(LR, P.FP32, tau, corner_correction=True), torch.float32, 3)
-        simf = P.Sim(LR, P.FP32, tau, corner_correction=True, factor_last=True)
+        cc = not args.acc_no_corners
+        r32, t32 = run(P.Sim(LR, P.FP32, tau, corner_correction=cc), torch.float32, 3)
+        simf = P.Sim(LR, P.FP32, tau, corner_correction=cc, factor_last=True)
         fsched, _ = simf.autotune(100)
         rf, tf = run(simf, torch.float32, 3)
-        r64, t64 = run(P.Sim(LR, P.FP64, tau, corner_correction=True), torch.float64, 1)
+        r64, t64 = run(P.Sim(LR, P.FP64, tau, corner_correction=cc), torch.float64, 1)
         rows.append({"face_modes": nm, "K_max": max(Ks), "offline_s": t_build,
                      "rel_l2_rom_fp64_vs_fine_fp64": rel(r64, ref), "rel_l2_rom_fp32_vs_fine_fp64": rel(r32, ref),
                      "rel_l2_rom_fp32_factored_vs_fine_fp64": rel(rf, ref),
@@ -855,6 +858,9 @@ def main():
     ap.add_argument("--acc-modes", default="15,28,45", help="face-mode counts of --accuracy")
     ap.add_argument("--acc-steps", type=int, default=3000)
     ap.add_argument("--acc-src", type=int, default=8, help="sources of --accuracy")
+    ap.add_argument("--acc-no-corners", action="store_true", help="--accuracy without the Appendix D correction")
+    ap.add_argument("--acc-src-centre", action="store_true", help="--accuracy with sources at cell centres")
+    ap.add_argument("--acc-shift", type=float, default=1.0, help="--accuracy shift as a multiple of -omega_max^2")
     ap.add_argument("--acc-m", type=int, default=4, help="S-fraction layers of --accuracy")
     ap.add_argument("--acc-band", default="cell", choices=["cell", "nyquist"],
                     help="band of --accuracy: one minimum wavelength per cell, or peak at 1/10 grid Nyquist")

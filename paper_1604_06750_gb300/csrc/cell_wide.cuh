@@ -1,15 +1,17 @@
-// Wide streamed cell kernel: the cell phase for large boundary dimensions (K_i up to 512), FP32 on
+// Wide streamed cell kernel: the cell phase for large boundary dimensions (K_i up to 384), FP32 on
 // the CUDA cores, 16-source tiles, the coefficient stream staged by TMA.
 //
 // At the paper's operating point (cells about one wavelength across, K~ = 180-294, Section 7) a
 // cell's 2m-1 coefficient matrices hold about 2 MB per step, more than the L2 share of the CTAs
 // resident at once, so the stream is moved by the copy engine, not by thread loads: one thread
 // issues 1-D bulk copies (cp.async.bulk) of whole stored rows into a ring of four 16 KB
-// shared-memory slots, each guarded by an mbarrier with a transaction count, and 512 threads
-// consume them.  Thread (g, r0): g = tid / 256 picks 8 of the 16 sources, r0 = tid % 256 picks the
-// output rows r0 and r0 + 256.  Row j of a stored symmetric matrix is also its column j, so
-//   acc[i][e] += G[j][r0 + 256 i] * D[j][8 g + e]
-// reads the slot without bank conflicts and D as a broadcast.
+// shared-memory slots, each guarded by an mbarrier with a transaction count, and 384 threads
+// consume them.  Thread (g, q): g = tid / 96 picks 4 of the 16 sources, q = tid % 96 the four
+// consecutive output rows 4q .. 4q+3.  Row j of a stored symmetric matrix is also its column j, so
+//   acc[i][e] += G[j][4q + i] * D[j][4g + e]
+// takes one 16-byte load of the slot and one broadcast 16-byte load of D per row j for 16 fused
+// multiply-adds (8 paired instructions): the kernel is bound by instruction issue, and this
+// register blocking halves the instructions per multiply-add against one row per thread.
 //
 // Factored last coefficient (Gamma^m = L L^T, the stored matrix W = L + L^T - diag(L) with its rows
 // in descending order): F^m = L (L^T D^m) in one pass over the stream.  Rows j arrive from K-1 down
@@ -25,10 +27,11 @@
 
 namespace mss {
 
-constexpr int kWideThreads = 512;
-constexpr int kWideSlots = 256;     // row slots: a thread owns rows r0 and r0 + kWideSlots
-constexpr int kWideRows = 2;        // rows per thread, so K_i <= kWideSlots * kWideRows
-constexpr int kWideCP = 8;          // sources per thread (two 8-source groups per 16-source tile)
+constexpr int kWideThreads = 384;
+constexpr int kWideQuads = 96;      // row quads per source group: K_i <= 4 kWideQuads
+constexpr int kWideRows = 4;        // consecutive rows per thread
+constexpr int kWideCP = 4;          // sources per thread (four 4-source groups per 16-source tile)
+constexpr int kWideMaxK = 4 * kWideQuads;
 
 // Shared memory of the wide kernel: ring and its barriers, U/F (X) and D/E (D) as m K 16 floats
 // each, the factored product's y (K 16 floats), the K boundary-row indices.
@@ -38,11 +41,9 @@ inline size_t wide_smem_bytes(int max_m, int max_K, int factor_last) {
          8 * (size_t)max_K;
 }
 
-__device__ __forceinline__ void fma8(float (&acc)[kWideCP], float gv, const float4 d0, const float4 d1) {
-  fma2(acc[0], acc[1], gv, d0.x, d0.y);
-  fma2(acc[2], acc[3], gv, d0.z, d0.w);
-  fma2(acc[4], acc[5], gv, d1.x, d1.y);
-  fma2(acc[6], acc[7], gv, d1.z, d1.w);
+__device__ __forceinline__ void fma4(float (&acc)[kWideCP], float gv, const float4 d) {
+  fma2(acc[0], acc[1], gv, d.x, d.y);
+  fma2(acc[2], acc[3], gv, d.z, d.w);
 }
 
 // One (cell, 16-source tile) of the cell phase.  gc: chunks this CTA has consumed so far; returns
@@ -111,12 +112,13 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
     D[i] = (k + 1 < m ? X[i + (size_t)K * ST] : 0.f) - X[i];
   }
   __syncthreads();
-  const int r0 = tid & (kWideSlots - 1), g = tid / kWideSlots;
+  const int g = tid / kWideQuads, r4 = 4 * (tid - g * kWideQuads);
+  const bool actq = r4 < K;                      // rows r4 .. r4+3 (those >= K read zero padding)
   int rr[kWideRows];
   bool act[kWideRows];
 #pragma unroll
   for (int i = 0; i < kWideRows; ++i) {
-    rr[i] = r0 + i * kWideSlots;
+    rr[i] = r4 + i;
     act[i] = rr[i] < K;
   }
   const float tau2 = a.tau2;
@@ -176,44 +178,47 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
       const float *sp = reinterpret_cast<const float *>(ring + (size_t)((gc0 + c) % kStreamSlots) * kStreamChunk) +
                         (size_t)(fr - c * CR) * Kq;
       if (!tri) {
-        // acc[i] += G[j][r_i] D^layer_j, j = j0 .. j1-1 ascending
+        // acc[i] += G[j][r4 + i] D^layer_j, j = j0 .. j1-1 ascending
+        if (actq) {
 #pragma unroll 2
-        for (int h = 0; h < n; ++h) {
-          const float4 *dp = reinterpret_cast<const float4 *>(Dl + (size_t)(j0 + h) * ST);
-          const float4 d0 = dp[0], d1 = dp[1];
-#pragma unroll
-          for (int i = 0; i < kWideRows; ++i)
-            if (act[i]) fma8(acc[i], sp[(size_t)h * Kq + rr[i]], d0, d1);
+          for (int h = 0; h < n; ++h) {
+            const float4 d = *reinterpret_cast<const float4 *>(Dl + (size_t)(j0 + h) * ST);
+            const float4 gq = *reinterpret_cast<const float4 *>(sp + (size_t)h * Kq + r4);
+            fma4(acc[0], gq.x, d);
+            fma4(acc[1], gq.y, d);
+            fma4(acc[2], gq.z, d);
+            fma4(acc[3], gq.w, d);
+          }
         }
       } else {
         // stored position p holds row K-1-p: the segment covers rows jt = K-1-j0 down to jb
         const int jt = K - 1 - j0, jb = K - j1;
 #pragma unroll 2
-        for (int h = 0; h < n; ++h) {
+        for (int h = 0; h < n && actq; ++h) {
           const int j = jt - h;
-          const float4 *dp = reinterpret_cast<const float4 *>(Dl + (size_t)j * ST);
-          const float4 d0 = dp[0], d1 = dp[1];
+          const float4 d = *reinterpret_cast<const float4 *>(Dl + (size_t)j * ST);
+          const float4 gq = *reinterpret_cast<const float4 *>(sp + (size_t)h * Kq + r4);
+          const float gv[4] = {gq.x, gq.y, gq.z, gq.w};
 #pragma unroll
           for (int i = 0; i < kWideRows; ++i)
-            if (act[i] && rr[i] <= j) fma8(yv[i], sp[(size_t)h * Kq + rr[i]], d0, d1);
+            if (rr[i] <= j) fma4(yv[i], gv[i], d);
         }
         // the y of this segment's rows are complete: share them
 #pragma unroll
         for (int i = 0; i < kWideRows; ++i)
-          if (act[i] && rr[i] >= jb && rr[i] <= jt) {
-            float4 *o = reinterpret_cast<float4 *>(Ys + (size_t)rr[i] * ST + CP * g);
-            o[0] = make_float4(yv[i][0], yv[i][1], yv[i][2], yv[i][3]);
-            o[1] = make_float4(yv[i][4], yv[i][5], yv[i][6], yv[i][7]);
-          }
+          if (act[i] && rr[i] >= jb && rr[i] <= jt)
+            *reinterpret_cast<float4 *>(Ys + (size_t)rr[i] * ST + CP * g) =
+                make_float4(yv[i][0], yv[i][1], yv[i][2], yv[i][3]);
         __syncthreads();
 #pragma unroll 2
-        for (int h = 0; h < n; ++h) {
+        for (int h = 0; h < n && actq; ++h) {
           const int j = jt - h;
-          const float4 *yp = reinterpret_cast<const float4 *>(Ys + (size_t)j * ST + CP * g);
-          const float4 y0 = yp[0], y1 = yp[1];
+          const float4 y = *reinterpret_cast<const float4 *>(Ys + (size_t)j * ST + CP * g);
+          const float4 gq = *reinterpret_cast<const float4 *>(sp + (size_t)h * Kq + r4);
+          const float gv[4] = {gq.x, gq.y, gq.z, gq.w};
 #pragma unroll
           for (int i = 0; i < kWideRows; ++i)
-            if (act[i] && rr[i] >= j) fma8(acc[i], sp[(size_t)h * Kq + rr[i]], y0, y1);
+            if (rr[i] >= j) fma4(acc[i], gv[i], y);
         }
       }
       j0 = j1;
@@ -224,9 +229,8 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
       if (!act[i]) continue;
       const int r = rr[i];
       if (q < m) {
-        float4 *o = reinterpret_cast<float4 *>(X + ((size_t)q * K + r) * ST + CP * g);
-        o[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        o[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+        *reinterpret_cast<float4 *>(X + ((size_t)q * K + r) * ST + CP * g) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
       } else {
         const int k = q - m + 1;
         const int64_t base = (so + (int64_t)(k - 1) * K + r) * S + s0 + CP * g;

@@ -1360,7 +1360,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
                         8 * (size_t)s.max_K;
     const bool narrow = !s.factor_last && s.max_K <= 128 && need <= (size_t)dev_smem;
     const size_t wneed = wide_smem_bytes(s.max_m, s.max_K, s.factor_last);
-    const bool wide = s.max_K <= kWideSlots * kWideRows && wneed <= (size_t)dev_smem;
+    const bool wide = s.max_K <= kWideMaxK && wneed <= (size_t)dev_smem;
     if (narrow || wide) {
       std::vector<float> blob;
       std::vector<int64_t> soff(R.n_cells);
