@@ -285,9 +285,6 @@ def _kernel_model(rom_info, topo_K, topo_m, n_src, es):
 
 
 SCHED_NAMES = ["graph", "graph_stream", "persistent", "persistent_stream", "graph_split"]
-CELL_KERNEL = {0: ("k_cell<float,16>", ["online.cu"]), 1: ("k_cell_s", ["cell_stream.cuh", "online.cu"]),
-               4: ("k_flux+k_accel", ["cell_split.cuh", "online.cu"])}
-
 
 def _traffic_record(kernel: str, sources):
     """ncu DRAM bytes per launch of a cell kernel, if recorded for these exact kernel sources."""
@@ -410,12 +407,23 @@ def run_native(args):
     sim.info()                                              # raises if a bounded device wait gave up
     tr32 = tr.double().cpu().numpy()
     # ---- per-kernel timing (eager, CUDA events on the launching stream): the cell kernel of the
-    # graph schedule (the persistent schedule runs the same cell body inside one kernel)
-    sim.set_schedule(P.SCHED_GRAPH)
+    # chosen schedule (the persistent schedule runs the plain cell body inside one kernel, so the
+    # graph schedule stands in for it)
+    prof_sched = {P.SCHED_PERSIST: P.SCHED_GRAPH, P.SCHED_PERSIST_STREAM: P.SCHED_GRAPH_STREAM}.get(sched, sched)
+    sim.set_schedule(prof_sched)
     sim.reset()
     ms = sim.step_profile(200, wd, tr)
     sim.set_schedule(sched)
-    kname = "k_cell<float,16> (factored last coefficient)" if factor else "k_cell<float,16>"
+    wide = max(Ks) > 128 or factor
+    if prof_sched == P.SCHED_GRAPH_STREAM:
+        kname = "k_cell_w (wide TMA-streamed)" if wide else "k_cell_s"
+    elif prof_sched == P.SCHED_GRAPH_SPLIT:
+        kname = "k_flux+k_accel"
+    else:
+        kname = "k_cell<float,16> (factored last coefficient)" if factor else "k_cell<float,16>"
+    ksrc = {"k_cell_w (wide TMA-streamed)": ["cell_wide.cuh", "cell_stream.cuh", "online.cu"],
+            "k_cell_s": ["cell_stream.cuh", "online.cu"], "k_flux+k_accel": ["cell_split.cuh", "online.cu"]}.get(
+        kname, ["online.cu"])
     algo_bytes, algo_flops = _kernel_model(None, Ks, cm, S, 4)
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -430,7 +438,7 @@ def run_native(args):
     achieved_tf = algo_flops / cell_s / 1e12
     ridge = alu_peak * 1e12 / (hbm * 1e9)
     intensity = algo_flops / algo_bytes
-    traffic = _traffic_record(kname, CELL_KERNEL[0][1])
+    traffic = _traffic_record(kname, ksrc)
     if intensity < ridge:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
                 "traffic": traffic}
@@ -493,7 +501,8 @@ def run_native(args):
         if dist:
             dist.destroy_process_group()
         return
-    launches = {0: nst * kper}.get(sched, -(-nst // 512))
+    launches = {P.SCHED_GRAPH: nst * kper, P.SCHED_GRAPH_STREAM: nst * kper,
+                P.SCHED_GRAPH_SPLIT: nst * (kper + 1)}.get(sched, -(-nst // 512))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

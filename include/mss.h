@@ -350,7 +350,8 @@ mss_status mss_sim_clear_error(mss_sim *s, void *stream);
 /* Tile of the step kernels (values <= 0 leave a field unchanged): CUDA-core source tile (a power
  * of two up to the one chosen at creation; 16 is needed by the streamed schedules, the schedule
  * falls back to GRAPH otherwise), sources per CTA of the split tensor-core kernels (16, 32, 64,
- * 128), thread groups of the streamed FP32 kernel (2 or 4).  Errors: INVALID_ARG. */
+ * 128), thread groups of the streamed FP32 kernel (2 or 4; for the wide streamed kernel of
+ * K_i > 128 or the factored last coefficient, its row-loop unroll depth).  Errors: INVALID_ARG. */
 mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources, int32_t groups);
 /* sched: current schedule; available (may be NULL): [MSS_SCHED_COUNT] 1 where usable; tile (may
  * be NULL): [3] = CUDA-core source tile, sources per CTA of the split tensor-core kernels (0 for

@@ -6,7 +6,7 @@
 // resident at once, so the stream is moved by the copy engine, not by thread loads: one thread
 // issues 1-D bulk copies (cp.async.bulk) of whole stored rows into a ring of four 16 KB
 // shared-memory slots, each guarded by an mbarrier with a transaction count, and 384 threads
-// consume them.  Thread (g, q): g = tid / 96 picks 4 of the 16 sources, q = tid % 96 the four
+// consume them.  Thread (q, g): g = tid % 4 picks 4 of the 16 sources, q = tid / 4 the four
 // consecutive output rows 4q .. 4q+3.  Row j of a stored symmetric matrix is also its column j, so
 //   acc[i][e] += G[j][4q + i] * D[j][4g + e]
 // takes one 16-byte load of the slot and one broadcast 16-byte load of D per row j for 16 fused
@@ -47,7 +47,9 @@ __device__ __forceinline__ void fma4(float (&acc)[kWideCP], float gv, const floa
 }
 
 // One (cell, 16-source tile) of the cell phase.  gc: chunks this CTA has consumed so far; returns
-// false if a wait timed out (error recorded, copies drained).
+// false if a wait timed out (error recorded, copies drained).  U: unroll depth of the row loops
+// (the autotuner picks 2 or 4; the arithmetic does not depend on it).
+template <int U>
 __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, const int cur, const int cell,
                                const int tile, unsigned char *smem, unsigned &gc) {
   constexpr int ST = kStreamST, CP = kWideCP;
@@ -112,7 +114,10 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
     D[i] = (k + 1 < m ? X[i + (size_t)K * ST] : 0.f) - X[i];
   }
   __syncthreads();
-  const int g = tid / kWideQuads, r4 = 4 * (tid - g * kWideQuads);
+  // consecutive threads share a row quad (one broadcast 16-byte coefficient load) and take its four
+  // 4-source groups; the quads of a small K are then packed into the first warps, and the warps
+  // beyond 4 K threads have no rows at all (no partially filled warps)
+  const int g = tid & 3, r4 = 4 * (tid >> 2);
   const bool actq = r4 < K;                      // rows r4 .. r4+3 (those >= K read zero padding)
   int rr[kWideRows];
   bool act[kWideRows];
@@ -180,7 +185,7 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
       if (!tri) {
         // acc[i] += G[j][r4 + i] D^layer_j, j = j0 .. j1-1 ascending
         if (actq) {
-#pragma unroll 2
+#pragma unroll U
           for (int h = 0; h < n; ++h) {
             const float4 d = *reinterpret_cast<const float4 *>(Dl + (size_t)(j0 + h) * ST);
             const float4 gq = *reinterpret_cast<const float4 *>(sp + (size_t)h * Kq + r4);
@@ -193,7 +198,7 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
       } else {
         // stored position p holds row K-1-p: the segment covers rows jt = K-1-j0 down to jb
         const int jt = K - 1 - j0, jb = K - j1;
-#pragma unroll 2
+#pragma unroll U
         for (int h = 0; h < n && actq; ++h) {
           const int j = jt - h;
           const float4 d = *reinterpret_cast<const float4 *>(Dl + (size_t)j * ST);
@@ -210,7 +215,7 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
             *reinterpret_cast<float4 *>(Ys + (size_t)rr[i] * ST + CP * g) =
                 make_float4(yv[i][0], yv[i][1], yv[i][2], yv[i][3]);
         __syncthreads();
-#pragma unroll 2
+#pragma unroll U
         for (int h = 0; h < n && actq; ++h) {
           const int j = jt - h;
           const float4 y = *reinterpret_cast<const float4 *>(Ys + (size_t)j * ST + CP * g);
@@ -265,13 +270,14 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   return true;
 }
 
+template <int U>
 __global__ void __launch_bounds__(kWideThreads, 1) k_cell_w(const StepArgs<float> a, const StreamArgs t, const int cur) {
   extern __shared__ __align__(128) unsigned char smem_w[];
   if (*(volatile const int *)t.err) return;
   stream_init(smem_w);
   unsigned gc = 0;
   const int tiles = (a.S + kStreamST - 1) / kStreamST;   // 1-D grid, tiles of a cell adjacent
-  cell_wide_item(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_w, gc);
+  cell_wide_item<U>(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_w, gc);
 }
 
 }  // namespace mss

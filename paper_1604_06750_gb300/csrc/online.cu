@@ -743,8 +743,10 @@ static void set_smem_attrs(const mss_sim &s) {
   MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
   if (s.factor_last)
     MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
-  if (s.wide_ok)
-    MSS_CUDA(cudaFuncSetAttribute(k_cell_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.wide_smem));
+  if (s.wide_ok) {
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_w<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.wide_smem));
+    MSS_CUDA(cudaFuncSetAttribute(k_cell_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.wide_smem));
+  }
   if (s.stream_ok)
   {
     MSS_CUDA(cudaFuncSetAttribute(k_cell_s<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.stream_smem));
@@ -787,7 +789,8 @@ static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStr
   const dim3 gc(s.n_cells * s.tiles);
   if constexpr (std::is_same<T, float>::value && ST == kStreamST) {
     if (s.sched == MSS_SCHED_GRAPH_STREAM) {
-      if (!s.stream_ok) k_cell_w<<<gc, kWideThreads, s.wide_smem, st>>>(a, s.sca, cur);
+      if (!s.stream_ok && s.stream_groups == 4) k_cell_w<4><<<gc, kWideThreads, s.wide_smem, st>>>(a, s.sca, cur);
+      else if (!s.stream_ok) k_cell_w<2><<<gc, kWideThreads, s.wide_smem, st>>>(a, s.sca, cur);
       else if (s.stream_groups == 4) k_cell_s<4><<<gc, 512, s.stream_smem, st>>>(a, s.sca, cur);
       else k_cell_s<2><<<gc, 256, s.stream_smem, st>>>(a, s.sca, cur);
       return;
