@@ -49,10 +49,10 @@ import synth  # noqa: E402
 # The headline workload: the 128^3 layered medium at the operating point of the paper's
 # experiments (Section 7: cells about one minimum wavelength across, m = 4, K~ = 180-294), where
 # the ROM reaches the 1e-3 receiver level against the fine grid.
-WORKLOAD = dict(n=128, cell=16, m=4, n_modes=45, n_src=16, n_steps=4000, band="cell")
+WORKLOAD = dict(n=128, cell=16, m=4, n_modes=45, n_src=16, n_steps=4000, band="cell", cellwl=1.0)
 # The learned-surrogate mode keeps the 1/10-Nyquist band and 15 modes (its network predicts a
 # (2m-1) Kp (Kp+1)/2 vector per cell, which stays small only at few modes).
-SURROGATE_WORKLOAD = dict(n=128, cell=16, m=4, n_modes=15, n_src=16, n_steps=4000, band="nyquist")
+SURROGATE_WORKLOAD = dict(n=128, cell=16, m=4, n_modes=15, n_src=16, n_steps=4000, band="nyquist", cellwl=1.0)
 METRIC = "online ROM source·cell-steps/s vs fine-grid stencil at ≤1e-3 receiver error"
 UNIT = "source·cell-steps/s"
 ACCURACY_TARGET = 1e-3
@@ -62,19 +62,22 @@ def _workload(spec=None, **over):
     p = dict(WORKLOAD if spec is None else spec)
     p.update({k: v for k, v in over.items() if v is not None})
     wl = synth.workload_3d_layers(p["n"], p["cell"], m=p["m"], n_modes=p["n_modes"], n_src=p["n_src"],
-                                  n_steps=p["n_steps"], band=p["band"])
+                                  n_steps=p["n_steps"], band=p["band"], cell_wavelengths=p["cellwl"])
     wl.band = p["band"]
+    wl.cellwl = p["cellwl"]
     return wl
 
 
 def _config(wl, extra=None):
     nc = int(np.prod([wl.grid.n[a] // wl.cell[a] for a in range(3)]))
-    band = {"cell": "one minimum wavelength per cell", "nyquist": "Ricker peak at 1/10 grid Nyquist"}[wl.band]
+    band = {"cell": "%g minimum wavelengths per cell" % wl.cellwl,
+            "nyquist": "Ricker peak at 1/10 grid Nyquist"}[wl.band]
     c = {"workload": "3d_layers_%d: %d^3 voxels, %d cells of 16^3, band %s, m=%d, %d modes/face, %d sources, "
                      "%d receivers, %d steps" % (wl.grid.n[0], wl.grid.n[0], nc, band, wl.m, wl.n_modes,
                                                   len(wl.src_nodes), len(wl.rcv_nodes), wl.n_steps),
          "cells": nc, "sources": int(len(wl.src_nodes)), "receivers": int(len(wl.rcv_nodes)),
-         "time_steps": int(wl.n_steps), "layers": wl.m, "face_modes": wl.n_modes, "band": wl.band}
+         "time_steps": int(wl.n_steps), "layers": wl.m, "face_modes": wl.n_modes, "band": wl.band,
+         "cell_wavelengths": wl.cellwl if wl.band == "cell" else None}
     if extra:
         c.update(extra)
     return c
@@ -228,7 +231,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = _workload(band=args.band, n_modes=args.modes)
+    wl = _workload(band=args.band, n_modes=args.modes, cellwl=args.cellwl)
     n_src, n_rcv = len(wl.src_nodes), len(wl.rcv_nodes)
     nc = tuple(wl.grid.n[a] // wl.cell[a] for a in range(3))
     topo = synth.box_topology(nc, modes=wl.n_modes, m=wl.m, io_cells=_box_io(wl), seed=7)
@@ -351,7 +354,7 @@ def run_native(args):
     if dist:
         dist.barrier()
     P.lib()
-    wl = _workload(band=args.band, n_modes=args.modes)
+    wl = _workload(band=args.band, n_modes=args.modes, cellwl=args.cellwl)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     # ---- off-line (not timed in the metric)
@@ -764,7 +767,7 @@ def run_accuracy(args):
     stream = torch.cuda.current_stream(dev)
     modes = [int(x) for x in args.acc_modes.split(",")]
     wl = synth.workload_3d_layers(args.acc_n, 16, m=args.acc_m, n_modes=modes[0], n_src=args.acc_src,
-                                  n_steps=args.acc_steps, band=args.acc_band)
+                                  n_steps=args.acc_steps, band=args.acc_band, cell_wavelengths=args.acc_cellwl)
     if args.acc_src_centre:          # sources at the cell centres of their line (8 voxels from the faces)
         wl.src_nodes = np.array([[args.acc_n, wl.src_nodes[0][1], 8 + 16 * j] for j in range(args.acc_n // 16)])
     L = P.Operator(wl.grid, wl.sigma, wl.rho)
@@ -858,6 +861,8 @@ def main():
     ap.add_argument("--band", default=None, choices=["cell", "nyquist"],
                     help="band of the headline workload (default: one minimum wavelength per cell)")
     ap.add_argument("--modes", type=int, default=None, help="face modes of the headline workload (default 45)")
+    ap.add_argument("--cellwl", type=float, default=None,
+                    help="minimum wavelengths per cell of the headline workload's band (default 1)")
     ap.add_argument("--plain-fp32", action="store_true", help="headline FP32 without the factored last coefficient")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle's host timing")
     ap.add_argument("--ref-sample", type=int, default=10, help="time steps per bench step of --impl reference")
@@ -870,6 +875,7 @@ def main():
     ap.add_argument("--acc-no-corners", action="store_true", help="--accuracy without the Appendix D correction")
     ap.add_argument("--acc-src-centre", action="store_true", help="--accuracy with sources at cell centres")
     ap.add_argument("--acc-shift", type=float, default=1.0, help="--accuracy shift as a multiple of -omega_max^2")
+    ap.add_argument("--acc-cellwl", type=float, default=1.0, help="--accuracy: minimum wavelengths per cell (band cell)")
     ap.add_argument("--acc-m", type=int, default=4, help="S-fraction layers of --accuracy")
     ap.add_argument("--acc-band", default="cell", choices=["cell", "nyquist"],
                     help="band of --accuracy: one minimum wavelength per cell, or peak at 1/10 grid Nyquist")

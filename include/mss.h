@@ -338,8 +338,9 @@ mss_status mss_sim_check_stability(mss_sim *s, int32_t n_steps, uint64_t seed, d
  * which the kernel records MSS_ERR_TIMEOUT in the sim's error word and returns):
  *   MSS_DEBUG_GRID_EXTRA_ARRIVALS  the persistent CUDA-core kernel's grid barrier waits for
  *                                  `value` CTAs beyond the grid (a missing neighbour);
- *   MSS_DEBUG_TC_EXTRA_TX          the split tensor-core kernels' matrix barrier expects `value`
- *                                  bytes beyond their copies.
+ *   MSS_DEBUG_TC_EXTRA_TX          the split tensor-core kernels' matrix barrier, and the wide
+ *                                  streamed cell kernel's chunk barriers, expect `value` bytes
+ *                                  beyond their copies.
  * value 0 restores normal operation.  mss_sim_clear_error resets the error word (and the grid
  * barrier) after a reported TIMEOUT; the state of the failed steps is undefined (reset or load a
  * saved state).  Errors: INVALID_ARG, CUDA. */
@@ -350,12 +351,14 @@ mss_status mss_sim_clear_error(mss_sim *s, void *stream);
 /* Tile of the step kernels (values <= 0 leave a field unchanged): CUDA-core source tile (a power
  * of two up to the one chosen at creation; 16 is needed by the streamed schedules, the schedule
  * falls back to GRAPH otherwise), sources per CTA of the split tensor-core kernels (16, 32, 64,
- * 128), thread groups of the streamed FP32 kernel (2 or 4; for the wide streamed kernel of
- * K_i > 128 or the factored last coefficient, its row-loop unroll depth).  Errors: INVALID_ARG. */
+ * 128), thread groups of the streamed FP32 kernel (2 or 4; for a sim whose streamed schedule runs
+ * the wide kernel -- K_i > 128 or the factored last coefficient -- its variant 1..4: unroll depth
+ * 2 or 4 of the row loops, and 4 or 2 rows per thread, as 1 = (2, 4), 2 = (4, 4), 3 = (2, 2),
+ * 4 = (4, 2); every variant gives the same bits).  Errors: INVALID_ARG. */
 mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources, int32_t groups);
 /* sched: current schedule; available (may be NULL): [MSS_SCHED_COUNT] 1 where usable; tile (may
  * be NULL): [3] = CUDA-core source tile, sources per CTA of the split tensor-core kernels (0 for
- * CUDA-core precisions), thread groups of the streamed FP32 kernel. */
+ * CUDA-core precisions), thread groups of the streamed FP32 kernel (the wide kernel's variant). */
 mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *available, int32_t *tile);
 /* Time n_steps (rounded up to even) of every available schedule and tile variant (CUDA-core
  * source tile 16 or 8, split tensor-core N of 16..128, streamed-kernel block size) on zero

@@ -33,6 +33,8 @@ struct StreamArgs {
   const int32_t *Kq;
   int *err;                 // 1: an mbarrier wait timed out; 2: a grid barrier timed out
   int extra_arrivals;       // failure-path test hook: arrivals a grid barrier waits for beyond the grid
+  unsigned extra_tx;        // failure-path test hook: bytes the wide kernel's chunk barriers wait for
+                            // beyond their copies
 };
 
 // Wait for chunk c's slot; uniform over the CTA.  On failure the caller drains and returns.

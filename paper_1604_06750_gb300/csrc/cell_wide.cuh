@@ -5,13 +5,14 @@
 // cell's 2m-1 coefficient matrices hold about 2 MB per step, more than the L2 share of the CTAs
 // resident at once, so the stream is moved by the copy engine, not by thread loads: one thread
 // issues 1-D bulk copies (cp.async.bulk) of whole stored rows into a ring of four 16 KB
-// shared-memory slots, each guarded by an mbarrier with a transaction count, and 384 threads
-// consume them.  Thread (q, g): g = tid % 4 picks 4 of the 16 sources, q = tid / 4 the four
-// consecutive output rows 4q .. 4q+3.  Row j of a stored symmetric matrix is also its column j, so
-//   acc[i][e] += G[j][4q + i] * D[j][4g + e]
-// takes one 16-byte load of the slot and one broadcast 16-byte load of D per row j for 16 fused
-// multiply-adds (8 paired instructions): the kernel is bound by instruction issue, and this
-// register blocking halves the instructions per multiply-add against one row per thread.
+// shared-memory slots, each guarded by an mbarrier with a transaction count, and the threads
+// consume them.  Thread (q, g): g = tid % 4 picks 4 of the 16 sources, q = tid / 4 the R
+// consecutive output rows Rq .. Rq+R-1 (R = 4 or 2).  Row j of a stored symmetric matrix is also
+// its column j, so
+//   acc[i][e] += G[j][Rq + i] * D[j][4g + e]
+// takes one 16-byte (or 8-byte) load of the slot and one broadcast 16-byte load of D per row j for
+// 4R fused multiply-adds (2R paired instructions).  R = 4 halves the instructions per multiply-add
+// against one row per thread; R = 2 doubles the warps that hide the shared-memory latency.
 //
 // Factored last coefficient (Gamma^m = L L^T, the stored matrix W = L + L^T - diag(L) with its rows
 // in descending order): F^m = L (L^T D^m) in one pass over the stream.  Rows j arrive from K-1 down
@@ -21,17 +22,19 @@
 // this is the same sequence of fused multiply-adds as the plain cell kernel's descending
 // triangular passes, so both give identical bits.
 //
-// Every wait is bounded (globaltimer); on timeout the CTA records an error, waits (bounded) for
-// its own copies in flight and returns.
+// Chunks advance per warp: each warp waits on the next chunk's barrier itself, and the last warp
+// to release a chunk (a count in shared memory) refills its slot, so no block-wide barrier is taken
+// per chunk.  Every wait is bounded (globaltimer); on timeout the error is recorded, the warps keep
+// the block's control flow without waiting, and the CTA waits (bounded) for its copies in flight
+// before it returns.
 #pragma once
 
 namespace mss {
 
-constexpr int kWideThreads = 384;
-constexpr int kWideQuads = 96;      // row quads per source group: K_i <= 4 kWideQuads
-constexpr int kWideRows = 4;        // consecutive rows per thread
+constexpr int kWideMaxK = 384;     // largest K_i of the wide kernel
 constexpr int kWideCP = 4;          // sources per thread (four 4-source groups per 16-source tile)
-constexpr int kWideMaxK = 4 * kWideQuads;
+// threads of the wide kernel with R consecutive rows per thread: 4 source groups x K_max / R
+__host__ __device__ constexpr int wide_threads(int R) { return 4 * kWideMaxK / R; }
 
 // Shared memory of the wide kernel: ring and its barriers, U/F (X) and D/E (D) as m K 16 floats
 // each, the factored product's y (K 16 floats), the K boundary-row indices.
@@ -41,6 +44,18 @@ inline size_t wide_smem_bytes(int max_m, int max_K, int factor_last) {
          8 * (size_t)max_K;
 }
 
+// R consecutive floats of a slot row (16-byte or 8-byte aligned: Kq and r4 are multiples of R)
+template <int R>
+__device__ __forceinline__ void load_rows(float (&gv)[R], const float *p) {
+  if constexpr (R == 4) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    gv[0] = q.x; gv[1] = q.y; gv[2] = q.z; gv[3] = q.w;
+  } else {
+    const float2 q = *reinterpret_cast<const float2 *>(p);
+    gv[0] = q.x; gv[1] = q.y;
+  }
+}
+
 __device__ __forceinline__ void fma4(float (&acc)[kWideCP], float gv, const float4 d) {
   fma2(acc[0], acc[1], gv, d.x, d.y);
   fma2(acc[2], acc[3], gv, d.z, d.w);
@@ -48,8 +63,9 @@ __device__ __forceinline__ void fma4(float (&acc)[kWideCP], float gv, const floa
 
 // One (cell, 16-source tile) of the cell phase.  gc: chunks this CTA has consumed so far; returns
 // false if a wait timed out (error recorded, copies drained).  U: unroll depth of the row loops
-// (the autotuner picks 2 or 4; the arithmetic does not depend on it).
-template <int U>
+// (the autotuner picks 2 or 4); R: consecutive rows per thread (4, or 2 for twice the warps); the
+// arithmetic depends on neither.
+template <int U, int R>
 __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, const int cur, const int cell,
                                const int tile, unsigned char *smem, unsigned &gc) {
   constexpr int ST = kStreamST, CP = kWideCP;
@@ -61,6 +77,9 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   const bool fac = a.factor_last != 0;
   unsigned char *ring = smem;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStreamSlots * kStreamChunk);
+  // after the four barriers: per-slot release counts of the warps, and the chunks issued so far
+  unsigned *released = reinterpret_cast<unsigned *>(smem + kStreamSlots * kStreamChunk + 32);
+  unsigned *issued = released + kStreamSlots;
   float *X = reinterpret_cast<float *>(smem + kStreamSlots * kStreamChunk + 64);
   float *D = X + (size_t)m * K * ST;
   float *Ys = D + (size_t)m * K * ST;
@@ -80,11 +99,14 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
     const int r0 = c * CR, nr = min(CR, total_rows - r0);
     const unsigned bytes = (unsigned)(nr * row_bytes);
     fence_async_smem();
-    mbar_expect_tx(smem_u32(full + slot), bytes);
+    mbar_expect_tx(smem_u32(full + slot), bytes + t.extra_tx);
     bulk_g2s(smem_u32(ring + (size_t)slot * kStreamChunk), src + (size_t)r0 * Kq, bytes, smem_u32(full + slot));
   };
-  if (tid == 0)
+  if (tid == 0) {
+    for (int i = 0; i < kStreamSlots; ++i) released[i] = 0;
+    *issued = (unsigned)min(nch, kStreamSlots);
     for (int c = 0; c < min(nch, kStreamSlots); ++c) issue(c);
+  }
   // operands: U (face rows gathered, then interior layers), then D^k = U^{k+1} - U^k
   for (int r = tid; r < K; r += blockDim.x) rows[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
   __syncthreads();
@@ -117,26 +139,33 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   // consecutive threads share a row quad (one broadcast 16-byte coefficient load) and take its four
   // 4-source groups; the quads of a small K are then packed into the first warps, and the warps
   // beyond 4 K threads have no rows at all (no partially filled warps)
-  const int g = tid & 3, r4 = 4 * (tid >> 2);
-  const bool actq = r4 < K;                      // rows r4 .. r4+3 (those >= K read zero padding)
-  int rr[kWideRows];
-  bool act[kWideRows];
+  const int g = tid & 3, r4 = R * (tid >> 2);
+  const bool actq = r4 < K;                      // rows r4 .. r4+R-1 (those >= K read zero padding)
+  int rr[R];
+  bool act[R];
 #pragma unroll
-  for (int i = 0; i < kWideRows; ++i) {
+  for (int i = 0; i < R; ++i) {
     rr[i] = r4 + i;
     act[i] = rr[i] < K;
   }
   const float tau2 = a.tau2;
-  auto fail = [&](int c) {
-    if (tid == 0) atomicExch(t.err, 1);
-    stream_drain(full, gc0 + (unsigned)c, gc0 + (unsigned)min(nch, c + kStreamSlots));
-    gc = gc0 + (unsigned)nch;   // bookkeeping only; the caller stops
+  const int lane = tid & 31;
+  const unsigned nwarps = blockDim.x >> 5;
+  // Chunks advance per warp, not per block: a warp waits for the next chunk's barrier on its own,
+  // and the last warp to release a chunk refills its slot (release counts in shared memory), so no
+  // block-wide barrier is taken per chunk.  A wait that runs out records the error; the warp then
+  // stops waiting (its results are void, the state of a failed step is undefined) but keeps the
+  // block's control flow, and the copies in flight are drained at the end.
+  bool bad = false;
+  auto wait_chunk = [&](int cc) {
+    const unsigned gg = gc0 + (unsigned)cc;
+    const bool ok = mbar_wait(smem_u32(full + gg % kStreamSlots), (gg / kStreamSlots) & 1u, t.err);
+    if (__all_sync(0xffffffffu, ok)) return;
+    if (lane == 0) atomicExch(t.err, 1);
+    bad = true;
   };
   int c = 0;                                      // chunk being read
-  if (!stream_wait(full, gc0, t.err)) {
-    fail(0);
-    return false;
-  }
+  wait_chunk(0);
   for (int q = 0; q < 2 * m - 1; ++q) {
     if (q == m) {
       // all fluxes are in X: publish F^1, then E^k = F^k - F^{k-1} into D
@@ -160,23 +189,32 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
     }
     const int layer = q < m ? q : q - m + 1;
     const bool tri = fac && q == m - 1;           // the factored last coefficient, rows descending
-    float acc[kWideRows][CP], yv[kWideRows][CP];
+    float acc[R][CP], yv[R][CP];
 #pragma unroll
-    for (int i = 0; i < kWideRows; ++i)
+    for (int i = 0; i < R; ++i)
 #pragma unroll
       for (int e = 0; e < CP; ++e) acc[i][e] = yv[i][e] = 0.f;
     const float *Dl = D + (size_t)layer * K * ST + CP * g;
     for (int j0 = 0; j0 < K;) {
       const int fr = q * K + j0;
       if (fr >= (c + 1) * CR) {
-        // chunk c consumed by every thread: refill its slot, move to the next chunk
-        __syncthreads();
-        if (tid == 0 && c + kStreamSlots < nch) issue(c + kStreamSlots);
-        ++c;
-        if (!stream_wait(full, gc0 + (unsigned)c, t.err)) {
-          fail(c);
-          return false;
+        // this warp is done with chunk c; the last warp to release it refills the slot
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          const unsigned slot = (gc0 + (unsigned)c) % kStreamSlots;
+          if (atomicAdd(released + slot, 1u) == nwarps - 1) {
+            atomicExch(released + slot, 0u);
+            __threadfence_block();
+            if (c + kStreamSlots < nch) {
+              issue(c + kStreamSlots);
+              atomicMax(issued, (unsigned)(c + kStreamSlots + 1));
+            }
+          }
         }
+        __syncwarp();
+        ++c;
+        if (!bad) wait_chunk(c);
       }
       const int j1 = min(K, (c + 1) * CR - q * K);
       const int n = j1 - j0;
@@ -188,11 +226,10 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
 #pragma unroll U
           for (int h = 0; h < n; ++h) {
             const float4 d = *reinterpret_cast<const float4 *>(Dl + (size_t)(j0 + h) * ST);
-            const float4 gq = *reinterpret_cast<const float4 *>(sp + (size_t)h * Kq + r4);
-            fma4(acc[0], gq.x, d);
-            fma4(acc[1], gq.y, d);
-            fma4(acc[2], gq.z, d);
-            fma4(acc[3], gq.w, d);
+            float gv[R];
+            load_rows<R>(gv, sp + (size_t)h * Kq + r4);
+#pragma unroll
+            for (int i = 0; i < R; ++i) fma4(acc[i], gv[i], d);
           }
         }
       } else {
@@ -202,15 +239,15 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
         for (int h = 0; h < n && actq; ++h) {
           const int j = jt - h;
           const float4 d = *reinterpret_cast<const float4 *>(Dl + (size_t)j * ST);
-          const float4 gq = *reinterpret_cast<const float4 *>(sp + (size_t)h * Kq + r4);
-          const float gv[4] = {gq.x, gq.y, gq.z, gq.w};
+          float gv[R];
+          load_rows<R>(gv, sp + (size_t)h * Kq + r4);
 #pragma unroll
-          for (int i = 0; i < kWideRows; ++i)
+          for (int i = 0; i < R; ++i)
             if (rr[i] <= j) fma4(yv[i], gv[i], d);
         }
         // the y of this segment's rows are complete: share them
 #pragma unroll
-        for (int i = 0; i < kWideRows; ++i)
+        for (int i = 0; i < R; ++i)
           if (act[i] && rr[i] >= jb && rr[i] <= jt)
             *reinterpret_cast<float4 *>(Ys + (size_t)rr[i] * ST + CP * g) =
                 make_float4(yv[i][0], yv[i][1], yv[i][2], yv[i][3]);
@@ -219,10 +256,10 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
         for (int h = 0; h < n && actq; ++h) {
           const int j = jt - h;
           const float4 y = *reinterpret_cast<const float4 *>(Ys + (size_t)j * ST + CP * g);
-          const float4 gq = *reinterpret_cast<const float4 *>(sp + (size_t)h * Kq + r4);
-          const float gv[4] = {gq.x, gq.y, gq.z, gq.w};
+          float gv[R];
+          load_rows<R>(gv, sp + (size_t)h * Kq + r4);
 #pragma unroll
-          for (int i = 0; i < kWideRows; ++i)
+          for (int i = 0; i < R; ++i)
             if (rr[i] >= j) fma4(acc[i], gv[i], y);
         }
       }
@@ -230,7 +267,7 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
     }
     // end of matrix q: rows of F^{q+1}, or leapfrog of U^k with Gamma-hat^k E^k
 #pragma unroll
-    for (int i = 0; i < kWideRows; ++i) {
+    for (int i = 0; i < R; ++i) {
       if (!act[i]) continue;
       const int r = rr[i];
       if (q < m) {
@@ -259,6 +296,20 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
     }
   }
   __syncthreads();   // last chunk consumed (its slot may be refilled by the next item)
+  if (*(volatile int *)t.err) {
+    // a wait ran out somewhere: let the copies still in flight (only the last kStreamSlots issued
+    // can be) land before the CTA leaves
+    if (tid == 0) {
+      const unsigned iss = *issued;
+      for (unsigned cc = iss > (unsigned)kStreamSlots ? iss - kStreamSlots : 0u; cc < iss; ++cc) {
+        const unsigned gg = gc0 + cc;
+        mbar_wait(smem_u32(full + gg % kStreamSlots), (gg / kStreamSlots) & 1u, nullptr);
+      }
+    }
+    __syncthreads();
+    gc = gc0 + (unsigned)nch;
+    return false;
+  }
   if (m == 1) {
     // no interior layers: publish F^1 here
     for (int i = tid; i < K * ST; i += blockDim.x) {
@@ -270,14 +321,14 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   return true;
 }
 
-template <int U>
-__global__ void __launch_bounds__(kWideThreads, 1) k_cell_w(const StepArgs<float> a, const StreamArgs t, const int cur) {
+template <int U, int R>
+__global__ void __launch_bounds__(wide_threads(R), 1) k_cell_w(const StepArgs<float> a, const StreamArgs t, const int cur) {
   extern __shared__ __align__(128) unsigned char smem_w[];
   if (*(volatile const int *)t.err) return;
   stream_init(smem_w);
   unsigned gc = 0;
   const int tiles = (a.S + kStreamST - 1) / kStreamST;   // 1-D grid, tiles of a cell adjacent
-  cell_wide_item<U>(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_w, gc);
+  cell_wide_item<U, R>(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_w, gc);
 }
 
 }  // namespace mss

@@ -621,8 +621,9 @@ struct mss_sim {
   size_t tcq_smem = 0;
   int tc_kpmax = 16, st_max = 1, dev_smem = 0;
   bool stream_blob = false;                    // streamed-kernel coefficient copy present
-  bool wide_blob = false, wide_ok = false;     // wide streamed kernel (K_i up to 512) usable
+  bool wide_blob = false, wide_ok = false;     // wide streamed kernel (K_i up to 384) usable
   size_t wide_smem = 0;
+  int wide_var = 0;                            // its variant: bit 0 unroll 4 (else 2), bit 1 two rows per thread
   mss::TcArgs tca{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
@@ -743,10 +744,10 @@ static void set_smem_attrs(const mss_sim &s) {
   MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
   if (s.factor_last)
     MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
-  if (s.wide_ok) {
-    MSS_CUDA(cudaFuncSetAttribute(k_cell_w<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.wide_smem));
-    MSS_CUDA(cudaFuncSetAttribute(k_cell_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.wide_smem));
-  }
+  if (s.wide_ok)
+    for (const void *kf : {(const void *)k_cell_w<2, 4>, (const void *)k_cell_w<4, 4>, (const void *)k_cell_w<2, 2>,
+                           (const void *)k_cell_w<4, 2>})
+      MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.wide_smem));
   if (s.stream_ok)
   {
     MSS_CUDA(cudaFuncSetAttribute(k_cell_s<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.stream_smem));
@@ -789,8 +790,14 @@ static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStr
   const dim3 gc(s.n_cells * s.tiles);
   if constexpr (std::is_same<T, float>::value && ST == kStreamST) {
     if (s.sched == MSS_SCHED_GRAPH_STREAM) {
-      if (!s.stream_ok && s.stream_groups == 4) k_cell_w<4><<<gc, kWideThreads, s.wide_smem, st>>>(a, s.sca, cur);
-      else if (!s.stream_ok) k_cell_w<2><<<gc, kWideThreads, s.wide_smem, st>>>(a, s.sca, cur);
+      if (!s.stream_ok) {
+        switch (s.wide_var) {
+          case 1: k_cell_w<4, 4><<<gc, wide_threads(4), s.wide_smem, st>>>(a, s.sca, cur); break;
+          case 2: k_cell_w<2, 2><<<gc, wide_threads(2), s.wide_smem, st>>>(a, s.sca, cur); break;
+          case 3: k_cell_w<4, 2><<<gc, wide_threads(2), s.wide_smem, st>>>(a, s.sca, cur); break;
+          default: k_cell_w<2, 4><<<gc, wide_threads(4), s.wide_smem, st>>>(a, s.sca, cur); break;
+        }
+      }
       else if (s.stream_groups == 4) k_cell_s<4><<<gc, 512, s.stream_smem, st>>>(a, s.sca, cur);
       else k_cell_s<2><<<gc, 256, s.stream_smem, st>>>(a, s.sca, cur);
       return;
@@ -934,7 +941,7 @@ static void step_impl(mss_sim &s, int64_t n, const double *w, void *traces, int 
     // capture and replay on the sim's own stream (the legacy stream cannot be captured)
     MSS_CUDA(cudaEventRecord(s.ev_in, st));
     MSS_CUDA(cudaStreamWaitEvent(s.cap, s.ev_in, 0));
-    GraphKey key{n, w, traces, s.cur, s.sched, s.stream_groups + 8 * s.ST + 4096 * s.tcs_nt};
+    GraphKey key{n, w, traces, s.cur, s.sched, s.stream_groups + 8 * s.ST + 4096 * s.tcs_nt + 65536 * s.wide_var};
     auto it = s.graphs.find(key);
     if (it == s.graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -1822,7 +1829,10 @@ mss_status mss_sim_debug(mss_sim *s, int32_t knob, int32_t value) {
     MSS_REQUIRE(s && value >= 0, MSS_ERR_INVALID_ARG, "bad argument");
     switch (knob) {
       case MSS_DEBUG_GRID_EXTRA_ARRIVALS: s->sca.extra_arrivals = value; break;
-      case MSS_DEBUG_TC_EXTRA_TX: s->tca.extra_tx = (unsigned)value; break;
+      case MSS_DEBUG_TC_EXTRA_TX:
+        s->tca.extra_tx = (unsigned)value;
+        s->sca.extra_tx = (unsigned)value;
+        break;
       default: MSS_REQUIRE(false, MSS_ERR_INVALID_ARG, "unknown debug knob");
     }
   });
@@ -1856,8 +1866,13 @@ mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources,
       apply_tcs_nt(*s, tc_sources);
     }
     if (groups > 0) {
-      MSS_REQUIRE(groups == 2 || groups == 4, MSS_ERR_INVALID_ARG, "thread groups must be 2 or 4");
-      s->stream_groups = groups;
+      if (s->wide_ok && !s->stream_ok) {
+        MSS_REQUIRE(groups <= 4, MSS_ERR_INVALID_ARG, "wide streamed kernel variant must be 1..4");
+        s->wide_var = groups - 1;
+      } else {
+        MSS_REQUIRE(groups == 2 || groups == 4, MSS_ERR_INVALID_ARG, "thread groups must be 2 or 4");
+        s->stream_groups = groups;
+      }
     }
   });
 }
@@ -1871,7 +1886,7 @@ mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *avail
     if (tile) {
       tile[0] = s->ST;
       tile[1] = s->tc ? s->tcs_nt : 0;
-      tile[2] = s->stream_groups;
+      tile[2] = s->wide_ok && !s->stream_ok ? s->wide_var + 1 : s->stream_groups;
     }
   });
 }
@@ -1896,7 +1911,7 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
     MSS_CUDA(cudaMemset(w.p, 0, (size_t)n * 8));
     tr.alloc((size_t)n * std::max(1, s->n_rcv) * s->n_src * es);
     const int cur0 = s->cur, sched0 = s->sched;
-    const int st_keep = s->ST, nt_keep = s->tcs_nt, g_keep = s->stream_groups;
+    const int st_keep = s->ST, nt_keep = s->tcs_nt, g_keep = s->stream_groups, wv_keep = s->wide_var;
     const int64_t steps0 = s->steps;
     cudaEvent_t e0, e1;
     MSS_CUDA(cudaEventCreate(&e0));
@@ -1913,7 +1928,7 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
       // candidates: every available schedule x its tile variants (CUDA-core source tile ST,
       // tensor-core split N, streamed-kernel thread groups); every variant computes each source's
       // columns with the same operations, so the choice does not change the arithmetic
-      struct Cand { int sched, st, nt, groups; };
+      struct Cand { int sched, st, nt, groups, wv; };
       std::vector<Cand> cands;
       const int st0 = s->ST, nt0 = s->tcs_nt, g0 = s->stream_groups;
       for (int k = 0; k < MSS_SCHED_COUNT; ++k) {
@@ -1924,28 +1939,32 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
           for (int st : {s->st_max, s->st_max / 2}) {
             if (st < 8 && st != s->st_max) continue;
             if (streamed && st != kStreamST) continue;
-            if (k == MSS_SCHED_GRAPH_STREAM) {
-              for (int gv : {4, 2}) cands.push_back({k, st, nt0, gv});
+            if (k == MSS_SCHED_GRAPH_STREAM && !s->stream_ok) {
+              for (int wv = 0; wv < 4; ++wv) cands.push_back({k, st, nt0, g0, wv});
+            } else if (k == MSS_SCHED_GRAPH_STREAM) {
+              for (int gv : {4, 2}) cands.push_back({k, st, nt0, gv, s->wide_var});
             } else {
-              cands.push_back({k, st, nt0, g0});
+              cands.push_back({k, st, nt0, g0, s->wide_var});
             }
           }
         } else if (k == MSS_SCHED_GRAPH_SPLIT || k == MSS_SCHED_PERSIST) {
           for (int nt : {16, 32, 64, 128}) {
             if (nt > 16 && nt / 2 >= s->n_src) continue;
             if (tcs_smem_bytes(nt, s->tc_kpmax) > (size_t)s->dev_smem) continue;
-            cands.push_back({k, st0, nt, g0});
+            cands.push_back({k, st0, nt, g0, s->wide_var});
           }
         } else {
-          cands.push_back({k, st0, nt0, g0});
+          cands.push_back({k, st0, nt0, g0, s->wide_var});
         }
       }
-      Cand best_c{sched0, st0, nt0, g0};
+      const int wv0 = s->wide_var;
+      Cand best_c{sched0, st0, nt0, g0, wv0};
       for (const Cand &c : cands) {
         s->sched = c.sched;
         if (c.st != s->ST) apply_tile(*s, c.st);
         if (s->tc && c.nt != s->tcs_nt) apply_tcs_nt(*s, c.nt);
         s->stream_groups = c.groups;
+        s->wide_var = c.wv;
         auto run = [&]() {
           if (s->prec == MSS_FP64) step_dispatch<double>(*s, n, w.as<double>(), tr.p, 1, st);
           else step_dispatch<float>(*s, n, w.as<double>(), tr.p, 1, st);
@@ -1973,12 +1992,14 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
       if (s->tc && best_c.nt != s->tcs_nt) apply_tcs_nt(*s, best_c.nt);
       const int best_groups = best_c.groups;
       s->stream_groups = best_groups;
+      s->wide_var = best_c.wv;
     } catch (...) {
       restore();
       s->sched = sched0;
       if (s->ST != st_keep) apply_tile(*s, st_keep);
       if (s->tc && s->tcs_nt != nt_keep) apply_tcs_nt(*s, nt_keep);
       s->stream_groups = g_keep;
+      s->wide_var = wv_keep;
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       throw;

@@ -126,15 +126,17 @@ def peak_frequency(sigma: np.ndarray, rho: np.ndarray, h: float) -> float:
     return c_min / (20.0 * h)
 
 
-def cell_wavelength_peak(sigma: np.ndarray, rho: np.ndarray, h: float, cell_edge: int) -> float:
-    """Ricker peak whose band limit (``ricker_band_limit``) has a minimum wavelength of one cell.
+def cell_wavelength_peak(sigma: np.ndarray, rho: np.ndarray, h: float, cell_edge: int,
+                         wavelengths: float = 1.0) -> float:
+    """Ricker peak whose band limit (``ricker_band_limit``) puts ``wavelengths`` minimum
+    wavelengths across a cell.
 
     The shortest wavelength c_min / f_max, at the slowest voxel, equals the cell edge
-    ``cell_edge * h``: the operating point of the paper's experiments (Section 7: coarse
-    cells about one minimum wavelength across).
+    ``cell_edge * h`` divided by ``wavelengths``; 1 is the operating point of the paper's
+    experiments (Section 7: coarse cells about one minimum wavelength across).
     """
     c_min = float(np.sqrt(np.min(sigma / rho)))
-    return c_min / (cell_edge * h) / ricker_band_limit(1.0)
+    return wavelengths * c_min / (cell_edge * h) / ricker_band_limit(1.0)
 
 
 # --------------------------------------------------------------------------- workloads
@@ -164,7 +166,7 @@ def workload_2d_layers(n: int = 64, cell: int = 8, m: int = 4, n_modes: int = 4,
 
 def workload_3d_layers(n: int = 128, cell: int = 16, m: int = 4, n_modes: int = 15,
                        n_src: int = 16, n_steps: int = 4000, seed_index: int = 1,
-                       band: str = "nyquist") -> Workload:
+                       band: str = "nyquist", cell_wavelengths: float = 1.0) -> Workload:
     """3D acoustic, n^3 voxels, Neumann top, Dirichlet elsewhere, 4 layers, lognormal noise.
 
     Layers top to bottom: sigma (1, 2, 4, 8), rho (1, 1.5, 2, 2.5); sigma multiplied
@@ -174,7 +176,8 @@ def workload_3d_layers(n: int = 128, cell: int = 16, m: int = 4, n_modes: int = 
     At n=128, cell=16 this is the 512-cell, 16-source surface workload.
     ``band``: ``"nyquist"`` puts the Ricker peak at one tenth of the grid Nyquist
     (``peak_frequency``; cells are then about 2.9 minimum wavelengths across at 16^3);
-    ``"cell"`` makes the minimum wavelength one cell edge (``cell_wavelength_peak``).
+    ``"cell"`` puts ``cell_wavelengths`` minimum wavelengths across a cell
+    (``cell_wavelength_peak``; 1 by default).
     """
     rng = np.random.default_rng(SEED_BASE + seed_index)
     grid = Grid(n=(n, n, n), h=1.0 / n, bc=(("D", "N"), ("D", "D"), ("D", "D")))
@@ -193,7 +196,7 @@ def workload_3d_layers(n: int = 128, cell: int = 16, m: int = 4, n_modes: int = 
     if band == "nyquist":
         fp = peak_frequency(sigma, rho, grid.h)
     elif band == "cell":
-        fp = cell_wavelength_peak(sigma, rho, grid.h, cell)
+        fp = cell_wavelength_peak(sigma, rho, grid.h, cell, cell_wavelengths)
     else:
         raise ValueError("band must be 'nyquist' or 'cell'")
     return Workload("3d_layers_%d" % n, grid, sigma, rho, (cell, cell, cell), m, n_modes, src, rcv,

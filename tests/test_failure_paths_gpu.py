@@ -1,6 +1,7 @@
 """Failure detection on the GPU without faulting it: a deliberately missing neighbour at the
 persistent kernel's grid barrier, and a matrix copy barrier of the split tensor-core kernels
-that expects bytes which never arrive.  Each bounded wait runs out (1 s / 100 ms), the kernel
+that expects bytes which never arrive, and the same for the wide streamed cell kernel's chunk
+barriers.  Each bounded wait runs out (1 s / 100 ms), the kernel
 records TIMEOUT in the sim's error word and returns; the host reads MSS_ERR_TIMEOUT, clears the
 word, and the same context then steps normally and bit-identically to an undisturbed run.
 """
@@ -27,14 +28,14 @@ def P():
     return pkg
 
 
-def _sim(P, prec, n_src=16):
+def _sim(P, prec, n_src=16, factor_last=False):
     topo = synth.box_topology((3, 2, 2), modes=5, m=[2, 3, 4] * 4, io_cells=[(0, 2), (7, 3)], seed=2,
                               ragged_modes=True)
     co = synth.random_coefficients(topo, seed=2)
     src, rcv = synth.random_io(topo, n_src, 4, seed=2)
     R = P.Rom.import_(topo, co)
     R.set_io(n_src, src, 4, rcv)
-    return P.Sim(R, prec, 0.08)
+    return P.Sim(R, prec, 0.08, factor_last=factor_last)
 
 
 def _run(P, sim, nst, prec, n_src=16):
@@ -48,16 +49,18 @@ def _run(P, sim, nst, prec, n_src=16):
 @pytest.mark.parametrize("prec,sched,knob,value", [
     ("fp32", "persist", "grid", 1),
     ("fp32_tc", "split", "tc", 16),
+    ("fp32_factored", "stream", "tc", 16),     # the wide TMA-streamed cell kernel's chunk barriers
 ])
 def test_bounded_wait_reports_timeout_and_context_recovers(P, prec, sched, knob, value):
-    pr = {"fp32": P.FP32, "fp32_tc": P.FP32_TC}[prec]
-    sc = {"persist": P.SCHED_PERSIST, "split": P.SCHED_GRAPH_SPLIT}[sched]
+    fac = prec == "fp32_factored"
+    pr = {"fp32": P.FP32, "fp32_tc": P.FP32_TC, "fp32_factored": P.FP32}[prec]
+    sc = {"persist": P.SCHED_PERSIST, "split": P.SCHED_GRAPH_SPLIT, "stream": P.SCHED_GRAPH_STREAM}[sched]
     kb = {"grid": P.DEBUG_GRID_EXTRA_ARRIVALS, "tc": P.DEBUG_TC_EXTRA_TX}[knob]
-    ref_sim = _sim(P, pr)
+    ref_sim = _sim(P, pr, factor_last=fac)
     ref_sim.set_schedule(sc)
     ref = _run(P, ref_sim, 60, pr).cpu().numpy()
     ref_sim.info()
-    sim = _sim(P, pr)
+    sim = _sim(P, pr, factor_last=fac)
     sim.set_schedule(sc)
     sim.debug(kb, value)
     t0 = time.perf_counter()

@@ -137,12 +137,34 @@ def test_factored_schedules_bit_identical(P, case):
         assert np.array_equal(outs[0], o)
 
 
+def _run_variant(P, c, factor_last, variant):
+    sim = P.Sim(c["LR"], P.FP32, c["tau"], corner_correction=True, factor_last=factor_last)
+    sim.set_schedule(P.SCHED_GRAPH_STREAM)
+    sim.set_tile(groups=variant)
+    assert sim.tile()[2] == variant
+    wd = torch.tensor(c["w"], device="cuda")
+    tr = torch.zeros((c["nst"], c["n_rcv"], c["n_src"]), device="cuda", dtype=torch.float32)
+    sim.step(c["nst"], wd, tr)
+    torch.cuda.synchronize()
+    sim.info()
+    return tr.cpu().numpy().astype(np.float64)
+
+
 def test_wide_streamed_kernel_bit_identical_unfactored(P, case):
     c16 = case["wide"]
     a = _run(P, c16, P.FP32, sched=P.SCHED_GRAPH)
     c = _run(P, c16, P.FP32, sched=P.SCHED_GRAPH_STREAM)
     assert np.linalg.norm(a) > 0
     assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("factor_last", [False, True])
+def test_wide_kernel_variants_bit_identical(P, case, factor_last):
+    """Unroll depth 2/4 and 4/2 rows per thread: the same multiply-adds in the same order."""
+    c16 = case["wide"]
+    ref = _run(P, c16, P.FP32, factor_last=factor_last, sched=P.SCHED_GRAPH)
+    for v in (1, 2, 3, 4):
+        assert np.array_equal(_run_variant(P, c16, factor_last, v), ref), v
 
 
 @pytest.mark.parametrize("n_src", [3, 16, 21])
