@@ -536,6 +536,118 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_c3(args):
+    """The 256^3 dipping-layer workload end to end on one GPU: GPU off-line build of all 4096 cell
+    ROMs (m = 4 in every cell; the per-cell layer rule runs in the oracle only), 256 sources on
+    face centres of the skeleton plane one cell below the top, 128 receivers on a line in that
+    plane, 6000 steps; FP32 with split-BF16 tensor-core products (the many-source path), BF16
+    products and CUDA-core FP32 timed; receiver error against the same GPU's FP64 fine-grid
+    leapfrog on the original graph; FP64 parity against the oracle's ROM leapfrog on the exported
+    coefficients for three sampled sources over a short window.  One JSON line."""
+    import torch
+    import paper_1604_06750_gb300 as P
+    from paper_1604_06750_gb300 import build as B
+    from oracle import online
+    B.build()
+    P.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    wl = synth.workload_3d_dipping(args.c3_n, 16, m=4, n_modes=args.c3_modes, n_steps=args.c3_steps)
+    t0 = time.perf_counter()
+    L = P.Operator(wl.grid, wl.sigma, wl.rho)
+    io = np.concatenate([wl.src_nodes, wl.rcv_nodes]).astype(np.int32)
+    LP = P.Partition(L, wl.cell, io)
+    lam = L.lambda_max(1e-7)
+    tau = wl.cfl_fraction * 2.0 / math.sqrt(lam)
+    s = -(2 * math.pi * wl.f_max) ** 2
+    t1 = time.perf_counter()
+    LR = P.Rom.build(LP, wl.m, wl.n_modes, s, cg_tol=1e-12)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    LR.set_io_nodes(LP, wl.src_nodes, wl.rcv_nodes)
+    cm, cfp, cf, fM, fc, _, _, _ = LR.export()
+    Ks = [int(sum(fM[cf[cfp[c]:cfp[c + 1]]])) for c in range(len(cm))]
+    nst, S, R = wl.n_steps, len(wl.src_nodes), len(wl.rcv_nodes)
+    units = len(cm) * S * nst
+    w = synth.ricker(np.arange(nst) * tau, wl.f_peak)
+    wd = torch.tensor(w, device=dev)
+    flush = torch.empty(int(512e6) // 4, device=dev, dtype=torch.float32)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    out = {"mode": "c3", "config": {"workload": "3d_dipping_%d: %d^3 voxels, %d cells of 16^3 (uneven K_i %d..%d), "
+                                                "m=4, %d modes/face, %d sources, %d receivers, %d steps"
+                                                % (args.c3_n, args.c3_n, len(cm), min(Ks), max(Ks), wl.n_modes, S,
+                                                   R, nst),
+                                    "band": "Ricker peak at 1/10 grid Nyquist", "layers": "m = 4 in every cell"},
+           "unit": UNIT, "offline_s": {"assemble_partition_cfl": t1 - t0, "gpu_rom_build": t2 - t1},
+           "tau": tau, "precisions": {}}
+    clocks = Clocks(0)
+    clocks.start()
+    traces = {}
+    for name, prec in (("fp32_tc", P.FP32_TC), ("bf16_tc", P.BF16_TC), ("fp32", P.FP32)):
+        sim = P.Sim(LR, prec, tau, corner_correction=True)
+        k, msk = sim.autotune(20)
+        tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+        _timed_runs(sim, nst, wd, tr, 1, stream)
+        t = _timed_runs(sim, nst, wd, tr, 1, stream, flush)[0]
+        sim.info()
+        traces[name] = tr.double().cpu().numpy()
+        out["precisions"][name] = {"value": units / t, "ms_per_time_step": 1e3 * t / nst,
+                                   "schedule": SCHED_NAMES[k]}
+        del sim, tr
+        torch.cuda.empty_cache()
+    # the accuracy reference: FP64 fine grid on the original graph, same tau and steps
+    fine64 = P.FineSim(L, P.FP64, tau, wl.src_nodes, wl.rcv_nodes)
+    trf = torch.zeros((nst, R, S), device=dev, dtype=torch.float64)
+    fine64.step(nst, wd, trf)
+    torch.cuda.synchronize()
+    ref = trf.cpu().numpy()
+    del fine64, trf
+    torch.cuda.empty_cache()
+    fine = P.FineSim(L, P.FP32, tau, wl.src_nodes, wl.rcv_nodes)
+    trf = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+    _timed_runs(fine, nst, wd, trf, 1, stream)
+    tf = _timed_runs(fine, nst, wd, trf, 1, stream, flush)[0]
+    fine32 = trf.double().cpu().numpy()
+    del fine, trf
+    torch.cuda.empty_cache()
+    out["clocks"] = clocks.stop()
+    out["fine_grid_fp32"] = {"value": units / tf, "ms_per_time_step": 1e3 * tf / nst,
+                             "receiver_rel_l2_vs_fine_fp64": rel(fine32, ref)}
+    for name in traces:
+        out["precisions"][name]["receiver_rel_l2_vs_fine_fp64"] = rel(traces[name], ref)
+        out["precisions"][name]["receiver_rel_l2_vs_fp32_tc"] = rel(traces[name], traces["fp32_tc"])
+    # FP64 parity against the oracle on the exported coefficients: three sampled sources, no
+    # corner correction (the oracle's C loops restate the leapfrog without it), a short window
+    npar = args.c3_parity_steps
+    pick = [0, S // 2, S - 1]
+    topo, co = _exported_rom(LR)
+    src_e, rcv_e, _ = LR.export_io()
+    src3 = [(f, pick.index(j), v) for (f, j, v) in src_e if j in pick]
+    gt = online.dense_io(topo, src3, len(pick), "src")
+    qt = online.dense_io(topo, rcv_e, R, "rcv")
+    step, label, threads = _oracle_stepper(topo, co, gt, qt)
+    t3 = time.perf_counter()
+    oref = step(w[:npar], tau, npar)
+    t_or = time.perf_counter() - t3
+    sim64 = P.Sim(LR, P.FP64, tau, corner_correction=False)
+    tr64 = torch.zeros((npar, R, S), device=dev, dtype=torch.float64)
+    sim64.step(npar, wd[:npar], tr64)
+    torch.cuda.synchronize()
+    g64 = tr64.cpu().numpy()[:, :, pick]
+    simtc = P.Sim(LR, P.FP32_TC, tau, corner_correction=False)
+    trtc = torch.zeros((npar, R, S), device=dev, dtype=torch.float32)
+    simtc.step(npar, wd[:npar], trtc)
+    torch.cuda.synchronize()
+    gtc = trtc.double().cpu().numpy()[:, :, pick]
+    out["parity_vs_oracle"] = {"sources": pick, "steps": npar, "fp64_rel_l2": rel(g64, oref),
+                               "fp32_tc_rel_l2": rel(gtc, oref), "oracle": "%s, %d threads, %.1f s"
+                               % (label, threads, t_or)}
+    print(json.dumps(out))
+
+
 def run_many_sources(args):
     """The 4096-cell, 256-source on-line shape of the 256^3 dipping-layer workload (synthetic SPD
     coefficients, m_i in 3..6, uneven K_i): throughput of every precision, the CUDA-core FP32
@@ -866,6 +978,12 @@ def main():
     ap.add_argument("--plain-fp32", action="store_true", help="headline FP32 without the factored last coefficient")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle's host timing")
     ap.add_argument("--ref-sample", type=int, default=10, help="time steps per bench step of --impl reference")
+    ap.add_argument("--config", default=None, choices=["c3"],
+                    help="c3: the 256^3 dipping-layer workload end to end (separate JSON line)")
+    ap.add_argument("--c3-n", type=int, default=256)
+    ap.add_argument("--c3-modes", type=int, default=15)
+    ap.add_argument("--c3-steps", type=int, default=6000)
+    ap.add_argument("--c3-parity-steps", type=int, default=200)
     ap.add_argument("--accuracy", action="store_true",
                     help="ROM vs fine grid at equal receiver accuracy over face-mode counts (JSON line)")
     ap.add_argument("--acc-n", type=int, default=64, help="voxels per edge of --accuracy")
@@ -880,6 +998,9 @@ def main():
     ap.add_argument("--acc-band", default="cell", choices=["cell", "nyquist"],
                     help="band of --accuracy: one minimum wavelength per cell, or peak at 1/10 grid Nyquist")
     args = ap.parse_args()
+    if args.config == "c3":
+        run_c3(args)
+        return
     if args.accuracy:
         run_accuracy(args)
         return
