@@ -352,9 +352,10 @@ mss_status mss_sim_clear_error(mss_sim *s, void *stream);
  * of two up to the one chosen at creation; 16 is needed by the streamed schedules, the schedule
  * falls back to GRAPH otherwise), sources per CTA of the split tensor-core kernels (16, 32, 64,
  * 128), thread groups of the streamed FP32 kernel (2 or 4; for a sim whose streamed schedule runs
- * the wide kernel -- K_i > 128 or the factored last coefficient -- its variant 1..4: unroll depth
- * 2 or 4 of the row loops, and 4 or 2 rows per thread, as 1 = (2, 4), 2 = (4, 4), 3 = (2, 2),
- * 4 = (4, 2); every variant gives the same bits).  Errors: INVALID_ARG. */
+ * the wide kernel -- K_i > 128 or the factored last coefficient -- its variant 1..8: unroll depth
+ * 2 or 4 of the row loops, 4 or 2 rows per thread, 16 or 8 sources per CTA, as 1 = (2, 4, 16),
+ * 2 = (4, 4, 16), 3 = (2, 2, 16), 4 = (4, 2, 16), 5..8 the same with 8 sources; every variant
+ * gives the same bits).  Errors: INVALID_ARG. */
 mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources, int32_t groups);
 /* sched: current schedule; available (may be NULL): [MSS_SCHED_COUNT] 1 where usable; tile (may
  * be NULL): [3] = CUDA-core source tile, sources per CTA of the split tensor-core kernels (0 for

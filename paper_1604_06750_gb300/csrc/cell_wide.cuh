@@ -33,15 +33,18 @@ namespace mss {
 
 constexpr int kWideMaxK = 384;     // largest K_i of the wide kernel
 constexpr int kWideCP = 4;          // sources per thread (four 4-source groups per 16-source tile)
-// threads of the wide kernel with R consecutive rows per thread: 4 source groups x K_max / R
-__host__ __device__ constexpr int wide_threads(int R) { return 4 * kWideMaxK / R; }
+// threads of the wide kernel with R consecutive rows per thread and NS-source tiles: NS / 4 source
+// groups x K_max / R
+__host__ __device__ constexpr int wide_threads(int R, int NS) { return NS / 4 * kWideMaxK / R; }
+// ring slots of the wide kernel: four 16 KB slots with 16-source tiles; two with 8-source tiles,
+// whose smaller operand blocks then let two CTAs share an SM
+__host__ __device__ constexpr int wide_slots(int NS) { return NS == 16 ? 4 : 2; }
 
-// Shared memory of the wide kernel: ring and its barriers, U/F (X) and D/E (D) as m K 16 floats
-// each, the factored product's y (K 16 floats), the K boundary-row indices.
-inline size_t wide_smem_bytes(int max_m, int max_K, int factor_last) {
-  return (size_t)kStreamSlots * kStreamChunk + 64 +
-         (2 * (size_t)max_m * max_K * kStreamST + (factor_last ? (size_t)max_K * kStreamST : 0)) * 4 +
-         8 * (size_t)max_K;
+// Shared memory of the wide kernel with NS-source tiles: ring and its barriers, U/F (X) and D/E
+// (D) as m K NS floats each, the factored product's y (K NS floats), the K boundary-row indices.
+inline size_t wide_smem_bytes(int max_m, int max_K, int factor_last, int NS) {
+  return (size_t)wide_slots(NS) * kStreamChunk + 64 +
+         (2 * (size_t)max_m * max_K * NS + (factor_last ? (size_t)max_K * NS : 0)) * 4 + 8 * (size_t)max_K;
 }
 
 // R consecutive floats of a slot row (16-byte or 8-byte aligned: Kq and r4 are multiples of R)
@@ -65,10 +68,10 @@ __device__ __forceinline__ void fma4(float (&acc)[kWideCP], float gv, const floa
 // false if a wait timed out (error recorded, copies drained).  U: unroll depth of the row loops
 // (the autotuner picks 2 or 4); R: consecutive rows per thread (4, or 2 for twice the warps); the
 // arithmetic depends on neither.
-template <int U, int R>
+template <int U, int R, int NS>
 __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, const int cur, const int cell,
                                const int tile, unsigned char *smem, unsigned &gc) {
-  constexpr int ST = kStreamST, CP = kWideCP;
+  constexpr int ST = NS, CP = kWideCP, SL = wide_slots(NS), G = NS / CP;
   const int s0 = tile * ST;
   const int K = a.cell_K[cell], m = a.cell_m[cell], Kq = t.Kq[cell];
   const int ns = min(ST, a.S - s0);
@@ -76,11 +79,11 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   const int tid = threadIdx.x;
   const bool fac = a.factor_last != 0;
   unsigned char *ring = smem;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStreamSlots * kStreamChunk);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + SL * kStreamChunk);
   // after the four barriers: per-slot release counts of the warps, and the chunks issued so far
-  unsigned *released = reinterpret_cast<unsigned *>(smem + kStreamSlots * kStreamChunk + 32);
-  unsigned *issued = released + kStreamSlots;
-  float *X = reinterpret_cast<float *>(smem + kStreamSlots * kStreamChunk + 64);
+  unsigned *released = reinterpret_cast<unsigned *>(smem + SL * kStreamChunk + 32);
+  unsigned *issued = released + SL;
+  float *X = reinterpret_cast<float *>(smem + SL * kStreamChunk + 64);
   float *D = X + (size_t)m * K * ST;
   float *Ys = D + (size_t)m * K * ST;
   int64_t *rows = reinterpret_cast<int64_t *>(Ys + (fac ? (size_t)K * ST : 0));
@@ -95,7 +98,7 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   const unsigned gc0 = gc;
   const float *src = t.coef + t.coef_off[cell];
   auto issue = [&](int c) {   // thread 0 only
-    const unsigned g = gc0 + (unsigned)c, slot = g % kStreamSlots;
+    const unsigned g = gc0 + (unsigned)c, slot = g % SL;
     const int r0 = c * CR, nr = min(CR, total_rows - r0);
     const unsigned bytes = (unsigned)(nr * row_bytes);
     fence_async_smem();
@@ -103,9 +106,9 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
     bulk_g2s(smem_u32(ring + (size_t)slot * kStreamChunk), src + (size_t)r0 * Kq, bytes, smem_u32(full + slot));
   };
   if (tid == 0) {
-    for (int i = 0; i < kStreamSlots; ++i) released[i] = 0;
-    *issued = (unsigned)min(nch, kStreamSlots);
-    for (int c = 0; c < min(nch, kStreamSlots); ++c) issue(c);
+    for (int i = 0; i < SL; ++i) released[i] = 0;
+    *issued = (unsigned)min(nch, SL);
+    for (int c = 0; c < min(nch, SL); ++c) issue(c);
   }
   // operands: U (face rows gathered, then interior layers), then D^k = U^{k+1} - U^k
   for (int r = tid; r < K; r += blockDim.x) rows[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
@@ -139,7 +142,7 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   // consecutive threads share a row quad (one broadcast 16-byte coefficient load) and take its four
   // 4-source groups; the quads of a small K are then packed into the first warps, and the warps
   // beyond 4 K threads have no rows at all (no partially filled warps)
-  const int g = tid & 3, r4 = R * (tid >> 2);
+  const int g = tid % G, r4 = R * (tid / G);
   const bool actq = r4 < K;                      // rows r4 .. r4+R-1 (those >= K read zero padding)
   int rr[R];
   bool act[R];
@@ -159,7 +162,7 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   bool bad = false;
   auto wait_chunk = [&](int cc) {
     const unsigned gg = gc0 + (unsigned)cc;
-    const bool ok = mbar_wait(smem_u32(full + gg % kStreamSlots), (gg / kStreamSlots) & 1u, t.err);
+    const bool ok = mbar_wait(smem_u32(full + gg % SL), (gg / SL) & 1u, t.err);
     if (__all_sync(0xffffffffu, ok)) return;
     if (lane == 0) atomicExch(t.err, 1);
     bad = true;
@@ -202,13 +205,13 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
         __syncwarp();
         if (lane == 0) {
           __threadfence_block();
-          const unsigned slot = (gc0 + (unsigned)c) % kStreamSlots;
+          const unsigned slot = (gc0 + (unsigned)c) % SL;
           if (atomicAdd(released + slot, 1u) == nwarps - 1) {
             atomicExch(released + slot, 0u);
             __threadfence_block();
-            if (c + kStreamSlots < nch) {
-              issue(c + kStreamSlots);
-              atomicMax(issued, (unsigned)(c + kStreamSlots + 1));
+            if (c + SL < nch) {
+              issue(c + SL);
+              atomicMax(issued, (unsigned)(c + SL + 1));
             }
           }
         }
@@ -218,7 +221,7 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
       }
       const int j1 = min(K, (c + 1) * CR - q * K);
       const int n = j1 - j0;
-      const float *sp = reinterpret_cast<const float *>(ring + (size_t)((gc0 + c) % kStreamSlots) * kStreamChunk) +
+      const float *sp = reinterpret_cast<const float *>(ring + (size_t)((gc0 + c) % SL) * kStreamChunk) +
                         (size_t)(fr - c * CR) * Kq;
       if (!tri) {
         // acc[i] += G[j][r4 + i] D^layer_j, j = j0 .. j1-1 ascending
@@ -297,13 +300,13 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   }
   __syncthreads();   // last chunk consumed (its slot may be refilled by the next item)
   if (*(volatile int *)t.err) {
-    // a wait ran out somewhere: let the copies still in flight (only the last kStreamSlots issued
+    // a wait ran out somewhere: let the copies still in flight (only the last SL issued
     // can be) land before the CTA leaves
     if (tid == 0) {
       const unsigned iss = *issued;
-      for (unsigned cc = iss > (unsigned)kStreamSlots ? iss - kStreamSlots : 0u; cc < iss; ++cc) {
+      for (unsigned cc = iss > (unsigned)SL ? iss - SL : 0u; cc < iss; ++cc) {
         const unsigned gg = gc0 + cc;
-        mbar_wait(smem_u32(full + gg % kStreamSlots), (gg / kStreamSlots) & 1u, nullptr);
+        mbar_wait(smem_u32(full + gg % SL), (gg / SL) & 1u, nullptr);
       }
     }
     __syncthreads();
@@ -321,14 +324,21 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   return true;
 }
 
-template <int U, int R>
-__global__ void __launch_bounds__(wide_threads(R), 1) k_cell_w(const StepArgs<float> a, const StreamArgs t, const int cur) {
+template <int U, int R, int NS>
+__global__ void __launch_bounds__(wide_threads(R, NS), NS == 16 ? 1 : 2)
+    k_cell_w(const StepArgs<float> a, const StreamArgs t, const int cur) {
   extern __shared__ __align__(128) unsigned char smem_w[];
   if (*(volatile const int *)t.err) return;
-  stream_init(smem_w);
+  constexpr int SL = wide_slots(NS);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_w + SL * kStreamChunk);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < SL; ++i) mbar_init(smem_u32(full + i), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
   unsigned gc = 0;
-  const int tiles = (a.S + kStreamST - 1) / kStreamST;   // 1-D grid, tiles of a cell adjacent
-  cell_wide_item<U, R>(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_w, gc);
+  const int tiles = (a.S + NS - 1) / NS;   // 1-D grid, tiles of a cell adjacent
+  cell_wide_item<U, R, NS>(a, t, cur, blockIdx.x / tiles, blockIdx.x % tiles, smem_w, gc);
 }
 
 }  // namespace mss

@@ -622,8 +622,9 @@ struct mss_sim {
   int tc_kpmax = 16, st_max = 1, dev_smem = 0;
   bool stream_blob = false;                    // streamed-kernel coefficient copy present
   bool wide_blob = false, wide_ok = false;     // wide streamed kernel (K_i up to 384) usable
-  size_t wide_smem = 0;
-  int wide_var = 0;                            // its variant: bit 0 unroll 4 (else 2), bit 1 two rows per thread
+  size_t wide_smem = 0, wide_smem8 = 0;       // with 16- and 8-source tiles
+  int wide_var = 0;                            // its variant: bit 0 unroll 4 (else 2), bit 1 two rows per
+                                               // thread (else 4), bit 2 8-source tiles (else 16)
   mss::TcArgs tca{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
@@ -744,10 +745,14 @@ static void set_smem_attrs(const mss_sim &s) {
   MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
   if (s.factor_last)
     MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
-  if (s.wide_ok)
-    for (const void *kf : {(const void *)k_cell_w<2, 4>, (const void *)k_cell_w<4, 4>, (const void *)k_cell_w<2, 2>,
-                           (const void *)k_cell_w<4, 2>})
+  if (s.wide_ok) {
+    for (const void *kf : {(const void *)k_cell_w<2, 4, 16>, (const void *)k_cell_w<4, 4, 16>,
+                           (const void *)k_cell_w<2, 2, 16>, (const void *)k_cell_w<4, 2, 16>})
       MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.wide_smem));
+    for (const void *kf : {(const void *)k_cell_w<2, 4, 8>, (const void *)k_cell_w<4, 4, 8>,
+                           (const void *)k_cell_w<2, 2, 8>, (const void *)k_cell_w<4, 2, 8>})
+      MSS_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.wide_smem8));
+  }
   if (s.stream_ok)
   {
     MSS_CUDA(cudaFuncSetAttribute(k_cell_s<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.stream_smem));
@@ -791,11 +796,16 @@ static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStr
   if constexpr (std::is_same<T, float>::value && ST == kStreamST) {
     if (s.sched == MSS_SCHED_GRAPH_STREAM) {
       if (!s.stream_ok) {
+        const dim3 g8(s.n_cells * ((s.n_src + 7) / 8));
         switch (s.wide_var) {
-          case 1: k_cell_w<4, 4><<<gc, wide_threads(4), s.wide_smem, st>>>(a, s.sca, cur); break;
-          case 2: k_cell_w<2, 2><<<gc, wide_threads(2), s.wide_smem, st>>>(a, s.sca, cur); break;
-          case 3: k_cell_w<4, 2><<<gc, wide_threads(2), s.wide_smem, st>>>(a, s.sca, cur); break;
-          default: k_cell_w<2, 4><<<gc, wide_threads(4), s.wide_smem, st>>>(a, s.sca, cur); break;
+          case 1: k_cell_w<4, 4, 16><<<gc, wide_threads(4, 16), s.wide_smem, st>>>(a, s.sca, cur); break;
+          case 2: k_cell_w<2, 2, 16><<<gc, wide_threads(2, 16), s.wide_smem, st>>>(a, s.sca, cur); break;
+          case 3: k_cell_w<4, 2, 16><<<gc, wide_threads(2, 16), s.wide_smem, st>>>(a, s.sca, cur); break;
+          case 4: k_cell_w<2, 4, 8><<<g8, wide_threads(4, 8), s.wide_smem8, st>>>(a, s.sca, cur); break;
+          case 5: k_cell_w<4, 4, 8><<<g8, wide_threads(4, 8), s.wide_smem8, st>>>(a, s.sca, cur); break;
+          case 6: k_cell_w<2, 2, 8><<<g8, wide_threads(2, 8), s.wide_smem8, st>>>(a, s.sca, cur); break;
+          case 7: k_cell_w<4, 2, 8><<<g8, wide_threads(2, 8), s.wide_smem8, st>>>(a, s.sca, cur); break;
+          default: k_cell_w<2, 4, 16><<<gc, wide_threads(4, 16), s.wide_smem, st>>>(a, s.sca, cur); break;
         }
       }
       else if (s.stream_groups == 4) k_cell_s<4><<<gc, 512, s.stream_smem, st>>>(a, s.sca, cur);
@@ -1369,7 +1379,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
     const size_t need = (size_t)kStreamSlots * kStreamChunk + 64 + 2 * (size_t)s.max_m * s.max_K * kStreamST * 4 +
                         8 * (size_t)s.max_K;
     const bool narrow = !s.factor_last && s.max_K <= 128 && need <= (size_t)dev_smem;
-    const size_t wneed = wide_smem_bytes(s.max_m, s.max_K, s.factor_last);
+    const size_t wneed = wide_smem_bytes(s.max_m, s.max_K, s.factor_last, 16);
     const bool wide = s.max_K <= kWideMaxK && wneed <= (size_t)dev_smem;
     if (narrow || wide) {
       std::vector<float> blob;
@@ -1399,6 +1409,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
         s.stream_ok = true;
       } else {
         s.wide_smem = wneed;
+        s.wide_smem8 = wide_smem_bytes(s.max_m, s.max_K, s.factor_last, 8);
         s.wide_blob = true;
         s.wide_ok = true;
       }
@@ -1867,7 +1878,7 @@ mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources,
     }
     if (groups > 0) {
       if (s->wide_ok && !s->stream_ok) {
-        MSS_REQUIRE(groups <= 4, MSS_ERR_INVALID_ARG, "wide streamed kernel variant must be 1..4");
+        MSS_REQUIRE(groups <= 8, MSS_ERR_INVALID_ARG, "wide streamed kernel variant must be 1..8");
         s->wide_var = groups - 1;
       } else {
         MSS_REQUIRE(groups == 2 || groups == 4, MSS_ERR_INVALID_ARG, "thread groups must be 2 or 4");
@@ -1940,7 +1951,7 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
             if (st < 8 && st != s->st_max) continue;
             if (streamed && st != kStreamST) continue;
             if (k == MSS_SCHED_GRAPH_STREAM && !s->stream_ok) {
-              for (int wv = 0; wv < 4; ++wv) cands.push_back({k, st, nt0, g0, wv});
+              for (int wv = 0; wv < 8; ++wv) cands.push_back({k, st, nt0, g0, wv});
             } else if (k == MSS_SCHED_GRAPH_STREAM) {
               for (int gv : {4, 2}) cands.push_back({k, st, nt0, gv, s->wide_var});
             } else {

@@ -160,10 +160,11 @@ def test_wide_streamed_kernel_bit_identical_unfactored(P, case):
 
 @pytest.mark.parametrize("factor_last", [False, True])
 def test_wide_kernel_variants_bit_identical(P, case, factor_last):
-    """Unroll depth 2/4 and 4/2 rows per thread: the same multiply-adds in the same order."""
+    """Unroll depth 2/4, 4/2 rows per thread, 16/8 sources per CTA: the same multiply-adds in the same
+    order."""
     c16 = case["wide"]
     ref = _run(P, c16, P.FP32, factor_last=factor_last, sched=P.SCHED_GRAPH)
-    for v in (1, 2, 3, 4):
+    for v in range(1, 9):
         assert np.array_equal(_run_variant(P, c16, factor_last, v), ref), v
 
 
