@@ -381,12 +381,14 @@ def run_native(args):
     if args.profile:
         sim = P.Sim(LR, P.FP32, tau, corner_correction=True, factor_last=factor)
         sim.set_schedule(args.sched)
+        if args.wide_var:
+            sim.set_tile(groups=args.wide_var)
         tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
         sim.step(args.profile, wd, tr, use_graph=False)
         torch.cuda.synchronize()
         sim.info()
         print(json.dumps({"profile_steps": args.profile, "factor_last": factor, "schedule": SCHED_NAMES[args.sched],
-                          "K_max": max(Ks)}))
+                          "tile": sim.tile(), "K_max": max(Ks)}))
         return
     # ---- headline: FP32 stepping, the last coefficient applied as its Cholesky factor
     sim = P.Sim(LR, P.FP32, tau, corner_correction=True, factor_last=factor)
@@ -450,7 +452,7 @@ def run_native(args):
                 "frac": achieved_tf / alu_peak, "traffic": traffic}
     roof.update({"kernel": kname, "algorithmic_bytes_per_launch": algo_bytes,
                  "algorithmic_flops_per_launch": algo_flops, "intensity_flop_per_byte": intensity,
-                 "ms_per_launch": ms[0], "fp32_alu_frac": achieved_tf / alu_peak, "fp32_alu_peak_tflops": alu_peak,
+                 "ms_per_launch": ms[0], "tile": sim.tile(), "fp32_alu_frac": achieved_tf / alu_peak, "fp32_alu_peak_tflops": alu_peak,
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
                  "other_kernels_ms": {"k_face": ms[1], "k_corner": ms[2]}})
     # ---- FP64 ROM stepping (same coefficients), one run
@@ -961,6 +963,8 @@ def main():
     ap.add_argument("--profile", type=int, default=0, help="run N eager time steps after setup and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32_tc", "bf16_tc"], help="precision of the --profile run")
     ap.add_argument("--sched", type=int, default=0, choices=[0, 1, 2, 3, 4], help="schedule of the --profile run")
+    ap.add_argument("--wide-var", type=int, default=0, choices=range(0, 9),
+                    help="wide cell kernel variant 1..8 of the --profile run (0: the default)")
     ap.add_argument("--many-sources", action="store_true",
                     help="measure the 4096-cell, 256-source launch shape instead (separate JSON line)")
     ap.add_argument("--many-steps", type=int, default=200, help="time steps per timed run of --many-sources")

@@ -4,8 +4,8 @@
 // At the paper's operating point (cells about one wavelength across, K~ = 180-294, Section 7) a
 // cell's 2m-1 coefficient matrices hold about 2 MB per step, more than the L2 share of the CTAs
 // resident at once, so the stream is moved by the copy engine, not by thread loads: one thread
-// issues 1-D bulk copies (cp.async.bulk) of whole stored rows into a ring of four 16 KB
-// shared-memory slots, each guarded by an mbarrier with a transaction count, and the threads
+// issues 1-D bulk copies (cp.async.bulk) of whole stored rows into a ring of 16 KB shared-memory
+// slots (eight per SM), each guarded by an mbarrier with a transaction count, and the threads
 // consume them.  Thread (q, g): g = tid % 4 picks 4 of the 16 sources, q = tid / 4 the R
 // consecutive output rows Rq .. Rq+R-1 (R = 4 or 2).  Row j of a stored symmetric matrix is also
 // its column j, so
@@ -36,15 +36,17 @@ constexpr int kWideCP = 4;          // sources per thread (four 4-source groups 
 // threads of the wide kernel with R consecutive rows per thread and NS-source tiles: NS / 4 source
 // groups x K_max / R
 __host__ __device__ constexpr int wide_threads(int R, int NS) { return NS / 4 * kWideMaxK / R; }
-// ring slots of the wide kernel: four 16 KB slots with 16-source tiles; two with 8-source tiles,
-// whose smaller operand blocks then let two CTAs share an SM
-__host__ __device__ constexpr int wide_slots(int NS) { return NS == 16 ? 4 : 2; }
+// ring slots of the wide kernel: eight 16 KB slots with 16-source tiles; four with 8-source tiles,
+// whose smaller operand block then lets two CTAs share an SM (eight slots per SM either way)
+__host__ __device__ constexpr int wide_slots(int NS) { return NS == 16 ? 8 : 4; }
 
-// Shared memory of the wide kernel with NS-source tiles: ring and its barriers, U/F (X) and D/E
-// (D) as m K NS floats each, the factored product's y (K NS floats), the K boundary-row indices.
+// Shared memory of the wide kernel with NS-source tiles: ring, a 128-byte header (the slots'
+// barriers, release counts and issue count), one operand block of m K NS floats (U, then D^k,
+// then F^k, then E^k, each in place), the factored product's y (K NS floats), the K boundary-row
+// indices.
 inline size_t wide_smem_bytes(int max_m, int max_K, int factor_last, int NS) {
-  return (size_t)wide_slots(NS) * kStreamChunk + 64 +
-         (2 * (size_t)max_m * max_K * NS + (factor_last ? (size_t)max_K * NS : 0)) * 4 + 8 * (size_t)max_K;
+  return (size_t)wide_slots(NS) * kStreamChunk + 128 +
+         ((size_t)max_m * max_K * NS + (factor_last ? (size_t)max_K * NS : 0)) * 4 + 8 * (size_t)max_K;
 }
 
 // R consecutive floats of a slot row (16-byte or 8-byte aligned: Kq and r4 are multiples of R)
@@ -79,12 +81,11 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   const int tid = threadIdx.x;
   const bool fac = a.factor_last != 0;
   unsigned char *ring = smem;
+  // header: the slots' barriers, per-slot release counts of the warps, the chunks issued so far
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + SL * kStreamChunk);
-  // after the four barriers: per-slot release counts of the warps, and the chunks issued so far
-  unsigned *released = reinterpret_cast<unsigned *>(smem + SL * kStreamChunk + 32);
+  unsigned *released = reinterpret_cast<unsigned *>(smem + SL * kStreamChunk + 64);
   unsigned *issued = released + SL;
-  float *X = reinterpret_cast<float *>(smem + SL * kStreamChunk + 64);
-  float *D = X + (size_t)m * K * ST;
+  float *D = reinterpret_cast<float *>(smem + SL * kStreamChunk + 128);
   float *Ys = D + (size_t)m * K * ST;
   int64_t *rows = reinterpret_cast<int64_t *>(Ys + (fac ? (size_t)K * ST : 0));
   const float *fs = cur ? a.fstate1 : a.fstate0;
@@ -110,33 +111,39 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
     *issued = (unsigned)min(nch, SL);
     for (int c = 0; c < min(nch, SL); ++c) issue(c);
   }
-  // operands: U (face rows gathered, then interior layers), then D^k = U^{k+1} - U^k
+  // operand block: U (face rows gathered, then interior layers), then D^k = U^{k+1} - U^k in place
   for (int r = tid; r < K; r += blockDim.x) rows[r] = a.row_face_row[rp + r] * 2 + a.row_side[rp + r];
   __syncthreads();
   const bool vec = (ns == ST) && (S % 4 == 0);
   if (vec) {
     for (int i = tid; i < K * (ST / 4); i += blockDim.x) {
       const int r = i / (ST / 4), v = i - r * (ST / 4);
-      reinterpret_cast<float4 *>(X)[i] = *reinterpret_cast<const float4 *>(fs + (rows[r] >> 1) * S + s0 + v * 4);
+      reinterpret_cast<float4 *>(D)[i] = *reinterpret_cast<const float4 *>(fs + (rows[r] >> 1) * S + s0 + v * 4);
     }
     for (int i = tid; i < (m - 1) * K * (ST / 4); i += blockDim.x) {
       const int r = i / (ST / 4), v = i - r * (ST / 4);
-      reinterpret_cast<float4 *>(X + (size_t)K * ST)[i] = *reinterpret_cast<const float4 *>(cs + (so + r) * S + s0 + v * 4);
+      reinterpret_cast<float4 *>(D + (size_t)K * ST)[i] = *reinterpret_cast<const float4 *>(cs + (so + r) * S + s0 + v * 4);
     }
   } else {
     for (int i = tid; i < K * ST; i += blockDim.x) {
       const int r = i / ST, s = i - r * ST;
-      X[i] = s < ns ? fs[(rows[r] >> 1) * S + s0 + s] : 0.f;
+      D[i] = s < ns ? fs[(rows[r] >> 1) * S + s0 + s] : 0.f;
     }
     for (int i = tid; i < (m - 1) * K * ST; i += blockDim.x) {
       const int r = i / ST, s = i - r * ST;
-      X[(size_t)K * ST + i] = s < ns ? cs[(so + r) * S + s0 + s] : 0.f;
+      D[(size_t)K * ST + i] = s < ns ? cs[(so + r) * S + s0 + s] : 0.f;
     }
   }
   __syncthreads();
-  for (int i = tid; i < m * K * ST; i += blockDim.x) {
-    const int k = i / (K * ST);
-    D[i] = (k + 1 < m ? X[i + (size_t)K * ST] : 0.f) - X[i];
+  // one thread per (row, source) position walks the layers upwards, so U^{k+1} is read before
+  // its own difference overwrites it
+  for (int p = tid; p < K * ST; p += blockDim.x) {
+    float u = D[p];
+    for (int k = 0; k < m; ++k) {
+      const float un = k + 1 < m ? D[(size_t)(k + 1) * K * ST + p] : 0.f;
+      D[(size_t)k * K * ST + p] = un - u;
+      u = un;
+    }
   }
   __syncthreads();
   // consecutive threads share a row quad (one broadcast 16-byte coefficient load) and take its four
@@ -171,23 +178,22 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
   wait_chunk(0);
   for (int q = 0; q < 2 * m - 1; ++q) {
     if (q == m) {
-      // all fluxes are in X: publish F^1, then E^k = F^k - F^{k-1} into D
+      // all fluxes are in the operand block: publish F^1, then E^k = F^k - F^{k-1} in place
       __syncthreads();
       if (vec) {
         for (int i = tid; i < K * (ST / 4); i += blockDim.x) {
           const int r = i / (ST / 4), v = i - r * (ST / 4);
-          *reinterpret_cast<float4 *>(a.flux + rows[r] * S + s0 + v * 4) = reinterpret_cast<const float4 *>(X)[i];
+          *reinterpret_cast<float4 *>(a.flux + rows[r] * S + s0 + v * 4) = reinterpret_cast<const float4 *>(D)[i];
         }
       } else {
         for (int i = tid; i < K * ST; i += blockDim.x) {
           const int r = i / ST, s = i - r * ST;
-          if (s < ns) a.flux[rows[r] * S + s0 + s] = X[i];
+          if (s < ns) a.flux[rows[r] * S + s0 + s] = D[i];
         }
       }
-      for (int i = tid; i < (m - 1) * K * ST; i += blockDim.x) {
-        const size_t jj = (size_t)K * ST + i;
-        D[jj] = X[jj] - X[jj - (size_t)K * ST];
-      }
+      // layers downwards per position, so F^{k-1} is read before it becomes E^{k-1}
+      for (int p = tid; p < K * ST; p += blockDim.x)
+        for (int k = m - 1; k >= 1; --k) D[(size_t)k * K * ST + p] -= D[(size_t)(k - 1) * K * ST + p];
       __syncthreads();
     }
     const int layer = q < m ? q : q - m + 1;
@@ -268,13 +274,15 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
       }
       j0 = j1;
     }
-    // end of matrix q: rows of F^{q+1}, or leapfrog of U^k with Gamma-hat^k E^k
+    // end of matrix q: rows of F^{q+1} (over D^{q+1}, once every warp has passed it), or leapfrog of
+    // U^k with Gamma-hat^k E^k
+    if (q < m) __syncthreads();
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       if (!act[i]) continue;
       const int r = rr[i];
       if (q < m) {
-        *reinterpret_cast<float4 *>(X + ((size_t)q * K + r) * ST + CP * g) =
+        *reinterpret_cast<float4 *>(D + ((size_t)q * K + r) * ST + CP * g) =
             make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
       } else {
         const int k = q - m + 1;
@@ -317,7 +325,7 @@ __device__ bool cell_wide_item(const StepArgs<float> &a, const StreamArgs &t, co
     // no interior layers: publish F^1 here
     for (int i = tid; i < K * ST; i += blockDim.x) {
       const int r = i / ST, s = i - r * ST;
-      if (s < ns) a.flux[rows[r] * S + s0 + s] = X[i];
+      if (s < ns) a.flux[rows[r] * S + s0 + s] = D[i];
     }
   }
   gc = gc0 + (unsigned)nch;
