@@ -379,57 +379,26 @@ def run_native(args):
     wd = torch.tensor(w, device=dev)
     factor = not args.plain_fp32
     if args.profile:
-        sim = P.Sim(LR, P.FP32, tau, corner_correction=True, factor_last=factor)
-        sim.set_schedule(args.sched)
+        if args.prec_profile == "tf32_tc":
+            sim = P.Sim(LR, P.TF32_TC, tau, corner_correction=True)
+        else:
+            sim = P.Sim(LR, P.FP32, tau, corner_correction=True, factor_last=factor)
+            sim.set_schedule(args.sched)
         if args.wide_var:
             sim.set_tile(groups=args.wide_var)
         tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
         sim.step(args.profile, wd, tr, use_graph=False)
         torch.cuda.synchronize()
         sim.info()
-        print(json.dumps({"profile_steps": args.profile, "factor_last": factor, "schedule": SCHED_NAMES[args.sched],
+        print(json.dumps({"profile_steps": args.profile, "precision": args.prec_profile, "factor_last": factor,
+                          "schedule": SCHED_NAMES[sim.schedule()[0]],
                           "tile": sim.tile(), "K_max": max(Ks)}))
         return
-    # ---- headline: FP32 stepping, the last coefficient applied as its Cholesky factor
-    sim = P.Sim(LR, P.FP32, tau, corner_correction=True, factor_last=factor)
-    kper = int(sim.info()[6])
-    sched, sched_ms = sim.autotune(100)
-    tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+    # ---- candidate headline arms: FP32 on the CUDA cores (autotuned schedule and tile, the last
+    # coefficient applied as its Cholesky factor), and FP32-class products on the tensor cores
+    # (TF32 split hi + lo, the wide tcgen05 kernel); each timed the same way, the faster one whose
+    # traces stay within the FP32 class of the FP64 ROM is the headline
     flush = torch.empty(int(512e6) // 4, device=dev, dtype=torch.float32)
-    _timed_runs(sim, nst, wd, tr, args.warmup, stream)       # warm-up (captures the CUDA graph)
-    torch.cuda.synchronize()
-    clocks = Clocks(torch.cuda.current_device())
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    times = _timed_runs(sim, nst, wd, tr, args.steps, stream, flush)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ck = clocks.stop()
-    value, t_step = whole_job_rate(units, statistics.mean(times), world, dist, dev)
-    sim.info()                                              # raises if a bounded device wait gave up
-    tr32 = tr.double().cpu().numpy()
-    # ---- per-kernel timing (eager, CUDA events on the launching stream): the cell kernel of the
-    # chosen schedule (the persistent schedule runs the plain cell body inside one kernel, so the
-    # graph schedule stands in for it)
-    prof_sched = {P.SCHED_PERSIST: P.SCHED_GRAPH, P.SCHED_PERSIST_STREAM: P.SCHED_GRAPH_STREAM}.get(sched, sched)
-    sim.set_schedule(prof_sched)
-    sim.reset()
-    ms = sim.step_profile(200, wd, tr)
-    sim.set_schedule(sched)
-    wide = max(Ks) > 128 or factor
-    if prof_sched == P.SCHED_GRAPH_STREAM:
-        kname = "k_cell_w (wide TMA-streamed)" if wide else "k_cell_s"
-    elif prof_sched == P.SCHED_GRAPH_SPLIT:
-        kname = "k_flux+k_accel"
-    else:
-        kname = "k_cell<float,16> (factored last coefficient)" if factor else "k_cell<float,16>"
-    ksrc = {"k_cell_w (wide TMA-streamed)": ["cell_wide.cuh", "cell_stream.cuh", "online.cu"],
-            "k_cell_s": ["cell_stream.cuh", "online.cu"], "k_flux+k_accel": ["cell_split.cuh", "online.cu"]}.get(
-        kname, ["online.cu"])
-    algo_bytes, algo_flops = _kernel_model(None, Ks, cm, S, 4)
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
@@ -438,23 +407,75 @@ def run_native(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12            # FP32 FMA lanes x 2 flops x clock (TFLOP/s)
-    cell_s = ms[0] / 1e3
-    achieved_gbs = algo_bytes / cell_s / 1e9
-    achieved_tf = algo_flops / cell_s / 1e12
-    ridge = alu_peak * 1e12 / (hbm * 1e9)
-    intensity = algo_flops / algo_bytes
-    traffic = _traffic_record(kname, ksrc)
-    if intensity < ridge:
+    algo_bytes, algo_flops = _kernel_model(None, Ks, cm, S, 4)
+
+    def measure(sim, sched, kname, ksrc):
+        tr = torch.zeros((nst, R, S), device=dev, dtype=torch.float32)
+        _timed_runs(sim, nst, wd, tr, args.warmup, stream)       # warm-up (captures the CUDA graph)
+        torch.cuda.synchronize()
+        clocks = Clocks(torch.cuda.current_device())
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        times = _timed_runs(sim, nst, wd, tr, args.steps, stream, flush)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ck = clocks.stop()
+        value, t_step = whole_job_rate(units, statistics.mean(times), world, dist, dev)
+        sim.info()                                              # raises if a bounded device wait gave up
+        trn = tr.double().cpu().numpy()
+        # per-kernel timing (eager, CUDA events on the launching stream): the cell kernel of the
+        # chosen schedule (the persistent schedule runs the plain cell body inside one kernel, so
+        # the graph schedule stands in for it)
+        prof_sched = {P.SCHED_PERSIST: P.SCHED_GRAPH, P.SCHED_PERSIST_STREAM: P.SCHED_GRAPH_STREAM}.get(sched, sched)
+        sim.set_schedule(prof_sched)
+        sim.reset()
+        ms = sim.step_profile(200, wd, tr)
+        sim.set_schedule(sched)
+        cell_s = ms[0] / 1e3
+        achieved_gbs = algo_bytes / cell_s / 1e9
+        achieved_tf = algo_flops / cell_s / 1e12
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
-                "traffic": traffic}
+                "traffic": _traffic_record(kname, ksrc)}
+        if algo_flops / algo_bytes >= alu_peak * 1e12 / (hbm * 1e9) and "tensor" not in kname:
+            roof = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved_tf / alu_peak, "traffic": roof["traffic"]}
+        roof.update({"kernel": kname, "algorithmic_bytes_per_launch": algo_bytes,
+                     "algorithmic_flops_per_launch": algo_flops, "intensity_flop_per_byte": algo_flops / algo_bytes,
+                     "ms_per_launch": ms[0], "tile": sim.tile(), "fp32_alu_frac": achieved_tf / alu_peak,
+                     "fp32_alu_peak_tflops": alu_peak,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
+                     "other_kernels_ms": {"k_face": ms[1], "k_corner": ms[2]}})
+        return {"sim": sim, "sched": sched, "value": value, "t_step": t_step, "clocks": ck, "tr": trn, "roof": roof,
+                "kper": int(sim.info()[6])}
+
+    arms = {}
+    sim = P.Sim(LR, P.FP32, tau, corner_correction=True, factor_last=factor)
+    sched, sched_ms = sim.autotune(100)
+    wide = max(Ks) > 128 or factor
+    if sched in (P.SCHED_GRAPH_STREAM, P.SCHED_PERSIST_STREAM):
+        kname = "k_cell_w (wide TMA-streamed)" if wide else "k_cell_s"
+    elif sched == P.SCHED_GRAPH_SPLIT:
+        kname = "k_flux+k_accel"
     else:
-        roof = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / alu_peak, "traffic": traffic}
-    roof.update({"kernel": kname, "algorithmic_bytes_per_launch": algo_bytes,
-                 "algorithmic_flops_per_launch": algo_flops, "intensity_flop_per_byte": intensity,
-                 "ms_per_launch": ms[0], "tile": sim.tile(), "fp32_alu_frac": achieved_tf / alu_peak, "fp32_alu_peak_tflops": alu_peak,
-                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
-                 "other_kernels_ms": {"k_face": ms[1], "k_corner": ms[2]}})
+        kname = "k_cell<float,16> (factored last coefficient)" if factor else "k_cell<float,16>"
+    ksrc = {"k_cell_w (wide TMA-streamed)": ["cell_wide.cuh", "cell_stream.cuh", "online.cu"],
+            "k_cell_s": ["cell_stream.cuh", "online.cu"], "k_flux+k_accel": ["cell_split.cuh", "online.cu"]}.get(
+        kname, ["online.cu"])
+    arms["fp32"] = measure(sim, sched, kname, ksrc)
+    arms["fp32"]["autotune"] = {SCHED_NAMES[k]: (float(sched_ms[k]) if sched_ms[k] >= 0 else None)
+                                for k in range(len(SCHED_NAMES))}
+    tw_note = None
+    if factor and args.arm in ("auto", "tf32_tc"):
+        try:
+            simtw = P.Sim(LR, P.TF32_TC, tau, corner_correction=True)
+        except P.MssError as ex:
+            tw_note = str(ex)
+        else:
+            arms["tf32_tc"] = measure(simtw, P.SCHED_GRAPH, "k_cell_tw (tensor-core TF32 split)",
+                                      ["cell_tw.cuh", "cell_tc.cuh", "online.cu"])
     # ---- FP64 ROM stepping (same coefficients), one run
     sim64 = P.Sim(LR, P.FP64, tau, corner_correction=True)
     tr64 = torch.zeros((nst, R, S), device=dev, dtype=torch.float64)
@@ -476,11 +497,30 @@ def run_native(args):
     tfine = statistics.mean(fine_times)
     fine32 = trf.double().cpu().numpy()
     del fine, trf
+    # ---- the headline arm: the fastest whose traces stay within FP32 class (1e-3) of the FP64 ROM
+    for k, arm in arms.items():
+        arm["vs_rom_fp64"] = _rel(arm["tr"], rom64)
+    ok = [k for k, arm in arms.items() if arm["vs_rom_fp64"] <= 1e-3] or ["fp32"]
+    head = min(ok, key=lambda k: arms[k]["t_step"])
+    if args.arm != "auto" and args.arm in arms:
+        head = args.arm
+    H = arms[head]
+    sim, sched, value, t_step, ck, roof = H["sim"], H["sched"], H["value"], H["t_step"], H["clocks"], H["roof"]
+    tr32, kper = H["tr"], H["kper"]
     err = _rel(tr32, ref)
     acc = {"target": ACCURACY_TARGET, "reference": "same GPU's FP64 fine-grid leapfrog on the original graph",
            "rom_fp32_vs_fine_fp64": err, "rom_fp32_vs_fine_fp64_max_per_receiver": _per_receiver(tr32, ref),
            "rom_fp64_vs_fine_fp64": _rel(rom64, ref), "rom_fp32_vs_rom_fp64": _rel(tr32, rom64),
            "fine_fp32_vs_fine_fp64": _rel(fine32, ref), "met": bool(err <= ACCURACY_TARGET)}
+    other = {}
+    for k, arm in arms.items():
+        if k != head:
+            other[k] = {"value": arm["value"], "unit": UNIT, "ms_per_step": 1e3 * arm["t_step"],
+                        "schedule": SCHED_NAMES[arm["sched"]], "rom_vs_rom_fp64": arm["vs_rom_fp64"],
+                        "rom_vs_fine_fp64": _rel(arm["tr"], ref), "cell_kernel": arm["roof"]["kernel"],
+                        "cell_kernel_ms": arm["roof"]["ms_per_launch"], "cell_kernel_hbm_frac": arm["roof"]["frac"]}
+    if tw_note:
+        other["tf32_tc"] = {"unavailable": tw_note}
     # ---- end to end through the C ABI with host buffers (H2D waveform, D2H traces)
     e2e_times = []
     for _ in range(max(1, args.steps)):
@@ -510,16 +550,19 @@ def run_native(args):
                 P.SCHED_GRAPH_SPLIT: nst * (kper + 1)}.get(sched, -(-nst // 512))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(wl, {"precision": "fp32 state and coefficients, last coefficient as its Cholesky "
-                                                "factor" if factor else "fp32 state and coefficients",
+            "vs_baseline": None, "dtype": "tf32x3+f32" if head == "tf32_tc" else "f32", "data": "synthetic",
+            "config": _config(wl, {"precision": ("fp32 state and coefficients, cell products on the tensor cores "
+                                                 "as TF32 with both operands split hi + lo (three products), last "
+                                                 "coefficient as its Cholesky factor") if head == "tf32_tc" else
+                                                ("fp32 state and coefficients, last coefficient as its Cholesky "
+                                                 "factor" if factor else "fp32 state and coefficients"),
                                    "corner_correction": True, "K_max": max(Ks), "tau": tau,
                                    "l2": "flushed between steps (512 MB write)",
                                    "parallelism": "independent source batches per GPU" if world > 1 else "single GPU"}),
             "clocks": ck, "gpu_launches": int(args.steps * launches),
-            "schedule": {"chosen": SCHED_NAMES[sched],
-                         "autotune_ms_per_time_step": {SCHED_NAMES[k]: (float(sched_ms[k]) if sched_ms[k] >= 0 else None)
-                                                       for k in range(len(SCHED_NAMES))}},
+            "schedule": {"chosen": SCHED_NAMES[sched], "arm": head,
+                         "fp32_autotune_ms_per_time_step": arms["fp32"]["autotune"]},
+            "other_arms": other,
             "receiver_rel_l2": acc,
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "fine_grid": {"value": units / tfine, "unit": UNIT, "ms": 1e3 * tfine,
@@ -529,8 +572,8 @@ def run_native(args):
                                   "same partition"},
             "speedup_vs_fine_grid": tfine / t_step,
             "fp64_rom": {"value": units / t64, "unit": UNIT, "ms": 1e3 * t64},
-            "fp32_tc": {"unavailable": "tensor-core cell kernels need K_i <= 128; this workload has K up to %d"
-                                      % max(Ks)} if max(Ks) > 128 else None,
+            "fp32_tc": {"unavailable": "split-BF16 tensor-core cell kernels need K_i <= 128; this workload has K "
+                                      "up to %d (the TF32 tensor-core arm covers it)" % max(Ks)} if max(Ks) > 128 else None,
             "offline_s": {"assemble_partition_cfl": t1 - t0, "gpu_rom_build": t2 - t1},
             "stability": stability}
     print(json.dumps(line))
@@ -963,6 +1006,10 @@ def main():
     ap.add_argument("--profile", type=int, default=0, help="run N eager time steps after setup and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32_tc", "bf16_tc"], help="precision of the --profile run")
     ap.add_argument("--sched", type=int, default=0, choices=[0, 1, 2, 3, 4], help="schedule of the --profile run")
+    ap.add_argument("--arm", default="auto", choices=["auto", "fp32", "tf32_tc"],
+                    help="headline arm (auto: the faster FP32-class one)")
+    ap.add_argument("--prec-profile", default="fp32", choices=["fp32", "tf32_tc"],
+                    help="precision of the default workload's --profile run")
     ap.add_argument("--wide-var", type=int, default=0, choices=range(0, 9),
                     help="wide cell kernel variant 1..8 of the --profile run (0: the default)")
     ap.add_argument("--many-sources", action="store_true",

@@ -59,7 +59,7 @@ enum { MSS_DIRICHLET = 0, MSS_NEUMANN = 1 };
 /* Precisions of the on-line stage.  MSS_FP32_TC: FP32 state, cell products on the tensor cores
  * (tcgen05, BF16 operands split into hi + lo parts, three products, FP32 accumulation);
  * MSS_BF16_TC: the same with one BF16 product.  Tensor-core modes need K_i <= 128. */
-enum { MSS_FP64 = 0, MSS_FP32 = 1, MSS_FP32_TC = 2, MSS_BF16_TC = 3 };
+enum { MSS_FP64 = 0, MSS_FP32 = 1, MSS_FP32_TC = 2, MSS_BF16_TC = 3, MSS_TF32_TC = 4 };
 
 const char *mss_status_string(mss_status s);
 /* Reason of the last failed call on this thread ("" if none). */
@@ -254,9 +254,13 @@ typedef struct mss_sim mss_sim;
  *   then (if enabled) the Appendix D correction of the new u~;
  * trace sample n = sum_f q~_f^T u~_f at step n (before it is advanced).
  * precision: MSS_FP64, MSS_FP32 (state, coefficients and arithmetic), MSS_FP32_TC or MSS_BF16_TC
- * (FP32 state, tensor-core cell products; traces are float).
+ * (FP32 state, tensor-core cell products with BF16 operands, split hi + lo for FP32_TC; K_i <= 128;
+ * traces are float), MSS_TF32_TC (FP32 state and coefficients, cell products on the tensor cores as
+ * TF32 with both operands split hi + lo, three products per pair, FP32-class; K_i <= 384 and
+ * 2 m_i ceil(K_i / 128) <= 32; the last coefficient always applied as its Cholesky factor, as with
+ * MSS_SIM_FACTOR_LAST below; schedule GRAPH; traces are float).
  * flags: MSS_SIM_CORNERS (the Appendix D correction; 1 keeps its old meaning) | MSS_SIM_FACTOR_LAST
- * (MSS_FP32 only: the last coefficient is applied as F^m = L (L^T D^m), L the lower Cholesky factor
+ * (MSS_FP32 and MSS_TF32_TC: the last coefficient is applied as F^m = L (L^T D^m), L the lower Cholesky factor
  * of Gamma^m computed in FP64 at creation, pivots at or below 1e-13 of its largest diagonal entry
  * raised to that floor; stored as one K x K matrix W = L + L^T - diag(L), so the coefficient bytes
  * do not change.  Rounding the entries of a nearly singular Gamma^m -- a cell without a Dirichlet
@@ -338,8 +342,9 @@ mss_status mss_sim_check_stability(mss_sim *s, int32_t n_steps, uint64_t seed, d
  * which the kernel records MSS_ERR_TIMEOUT in the sim's error word and returns):
  *   MSS_DEBUG_GRID_EXTRA_ARRIVALS  the persistent CUDA-core kernel's grid barrier waits for
  *                                  `value` CTAs beyond the grid (a missing neighbour);
- *   MSS_DEBUG_TC_EXTRA_TX          the split tensor-core kernels' matrix barrier, and the wide
- *                                  streamed cell kernel's chunk barriers, expect `value` bytes
+ *   MSS_DEBUG_TC_EXTRA_TX          the split tensor-core kernels' matrix barrier, the wide
+ *                                  streamed cell kernel's chunk barriers and the wide tensor-core
+ *                                  (MSS_TF32_TC) kernel's copy barriers expect `value` bytes
  *                                  beyond their copies.
  * value 0 restores normal operation.  mss_sim_clear_error resets the error word (and the grid
  * barrier) after a reported TIMEOUT; the state of the failed steps is undefined (reset or load a

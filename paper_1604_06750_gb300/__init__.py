@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmss.so")
 
-FP64, FP32, FP32_TC, BF16_TC = 0, 1, 2, 3
+FP64, FP32, FP32_TC, BF16_TC, TF32_TC = 0, 1, 2, 3, 4
 SCHED_GRAPH, SCHED_GRAPH_STREAM, SCHED_PERSIST, SCHED_PERSIST_STREAM, SCHED_GRAPH_SPLIT = 0, 1, 2, 3, 4
 SCHED_COUNT = 5
 SIM_CORNERS, SIM_FACTOR_LAST = 1, 2

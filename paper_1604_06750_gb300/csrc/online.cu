@@ -582,6 +582,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_corner(const StepArgs<T> a, co
 #include "cell_split.cuh"
 #include "cell_tc_split.cuh"
 #include "cell_tc_pipe.cuh"
+#include "cell_tw.cuh"
 
 namespace mss {
 
@@ -594,6 +595,7 @@ struct SimDev {
   DevMem coef, minv, src_val, rcv_val, cg_rows, cg_w;
   DevMem fstate[2], cstate[2], flux, uhat, cfaces, wbuf, tbuf;
   DevMem tc_blob, tc_off, tc_Kp, tc_Kr, tc_err;
+  DevMem tw_blob, tw_off;               // wide tensor-core (TF32) cell kernel blob
   DevMem sc_coef, sc_off, sc_Kq, bar;   // streamed cell kernel blob, grid barrier words
   DevMem flux_items, accel_items, f_off, F;   // split cell phase
 };
@@ -626,6 +628,9 @@ struct mss_sim {
   int wide_var = 0;                            // its variant: bit 0 unroll 4 (else 2), bit 1 two rows per
                                                // thread (else 4), bit 2 8-source tiles (else 16)
   mss::TcArgs tca{};
+  int tw = 0;                                  // MSS_TF32_TC: the wide tensor-core cell kernel
+  size_t tw_smem = 0;
+  mss::TwArgs twa{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
   int corners = 0, max_K = 0, max_m = 0, max_M = 0, max_nm = 0, n_cfaces = 0;
   int factor_last = 0;                         // FP32: Gamma^m applied as L (L^T .)
@@ -743,6 +748,7 @@ static void set_smem_attrs(const mss_sim &s) {
     MSS_CUDA(cudaFuncSetAttribute(k_cell_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tc_smem));
   }
   MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
+  if (s.tw) MSS_CUDA(cudaFuncSetAttribute(k_cell_tw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.tw_smem));
   if (s.factor_last)
     MSS_CUDA(cudaFuncSetAttribute(k_cell<T, ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.cell_smem));
   if (s.wide_ok) {
@@ -779,6 +785,10 @@ static void launch_tc(const mss_sim &s, const StepArgs<float> &a, int cur, cudaS
 template <typename T, int ST>
 static void launch_cell(const mss_sim &s, const StepArgs<T> &a, int cur, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
+    if (s.tw) {
+      k_cell_tw<<<s.n_cells * ((s.n_src + kTwNT - 1) / kTwNT), kTwThreads, s.tw_smem, st>>>(a, s.twa, cur);
+      return;
+    }
     if (s.tc && s.sched == MSS_SCHED_PERSIST_STREAM) {
       if (s.tcq_nt == 32) launch_tcp<32>(s, a, cur, st);
       else launch_tcp<16>(s, a, cur, st);
@@ -1127,6 +1137,43 @@ static void build_tc_blob(const Rom &R, std::vector<uint16_t> &blob, std::vector
   }
 }
 
+// Coefficients of every cell in the wide tensor-core kernel's layout (cell_tw.cuh): per cell, the
+// A blocks of its 2m products in the order the kernel consumes them -- Gamma^1..Gamma^{m-1}, the
+// factored last coefficient twice (L^T: W's upper triangle, L: its lower triangle, W = L + L^T -
+// diag(L) at matrix m-1 of coef), Gamma-hat^2..Gamma-hat^m -- each block 128 rows (fewer in the
+// last M tile) x 32 columns (fewer in the last chunk), FP32, K-major core-matrix layout.
+static void build_tw_blob(const Rom &R, const std::vector<double> &coef, const std::vector<int64_t> &cell_coef,
+                          std::vector<float> &blob, std::vector<int64_t> &off) {
+  blob.clear();
+  off.assign(R.n_cells, 0);
+  for (int c = 0; c < R.n_cells; ++c) {
+    const int K = R.cell_K[c], m = R.cell_m[c], K8 = (K + 7) & ~7, MT = tw_mt(K);
+    off[c] = (int64_t)blob.size();
+    for (int j = 0; j < 2 * m; ++j) {
+      const int q = j < m - 1 ? j : (j <= m ? m - 1 : j - 1);
+      const double *A = coef.data() + cell_coef[c] + (size_t)q * K * K;
+      for (int t = 0; t < MT; ++t) {
+        int c0, c1;
+        tw_chunks(j, t, m, K, c0, c1);
+        const int rows = std::min(128, K8 - 128 * t);
+        for (int ch = c0; ch < c1; ++ch) {
+          const int kc = std::min(32, K8 - 32 * ch);
+          const size_t base = blob.size();
+          blob.resize(base + (size_t)rows * kc, 0.f);
+          for (int row = 0; row < rows; ++row)
+            for (int k = 0; k < kc; ++k) {
+              const int gi = 128 * t + row, gk = 32 * ch + k;
+              if (gi >= K || gk >= K) continue;
+              if ((j == m - 1 && gk < gi) || (j == m && gk > gi)) continue;   // the other triangle
+              blob[base + (size_t)(row >> 3) * (8 * kc) + (size_t)(k >> 2) * 32 + (row & 7) * 4 + (k & 3)] =
+                  (float)A[(size_t)gi * K + gk];
+            }
+        }
+      }
+    }
+  }
+}
+
 // Shared memory of the CUDA-core cell kernel: U and D (m K ST values each), the factored last
 // coefficient's intermediate (K ST values, rounded up to even), and the K boundary-row indices.
 static size_t cell_smem_bytes(int max_m, int max_K, int ST, size_t es, int factor_last) {
@@ -1195,11 +1242,11 @@ static void apply_tcs_nt(mss_sim &s, int nt) {
 static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags) {
   MSS_REQUIRE((flags & ~(MSS_SIM_CORNERS | MSS_SIM_FACTOR_LAST)) == 0, MSS_ERR_INVALID_ARG, "unknown sim flags");
   const int corners = flags & MSS_SIM_CORNERS;
-  MSS_REQUIRE(!(flags & MSS_SIM_FACTOR_LAST) || prec == MSS_FP32, MSS_ERR_INVALID_ARG,
-              "the factored last coefficient is an option of MSS_FP32");
-  s.factor_last = (flags & MSS_SIM_FACTOR_LAST) ? 1 : 0;
-  MSS_REQUIRE(prec == MSS_FP64 || prec == MSS_FP32 || prec == MSS_FP32_TC || prec == MSS_BF16_TC, MSS_ERR_INVALID_ARG,
-              "precision must be MSS_FP64, MSS_FP32, MSS_FP32_TC or MSS_BF16_TC");
+  MSS_REQUIRE(!(flags & MSS_SIM_FACTOR_LAST) || prec == MSS_FP32 || prec == MSS_TF32_TC, MSS_ERR_INVALID_ARG,
+              "the factored last coefficient is an option of MSS_FP32 (MSS_TF32_TC always applies it)");
+  s.factor_last = ((flags & MSS_SIM_FACTOR_LAST) || prec == MSS_TF32_TC) ? 1 : 0;
+  MSS_REQUIRE(prec == MSS_FP64 || prec == MSS_FP32 || prec == MSS_FP32_TC || prec == MSS_BF16_TC || prec == MSS_TF32_TC,
+              MSS_ERR_INVALID_ARG, "precision must be MSS_FP64, MSS_FP32, MSS_FP32_TC, MSS_BF16_TC or MSS_TF32_TC");
   MSS_REQUIRE(tau > 0 && std::isfinite(tau), MSS_ERR_CFL, "tau must be positive");
   MSS_REQUIRE(R.has_io, MSS_ERR_STATE, "ROM has no sources/receivers (mss_rom_set_io*)");
   MSS_CUDA(cudaGetDevice(&s.device));
@@ -1352,6 +1399,32 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
     for (int b : bad)
       MSS_REQUIRE(b < 0, MSS_ERR_COEF_NOT_SPD, "last coefficient of cell " + std::to_string(b) + " is indefinite");
   }
+  if (prec == MSS_TF32_TC) {
+    // wide tensor-core kernel: K_i <= 384, 2m accumulators of 16 columns per M tile in TMEM, the
+    // largest copy ring (2..8 slots of 16 KB) that fits beside the stages and B buffers
+    MSS_REQUIRE(s.max_K <= kTwMaxK, MSS_ERR_INVALID_ARG, "MSS_TF32_TC needs K_i <= 384");
+    unsigned cols = 32;
+    for (int c = 0; c < R.n_cells; ++c)
+      while (cols < (unsigned)(2 * R.cell_m[c] * tw_mt(R.cell_K[c]) * kTwNT)) cols <<= 1;
+    MSS_REQUIRE(cols <= 512, MSS_ERR_INVALID_ARG, "MSS_TF32_TC: 2 m_i ceil(K_i / 128) x 16 accumulator columns exceed TMEM");
+    const int k8max = (s.max_K + 7) & ~7;
+    int ring = kTwMaxRing;
+    while (ring > 2 && tw_smem_bytes(ring, k8max) > (size_t)dev_smem) --ring;
+    MSS_REQUIRE(tw_smem_bytes(ring, k8max) <= (size_t)dev_smem, MSS_ERR_INVALID_ARG,
+                "MSS_TF32_TC: cells too large for shared memory");
+    std::vector<float> blob;
+    std::vector<int64_t> off;
+    build_tw_blob(R, coef, cell_coef, blob, off);
+    upload(s.d.tw_blob, blob);
+    upload(s.d.tw_off, off);
+    s.tw = 1;
+    s.tw_smem = tw_smem_bytes(ring, k8max);
+    s.twa.blob = s.d.tw_blob.as<float>();
+    s.twa.blob_off = s.d.tw_off.as<int64_t>();
+    s.twa.ring = ring;
+    s.twa.k8max = k8max;
+    s.twa.tmem_cols = cols;
+  }
   {
     // split cell phase: one item per (cell, matrix) and an F scratch block of m K rows per cell
     std::vector<int2> fi, ai;
@@ -1417,6 +1490,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
   }
   if (!s.tc) upload(s.d.tc_err, std::vector<int>(1, 0));   // error word of the bounded waits
   s.sca.err = s.d.tc_err.as<int>();
+  s.twa.err = s.d.tc_err.as<int>();
   upload(s.d.bar, std::vector<unsigned>(2, 0u));
   std::vector<double> minv(R.fmass_off[R.n_faces]);
   for (int f = 0; f < R.n_faces; ++f) {
@@ -1544,7 +1618,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
     if (prec == MSS_FP64) upload_as<double>(m, v);
     else upload_as<float>(m, v);
   };
-  up(d.coef, s.tc ? std::vector<double>() : coef);
+  up(d.coef, (s.tc || s.tw) ? std::vector<double>() : coef);
   up(d.minv, minv);
   up(d.src_val, R.src_vals);
   up(d.rcv_val, R.rcv_vals);
@@ -1815,6 +1889,7 @@ mss_status mss_step_profile(mss_sim *s, int64_t n_steps, const double *waveform,
 }
 
 static bool sched_allowed(const mss_sim &s, int sched) {
+  if (s.tw) return sched == MSS_SCHED_GRAPH;
   if (s.factor_last)
     return sched == MSS_SCHED_GRAPH || sched == MSS_SCHED_PERSIST || (sched == MSS_SCHED_GRAPH_STREAM && s.wide_ok);
   switch (sched) {
@@ -1843,6 +1918,7 @@ mss_status mss_sim_debug(mss_sim *s, int32_t knob, int32_t value) {
       case MSS_DEBUG_TC_EXTRA_TX:
         s->tca.extra_tx = (unsigned)value;
         s->sca.extra_tx = (unsigned)value;
+        s->twa.extra_tx = (unsigned)value;
         break;
       default: MSS_REQUIRE(false, MSS_ERR_INVALID_ARG, "unknown debug knob");
     }
@@ -2047,7 +2123,7 @@ mss_status mss_run_host(mss_sim *s, int64_t n_steps, const double *waveform_host
     else step_dispatch<float>(*s, n_steps, s->d.wbuf.as<double>(), s->d.tbuf.p, 1, st);
     MSS_CUDA(cudaMemcpyAsync(traces_host, s->d.tbuf.p, tb, cudaMemcpyDeviceToHost, st));
     MSS_CUDA(cudaStreamSynchronize(st));
-    if (s->tc) {
+    if (s->tc || s->tw) {
       int e = 0;
       MSS_CUDA(cudaMemcpy(&e, s->d.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
       MSS_REQUIRE(e == 0, MSS_ERR_TIMEOUT, "a tensor-core cell kernel's bounded wait gave up");

@@ -50,11 +50,13 @@ def _run(P, sim, nst, prec, n_src=16):
     ("fp32", "persist", "grid", 1),
     ("fp32_tc", "split", "tc", 16),
     ("fp32_factored", "stream", "tc", 16),     # the wide TMA-streamed cell kernel's chunk barriers
+    ("tf32_tc", "graph", "tc", 16),            # the wide tensor-core kernel's copy barriers
 ])
 def test_bounded_wait_reports_timeout_and_context_recovers(P, prec, sched, knob, value):
     fac = prec == "fp32_factored"
-    pr = {"fp32": P.FP32, "fp32_tc": P.FP32_TC, "fp32_factored": P.FP32}[prec]
-    sc = {"persist": P.SCHED_PERSIST, "split": P.SCHED_GRAPH_SPLIT, "stream": P.SCHED_GRAPH_STREAM}[sched]
+    pr = {"fp32": P.FP32, "fp32_tc": P.FP32_TC, "fp32_factored": P.FP32, "tf32_tc": P.TF32_TC}[prec]
+    sc = {"persist": P.SCHED_PERSIST, "split": P.SCHED_GRAPH_SPLIT, "stream": P.SCHED_GRAPH_STREAM,
+          "graph": P.SCHED_GRAPH}[sched]
     kb = {"grid": P.DEBUG_GRID_EXTRA_ARRIVALS, "tc": P.DEBUG_TC_EXTRA_TX}[knob]
     ref_sim = _sim(P, pr, factor_last=fac)
     ref_sim.set_schedule(sc)

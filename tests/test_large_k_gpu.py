@@ -123,6 +123,26 @@ def test_fp32_factored_last_parity_at_k270(P, case):
     assert e_fac <= 2.0 * e_plain + 1e-5
 
 
+def test_tf32_tensor_core_parity_at_k270(P, case):
+    """MSS_TF32_TC: every cell product on tcgen05 kind::tf32 with both operands split hi + lo
+    (three products per pair), the last coefficient factored; three M tiles of 128 rows at K = 270.
+    FP32-class: the same bar as the factored FP32 path, and close to it."""
+    ref = case["ref"]
+    tw = _run(P, case, P.TF32_TC)
+    fac = _run(P, case, P.FP32, factor_last=True)
+    e_tw = np.linalg.norm(tw - ref) / np.linalg.norm(ref)
+    print("TF32_TC vs oracle at K=270: %.3e (per receiver %.3e); vs factored FP32 %.3e" %
+          (e_tw, _per_receiver(tw, ref), np.linalg.norm(tw - fac) / np.linalg.norm(ref)))
+    assert e_tw <= FP32_TOL
+    assert _per_receiver(tw, ref) <= FP32_TOL
+    assert np.linalg.norm(tw - fac) <= FP32_TOL * np.linalg.norm(ref)
+    c16 = case["wide"]
+    a = _run(P, c16, P.TF32_TC)
+    b = _run(P, c16, P.FP32, factor_last=True)
+    assert np.linalg.norm(b) > 0
+    assert np.linalg.norm(a - b) <= FP32_TOL * np.linalg.norm(b)
+
+
 def test_factored_schedules_bit_identical(P, case):
     """Plain cell kernel (graph), persistent kernel, and the TMA-streamed wide kernel (rows of the
     factored coefficient met in descending order) give the same bits."""

@@ -250,6 +250,47 @@ def test_tensor_core_parity_ragged(P, n_src):
     assert errs[P.FP32_TC] < errs[P.BF16_TC]
 
 
+TF32_TOL = 1e-3   # TF32_TC: split TF32 (three products), FP32-class
+
+
+def _worst_receiver(a, b):
+    return max(float(np.linalg.norm(a[:, r] - b[:, r]) / np.linalg.norm(b[:, r]))
+               for r in range(b.shape[1]) if np.linalg.norm(b[:, r]) > 1e-12 * np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n_src", [1, 16, 37])
+def test_tf32_tensor_core_parity_ragged(P, n_src):
+    """The wide tensor-core kernel (MSS_TF32_TC) on small ragged cells (m = 2..4, uneven K, one
+    M tile): 1 and 37 sources exercise a partial 16-source tile, 37 three tiles per cell."""
+    topo, co, src, rcv = _random_case(n_src=n_src, seed=60 + n_src)
+    tau, nst = 0.08, 150
+    w = synth.ricker(np.arange(nst) * tau, 0.6)
+    ref = _oracle(topo, co, src, rcv, n_src, 4, w, tau, nst)
+    out, sim = _lib_run(P, topo, co, src, rcv, n_src, 4, w, tau, nst, P.TF32_TC)
+    assert sim.schedule()[1].tolist() == [1, 0, 0, 0, 0]
+    assert _rel(out, ref) <= TF32_TOL
+    assert _worst_receiver(out, ref) <= TF32_TOL
+
+
+@pytest.mark.parametrize("modes,ms", [(24, (2, 5)), (45, (3, 4, 5)), (64, (2, 3, 4, 5))])
+def test_tf32_tensor_core_multi_tile(P, modes, ms):
+    """K_i up to 144, 270 and 384 (two and three M tiles of 128 rows, the last one short; the
+    triangular factor's blocks skipped off its triangle) on a 3 x 3 x 3 box, random coefficients,
+    16 sources, against the FP64 oracle."""
+    topo = synth.box_topology((3, 3, 3), modes=modes, m=[ms[i % len(ms)] for i in range(27)],
+                              io_cells=[(0, 2), (26, 3)], seed=modes, ragged_modes=False)
+    assert max(topo.cell_K()) == 6 * modes
+    co = synth.random_coefficients(topo, seed=modes)
+    src, rcv = synth.random_io(topo, 16, 6, seed=modes)
+    tau, nst = 0.05, 120
+    w = synth.ricker(np.arange(nst) * tau, 0.8)
+    ref = _oracle(topo, co, src, rcv, 16, 6, w, tau, nst)
+    assert np.linalg.norm(ref) > 0
+    out, _ = _lib_run(P, topo, co, src, rcv, 16, 6, w, tau, nst, P.TF32_TC)
+    assert _rel(out, ref) <= TF32_TOL
+    assert _worst_receiver(out, ref) <= TF32_TOL
+
+
 def test_tensor_core_uneven_cells_256_sources(P):
     """512 cells with 3..6 S-fraction layers and 8..16 modes per face, 256 sources (the
     many-source launch shape); the oracle steps sources 0, 77 and 255."""
