@@ -474,6 +474,7 @@ def run_native(args):
         except P.MssError as ex:
             tw_note = str(ex)
         else:
+            simtw.autotune(100)                                 # copy-ring depth of its cell kernel
             arms["tf32_tc"] = measure(simtw, P.SCHED_GRAPH, "k_cell_tw (tensor-core TF32 split)",
                                       ["cell_tw.cuh", "cell_tc.cuh", "online.cu"])
     # ---- FP64 ROM stepping (same coefficients), one run

@@ -360,11 +360,13 @@ mss_status mss_sim_clear_error(mss_sim *s, void *stream);
  * the wide kernel -- K_i > 128 or the factored last coefficient -- its variant 1..8: unroll depth
  * 2 or 4 of the row loops, 4 or 2 rows per thread, 16 or 8 sources per CTA, as 1 = (2, 4, 16),
  * 2 = (4, 4, 16), 3 = (2, 2, 16), 4 = (4, 2, 16), 5..8 the same with 8 sources; every variant
- * gives the same bits).  Errors: INVALID_ARG. */
+ * gives the same bits; for an MSS_TF32_TC sim, the copy-ring slots of its cell kernel, 2 up to the
+ * most that fit shared memory, also bit-identical).  Errors: INVALID_ARG. */
 mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources, int32_t groups);
 /* sched: current schedule; available (may be NULL): [MSS_SCHED_COUNT] 1 where usable; tile (may
  * be NULL): [3] = CUDA-core source tile, sources per CTA of the split tensor-core kernels (0 for
- * CUDA-core precisions), thread groups of the streamed FP32 kernel (the wide kernel's variant). */
+ * CUDA-core precisions), thread groups of the streamed FP32 kernel (the wide kernel's variant; the
+ * copy-ring slots for an MSS_TF32_TC sim). */
 mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *available, int32_t *tile);
 /* Time n_steps (rounded up to even) of every available schedule and tile variant (CUDA-core
  * source tile 16 or 8, split tensor-core N of 16..128, streamed-kernel block size) on zero

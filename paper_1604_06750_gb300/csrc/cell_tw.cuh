@@ -9,7 +9,11 @@
 // sources, 8 k per instruction, FP32 accumulators in TMEM.  TF32 keeps 10 explicit mantissa bits,
 // so both operands are split, x = hi + lo, hi = x with its low 13 mantissa bits cleared and lo =
 // (x - hi) cleared the same way, and every product is A_hi B_hi + A_hi B_lo + A_lo B_hi: each term
-// then carries about 21 bits, against FP32's 24, and the dropped A_lo B_lo is below both.
+// then carries about 21 bits, against FP32's 24, and the dropped A_lo B_lo is below both.  The
+// coefficient's hi part is the landed FP32 block itself: the tensor core reads a TF32 operand from
+// a 32-bit container and ignores its low 13 bits, which is the same truncation (the parity tests
+// against the FP64 oracle would fail by orders of magnitude otherwise: a coefficient rounded to TF32
+// without its lo part makes the stepping unstable).
 //
 // The coefficients stream from HBM as FP32 (the algorithm's own bytes), in 128-row x 32-column
 // blocks, each stored in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
@@ -19,11 +23,12 @@
 // Only the rows of the cell are stored (the last M tile is short) and, for the two triangular
 // products, only blocks that meet the triangle (with the other triangle stored as zeros).
 //
-// Warp roles (320 threads):
-//   warp 0     producer: bulk copies into a ring of 16 KB slots (mbarrier with transaction count);
-//   warp 1     one thread issues the MMAs, commits each stage and each product to mbarriers;
-//   warps 2-5  converters: split a landed block into hi/lo stage buffers (rows past the cell zero)
-//              and release its slot;
+// Warp roles (320 threads), around a ring of slots (a 16 KB block and its 16 KB lo part each):
+//   warp 0     producer: one bulk copy per block into the next free slot (mbarrier with
+//              transaction count);
+//   warps 2-5  converters: the lo part of a landed block (rows past the block zero);
+//   warp 1     one thread issues the block's MMAs and commits them to the slot's barrier, which
+//              frees the slot for the producer, and commits each product to a B-buffer barrier;
 //   warps 6-9  epilogue (warp w reads TMEM lanes 32 (w % 4) ..): stage each product's B operand
 //              (D^k from the state, y and E^k from TMEM) into a double buffer, publish F^1, and
 //              apply the hidden-layer leapfrog once the last product is complete.
@@ -37,8 +42,7 @@ constexpr int kTwMaxK = 384;                 // three M tiles of 128 rows
 constexpr int kTwNT = 16;                    // sources per CTA (MMA N)
 constexpr int kTwThreads = 320;
 constexpr int kTwBlock = 128 * 32 * 4;       // bytes of one FP32 A block (128 rows x 32 k)
-constexpr int kTwStages = 2;                 // converted (hi + lo) blocks the MMA side may hold
-constexpr int kTwMaxRing = 8;                // 2 x 8 + 9 barriers stay below the control words at byte 240
+constexpr int kTwMaxRing = 6;                // 3 x 6 + 5 barriers stay below the control words at byte 240
 
 struct TwArgs {
   const float *blob;          // per cell: the A blocks of every product, in consumption order
@@ -64,11 +68,10 @@ __host__ __device__ inline void tw_chunks(int j, int t, int m, int K, int &c0, i
   if (j == m) c1 = (((128 * t + 127) < (K - 1) ? (128 * t + 127) : (K - 1)) >> 5) + 1;
 }
 
-// Bytes of shared memory: barriers and control words, the copy ring, two stages (hi, lo), the
+// Bytes of shared memory: barriers and control words, the ring (block and lo part per slot), the
 // double-buffered B operand (hi, lo of 16 x K8 each), the K boundary-row indices.
 inline size_t tw_smem_bytes(int ring, int k8max) {
-  return 256 + (size_t)ring * kTwBlock + (size_t)kTwStages * 2 * kTwBlock + (size_t)4 * kTwNT * k8max * 4 +
-         8 * (size_t)k8max;
+  return 256 + (size_t)ring * 2 * kTwBlock + (size_t)4 * kTwNT * k8max * 4 + 8 * (size_t)k8max;
 }
 
 // instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M x N
@@ -145,25 +148,43 @@ __device__ __forceinline__ void tw_ld16(unsigned taddr, float (&v)[16]) {
   }
 }
 
-// The cell's A blocks in consumption order: product j, M tile t, k chunk c.
+// The cell's A blocks in consumption order: product j, then k chunk c, then the M tiles t whose
+// chunk range holds c, so consecutive blocks feed different accumulators.
 struct TwIter {
-  int m, K, K8, MT, NP;
-  int j, t, c, cfirst, clast;
-  int64_t off;   // bytes from the start of the cell's blob
+  int m, K, K8, MT, NP, nch;
+  int j, c, t, cfirst;   // cfirst: first chunk of (j, t), whose first MMA starts the accumulator
+  int64_t off;           // bytes from the start of the cell's blob
   __device__ void begin(int m_, int K_) {
     m = m_;
     K = K_;
     K8 = (K + 7) & ~7;
     MT = tw_mt(K);
     NP = 2 * m;
+    nch = (K8 + 31) / 32;
     j = 0;
-    t = 0;
+    c = 0;
+    t = -1;
     off = 0;
-    tile();
+    advance();
   }
-  __device__ void tile() {
-    tw_chunks(j, t, m, K, cfirst, clast);
-    c = cfirst;
+  // the next (j, c, t) whose chunk range holds c; every (j, c) has one (tile 0 for j != m, the last
+  // tile for j = m)
+  __device__ void advance() {
+    for (;;) {
+      if (++t >= MT) {
+        t = 0;
+        if (++c >= nch) {
+          c = 0;
+          if (++j >= NP) return;
+        }
+      }
+      int a, b;
+      tw_chunks(j, t, m, K, a, b);
+      if (c >= a && c < b) {
+        cfirst = a;
+        return;
+      }
+    }
   }
   __device__ bool valid() const { return j < NP; }
   __device__ int rows() const { return min(128, K8 - 128 * t); }
@@ -171,13 +192,7 @@ struct TwIter {
   __device__ unsigned bytes() const { return (unsigned)(rows() * kc() * 4); }
   __device__ void next() {
     off += bytes();
-    if (++c >= clast) {
-      if (++t >= MT) {
-        t = 0;
-        ++j;
-      }
-      if (j < NP) tile();
-    }
+    advance();
   }
 };
 
@@ -192,13 +207,12 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_cell_tw(const StepArgs<float>
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R = t.ring;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-  // barriers: copy full[R], copy empty[R], stage full[2], stage empty[2], B ready[2], B free[2], done
-  const int TF = 0, TE = R, SF = 2 * R, SE = 2 * R + 2, BR = 2 * R + 4, BF = 2 * R + 6, DN = 2 * R + 8;
+  // barriers: copy landed[R], lo part ready[R], slot free[R] (MMAs done), B ready[2], B free[2], done
+  const int TF = 0, SF = R, SE = 2 * R, BR = 3 * R, BF = 3 * R + 2, DN = 3 * R + 4;
   auto bar = [&](int i) { return smem_u32(bars + i); };
   volatile int *ctl = reinterpret_cast<volatile int *>(smem + 240);   // [0] TMEM base, [1] abort, [2] copies issued
   unsigned char *ring = smem + 256;
-  unsigned char *stage = ring + (size_t)R * kTwBlock;                 // hi0 lo0 hi1 lo1
-  unsigned char *bbuf = stage + (size_t)kTwStages * 2 * kTwBlock;     // hi0 lo0 hi1 lo1
+  unsigned char *bbuf = ring + (size_t)R * 2 * kTwBlock;              // hi0 lo0 hi1 lo1
   const size_t bhalf = (size_t)kTwNT * t.k8max * 4;
   int64_t *rows = reinterpret_cast<int64_t *>(bbuf + 4 * bhalf);
   const float *fs = cur ? a.fstate1 : a.fstate0;
@@ -220,11 +234,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_cell_tw(const StepArgs<float>
   if (tid == 0) {
     for (int i = 0; i < R; ++i) {
       mbar_init(bar(TF + i), 1);
-      mbar_init(bar(TE + i), 128);
-    }
-    for (int i = 0; i < 2; ++i) {
       mbar_init(bar(SF + i), 128);
       mbar_init(bar(SE + i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(bar(BR + i), 128);
       mbar_init(bar(BF + i), 1);
     }
@@ -251,11 +264,11 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_cell_tw(const StepArgs<float>
       it.begin(m, K);
       for (int b = 0; it.valid(); it.next(), ++b) {
         const int s = b % R;
-        if (b >= R && !mbar_wait(bar(TE + s), ((b / R) - 1) & 1, t.err)) { fail(); break; }
+        if (b >= R && !mbar_wait(bar(SE + s), ((b / R) - 1) & 1, t.err)) { fail(); break; }
         if (ctl[1]) break;
         const unsigned bytes = it.bytes();
         mbar_expect_tx(bar(TF + s), bytes + t.extra_tx);
-        bulk_g2s(smem_u32(ring + (size_t)s * kTwBlock), src + it.off, bytes, bar(TF + s));
+        bulk_g2s(smem_u32(ring + (size_t)s * 2 * kTwBlock), src + it.off, bytes, bar(TF + s));
         ctl[2] = b + 1;
       }
     }
@@ -273,21 +286,30 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_cell_tw(const StepArgs<float>
         tc_fence_after();
         const unsigned bh = smem_u32(bbuf + (size_t)(j & 1) * 2 * bhalf), bl = bh + (unsigned)bhalf;
         while (it.valid() && it.j == j) {
-          const int st = b % kTwStages;
-          if (!mbar_wait(bar(SF + st), (b / kTwStages) & 1, t.err)) { ok = false; break; }
+          const int s = b % R;
+          if (!mbar_wait(bar(SF + s), (b / R) & 1, t.err)) { ok = false; break; }
           tc_fence_after();
-          const unsigned ah = smem_u32(stage + (size_t)st * 2 * kTwBlock), al = ah + kTwBlock;
+          const unsigned ah = smem_u32(ring + (size_t)s * 2 * kTwBlock);
           const int kc = it.kc();
           const unsigned sbo_a = (unsigned)kc * 32u;
           const unsigned dcol = tmem + (unsigned)((j * MT + it.t) * kTwNT);
-          const bool first = it.c == it.cfirst;
-          for (int kk = 0; kk < kc / 8; ++kk) {
-            const unsigned ao = (unsigned)kk * 256u, bo = (unsigned)(8 * it.c + 2 * kk) * 128u;
-            mma_tf32(dcol, sdesc(ah + ao, 128, sbo_a), sdesc(bh + bo, 128, sbo_b), idesc, (first && kk == 0) ? 0u : 1u);
-            mma_tf32(dcol, sdesc(ah + ao, 128, sbo_a), sdesc(bl + bo, 128, sbo_b), idesc, 1u);
-            mma_tf32(dcol, sdesc(al + ao, 128, sbo_a), sdesc(bh + bo, 128, sbo_b), idesc, 1u);
+          // descriptors of the block's first k step; each further step of 8 k advances both operands
+          // by two core matrices (256 bytes, 16 in the descriptor's address field, which cannot carry
+          // out: shared addresses stay below 256 KB)
+          const uint64_t dah = sdesc(ah, 128, sbo_a), dal = sdesc(ah + kTwBlock, 128, sbo_a);
+          const uint64_t dbh = sdesc(bh + (unsigned)it.c * 1024u, 128, sbo_b);
+          const uint64_t dbl = sdesc(bl + (unsigned)it.c * 1024u, 128, sbo_b);
+          const unsigned acc0 = it.c == it.cfirst ? 0u : 1u;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            if (kk * 8 < kc) {
+              const uint64_t o = (uint64_t)(16 * kk);
+              mma_tf32(dcol, dah + o, dbh + o, idesc, kk == 0 ? acc0 : 1u);
+              mma_tf32(dcol, dah + o, dbl + o, idesc, 1u);
+              mma_tf32(dcol, dal + o, dbh + o, idesc, 1u);
+            }
           }
-          tc_commit(bar(SE + st));
+          tc_commit(bar(SE + s));
           it.next();
           ++b;
         }
@@ -298,36 +320,43 @@ __global__ void __launch_bounds__(kTwThreads, 1) k_cell_tw(const StepArgs<float>
       tc_commit(bar(DN));   // arrives once every MMA issued above has completed
     }
   } else if (warp < 6) {
-    // ---- converters: FP32 block -> TF32 hi / lo stage buffers of 128 rows
+    // ---- converters: lo part of each landed FP32 block, 128 rows (the block's own rows as the MMA
+    // reads them; rows past a short block read stale values there, which reach only accumulator
+    // rows past the cell, never stored, so their lo part is simply zero)
     const int ct = tid - 64;
     TwIter it;
     it.begin(m, K);
     for (int b = 0; it.valid(); it.next(), ++b) {
-      const int s = b % R, st = b % kTwStages;
-      bool ok = mbar_wait(bar(TF + s), (b / R) & 1, t.err);
-      if (ok && b >= kTwStages) ok = mbar_wait(bar(SE + st), ((b / kTwStages) - 1) & 1, t.err);
+      const int s = b % R;
+      const bool ok = mbar_wait(bar(TF + s), (b / R) & 1, t.err);
       if (!ok || ctl[1]) {
         if (!ok) fail();
         break;
       }
       const unsigned real = it.bytes(), full = 128u * (unsigned)it.kc() * 4u;
-      const unsigned char *src = ring + (size_t)s * kTwBlock;
-      unsigned char *dh = stage + (size_t)st * 2 * kTwBlock, *dl = dh + kTwBlock;
-      for (unsigned o = (unsigned)ct * 16u; o < full; o += 128u * 16u) {
-        float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-        if (o < real) {
-          const float4 v = *reinterpret_cast<const float4 *>(src + o);
-          tf32_split(v.x, h.x, l.x);
-          tf32_split(v.y, h.y, l.y);
-          tf32_split(v.z, h.z, l.z);
-          tf32_split(v.w, h.w, l.w);
+      const unsigned char *src = ring + (size_t)s * 2 * kTwBlock;
+      unsigned char *dl = ring + (size_t)s * 2 * kTwBlock + kTwBlock;
+      // four 16-byte pieces per thread per round, their loads issued together
+      for (unsigned o0 = (unsigned)ct * 16u; o0 < full; o0 += 4u * 128u * 16u) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned o = o0 + (unsigned)u * 128u * 16u;
+          v[u] = o < real ? *reinterpret_cast<const float4 *>(src + o) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        *reinterpret_cast<float4 *>(dh + o) = h;
-        *reinterpret_cast<float4 *>(dl + o) = l;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned o = o0 + (unsigned)u * 128u * 16u;
+          float4 h, l;
+          tf32_split(v[u].x, h.x, l.x);
+          tf32_split(v[u].y, h.y, l.y);
+          tf32_split(v[u].z, h.z, l.z);
+          tf32_split(v[u].w, h.w, l.w);
+          if (o < full) *reinterpret_cast<float4 *>(dl + o) = l;
+        }
       }
       fence_async_smem();
-      mbar_arrive(bar(TE + s));
-      mbar_arrive(bar(SF + st));
+      mbar_arrive(bar(SF + s));
     }
   } else {
     // ---- epilogue: B operands, F^1, leapfrog

@@ -629,6 +629,7 @@ struct mss_sim {
                                                // thread (else 4), bit 2 8-source tiles (else 16)
   mss::TcArgs tca{};
   int tw = 0;                                  // MSS_TF32_TC: the wide tensor-core cell kernel
+  int tw_ring_max = 2;                         // its copy-ring slots: the most that fit; twa.ring in use
   size_t tw_smem = 0;
   mss::TwArgs twa{};
   int n_cells = 0, n_faces = 0, n_src = 0, n_rcv = 0, ST = 1, tiles = 1;
@@ -961,7 +962,8 @@ static void step_impl(mss_sim &s, int64_t n, const double *w, void *traces, int 
     // capture and replay on the sim's own stream (the legacy stream cannot be captured)
     MSS_CUDA(cudaEventRecord(s.ev_in, st));
     MSS_CUDA(cudaStreamWaitEvent(s.cap, s.ev_in, 0));
-    GraphKey key{n, w, traces, s.cur, s.sched, s.stream_groups + 8 * s.ST + 4096 * s.tcs_nt + 65536 * s.wide_var};
+    GraphKey key{n, w, traces, s.cur, s.sched,
+                 s.stream_groups + 8 * s.ST + 4096 * s.tcs_nt + 65536 * s.wide_var + (1 << 20) * s.twa.ring};
     auto it = s.graphs.find(key);
     if (it == s.graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -1140,8 +1142,9 @@ static void build_tc_blob(const Rom &R, std::vector<uint16_t> &blob, std::vector
 // Coefficients of every cell in the wide tensor-core kernel's layout (cell_tw.cuh): per cell, the
 // A blocks of its 2m products in the order the kernel consumes them -- Gamma^1..Gamma^{m-1}, the
 // factored last coefficient twice (L^T: W's upper triangle, L: its lower triangle, W = L + L^T -
-// diag(L) at matrix m-1 of coef), Gamma-hat^2..Gamma-hat^m -- each block 128 rows (fewer in the
-// last M tile) x 32 columns (fewer in the last chunk), FP32, K-major core-matrix layout.
+// diag(L) at matrix m-1 of coef), Gamma-hat^2..Gamma-hat^m; within a product by k chunk, then M
+// tile -- each block 128 rows (fewer in the last M tile) x 32 columns (fewer in the last chunk),
+// FP32, K-major core-matrix layout.
 static void build_tw_blob(const Rom &R, const std::vector<double> &coef, const std::vector<int64_t> &cell_coef,
                           std::vector<float> &blob, std::vector<int64_t> &off) {
   blob.clear();
@@ -1152,11 +1155,13 @@ static void build_tw_blob(const Rom &R, const std::vector<double> &coef, const s
     for (int j = 0; j < 2 * m; ++j) {
       const int q = j < m - 1 ? j : (j <= m ? m - 1 : j - 1);
       const double *A = coef.data() + cell_coef[c] + (size_t)q * K * K;
-      for (int t = 0; t < MT; ++t) {
-        int c0, c1;
-        tw_chunks(j, t, m, K, c0, c1);
-        const int rows = std::min(128, K8 - 128 * t);
-        for (int ch = c0; ch < c1; ++ch) {
+      const int nch = (K8 + 31) / 32;
+      for (int ch = 0; ch < nch; ++ch) {
+        for (int t = 0; t < MT; ++t) {
+          int c0, c1;
+          tw_chunks(j, t, m, K, c0, c1);
+          if (ch < c0 || ch >= c1) continue;
+          const int rows = std::min(128, K8 - 128 * t);
           const int kc = std::min(32, K8 - 32 * ch);
           const size_t base = blob.size();
           blob.resize(base + (size_t)rows * kc, 0.f);
@@ -1422,6 +1427,7 @@ static void sim_create(mss_sim &s, const Rom &R, int prec, double tau, int flags
     s.twa.blob = s.d.tw_blob.as<float>();
     s.twa.blob_off = s.d.tw_off.as<int64_t>();
     s.twa.ring = ring;
+    s.tw_ring_max = ring;
     s.twa.k8max = k8max;
     s.twa.tmem_cols = cols;
   }
@@ -1953,7 +1959,11 @@ mss_status mss_sim_set_tile(mss_sim *s, int32_t source_tile, int32_t tc_sources,
       apply_tcs_nt(*s, tc_sources);
     }
     if (groups > 0) {
-      if (s->wide_ok && !s->stream_ok) {
+      if (s->tw) {
+        MSS_REQUIRE(groups >= 2 && groups <= s->tw_ring_max, MSS_ERR_INVALID_ARG,
+                    "copy-ring slots of the wide tensor-core kernel must be 2 .. the most that fit");
+        s->twa.ring = groups;
+      } else if (s->wide_ok && !s->stream_ok) {
         MSS_REQUIRE(groups <= 8, MSS_ERR_INVALID_ARG, "wide streamed kernel variant must be 1..8");
         s->wide_var = groups - 1;
       } else {
@@ -1973,7 +1983,7 @@ mss_status mss_sim_get_schedule(const mss_sim *s, int32_t *sched, int32_t *avail
     if (tile) {
       tile[0] = s->ST;
       tile[1] = s->tc ? s->tcs_nt : 0;
-      tile[2] = s->wide_ok && !s->stream_ok ? s->wide_var + 1 : s->stream_groups;
+      tile[2] = s->tw ? s->twa.ring : s->wide_ok && !s->stream_ok ? s->wide_var + 1 : s->stream_groups;
     }
   });
 }
@@ -1999,6 +2009,7 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
     tr.alloc((size_t)n * std::max(1, s->n_rcv) * s->n_src * es);
     const int cur0 = s->cur, sched0 = s->sched;
     const int st_keep = s->ST, nt_keep = s->tcs_nt, g_keep = s->stream_groups, wv_keep = s->wide_var;
+    const int ring_keep = s->twa.ring;
     const int64_t steps0 = s->steps;
     cudaEvent_t e0, e1;
     MSS_CUDA(cudaEventCreate(&e0));
@@ -2021,7 +2032,10 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
       for (int k = 0; k < MSS_SCHED_COUNT; ++k) {
         if (ms) ms[k] = -1.0;
         if (!sched_allowed(*s, k)) continue;
-        if (!s->tc) {
+        if (s->tw) {
+          // the wide tensor-core kernel: its copy-ring depth (groups field)
+          for (int ring = 2; ring <= s->tw_ring_max; ++ring) cands.push_back({k, st0, nt0, ring, s->wide_var});
+        } else if (!s->tc) {
           const bool streamed = k == MSS_SCHED_GRAPH_STREAM || k == MSS_SCHED_PERSIST_STREAM;
           for (int st : {s->st_max, s->st_max / 2}) {
             if (st < 8 && st != s->st_max) continue;
@@ -2050,7 +2064,8 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
         s->sched = c.sched;
         if (c.st != s->ST) apply_tile(*s, c.st);
         if (s->tc && c.nt != s->tcs_nt) apply_tcs_nt(*s, c.nt);
-        s->stream_groups = c.groups;
+        if (s->tw) s->twa.ring = c.groups;
+        else s->stream_groups = c.groups;
         s->wide_var = c.wv;
         auto run = [&]() {
           if (s->prec == MSS_FP64) step_dispatch<double>(*s, n, w.as<double>(), tr.p, 1, st);
@@ -2078,7 +2093,8 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
       if (best_c.st != s->ST) apply_tile(*s, best_c.st);
       if (s->tc && best_c.nt != s->tcs_nt) apply_tcs_nt(*s, best_c.nt);
       const int best_groups = best_c.groups;
-      s->stream_groups = best_groups;
+      if (s->tw) s->twa.ring = best_groups;
+      else s->stream_groups = best_groups;
       s->wide_var = best_c.wv;
     } catch (...) {
       restore();
@@ -2087,6 +2103,7 @@ mss_status mss_sim_autotune(mss_sim *s, int32_t n_steps, void *stream, double *m
       if (s->tc && s->tcs_nt != nt_keep) apply_tcs_nt(*s, nt_keep);
       s->stream_groups = g_keep;
       s->wide_var = wv_keep;
+      s->twa.ring = ring_keep;
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       throw;
