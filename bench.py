@@ -584,7 +584,8 @@ def run_native(args):
 
 def run_c3(args):
     """The 256^3 dipping-layer workload end to end on one GPU: GPU off-line build of all 4096 cell
-    ROMs (m = 4 in every cell; the per-cell layer rule runs in the oracle only), 256 sources on
+    ROMs (m = 4 in every cell, or with --c3-rule m_i in 3..6 per cell by the library's layer-count
+    rule, mss_layer_rule), 256 sources on
     face centres of the skeleton plane one cell below the top, 128 receivers on a line in that
     plane, 6000 steps; FP32 with split-BF16 tensor-core products (the many-source path), BF16
     products and CUDA-core FP32 timed; receiver error against the same GPU's FP64 fine-grid
@@ -607,7 +608,17 @@ def run_c3(args):
     tau = wl.cfl_fraction * 2.0 / math.sqrt(lam)
     s = -(2 * math.pi * wl.f_max) ** 2
     t1 = time.perf_counter()
-    LR = P.Rom.build(LP, wl.m, wl.n_modes, s, cg_tol=1e-12)
+    rule = None
+    if args.c3_rule:
+        w_max = 2 * math.pi * wl.f_max
+        cm_rule, err_rule = P.Rom.layer_rule(LP, wl.n_modes, s, w_max, (3, 6), 1e-4, cg_tol=1e-12)
+        t_rule = time.perf_counter() - t1
+        rule = {"m_counts": {str(k): int(np.sum(cm_rule == k)) for k in range(3, 7)}, "tol": 1e-4,
+                "largest_error_kept": float(np.max(err_rule)), "seconds": t_rule}
+        t1 = time.perf_counter()
+        LR = P.Rom.build(LP, 6, wl.n_modes, s, cg_tol=1e-12, cell_m=cm_rule)
+    else:
+        LR = P.Rom.build(LP, wl.m, wl.n_modes, s, cg_tol=1e-12)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     LR.set_io_nodes(LP, wl.src_nodes, wl.rcv_nodes)
@@ -623,10 +634,13 @@ def run_c3(args):
         return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
     out = {"mode": "c3", "config": {"workload": "3d_dipping_%d: %d^3 voxels, %d cells of 16^3 (uneven K_i %d..%d), "
-                                                "m=4, %d modes/face, %d sources, %d receivers, %d steps"
-                                                % (args.c3_n, args.c3_n, len(cm), min(Ks), max(Ks), wl.n_modes, S,
-                                                   R, nst),
-                                    "band": "Ricker peak at 1/10 grid Nyquist", "layers": "m = 4 in every cell"},
+                                                "m=%s, %d modes/face, %d sources, %d receivers, %d steps"
+                                                % (args.c3_n, args.c3_n, len(cm), min(Ks), max(Ks),
+                                                   "3..6" if rule else "4", wl.n_modes, S, R, nst),
+                                    "band": "Ricker peak at 1/10 grid Nyquist",
+                                    "layers": ("m_i per cell by the layer-count rule (3..6, tol 1e-4)" if rule
+                                               else "m = 4 in every cell")},
+           "layer_rule": rule,
            "unit": UNIT, "offline_s": {"assemble_partition_cfl": t1 - t0, "gpu_rom_build": t2 - t1},
            "tau": tau, "precisions": {}}
     clocks = Clocks(0)
@@ -1034,6 +1048,8 @@ def main():
                     help="c3: the 256^3 dipping-layer workload end to end (separate JSON line)")
     ap.add_argument("--c3-n", type=int, default=256)
     ap.add_argument("--c3-modes", type=int, default=15)
+    ap.add_argument("--c3-rule", action="store_true",
+                    help="--config c3: per-cell layer counts (3..6) by the library's layer-count rule")
     ap.add_argument("--c3-steps", type=int, default=6000)
     ap.add_argument("--c3-parity-steps", type=int, default=200)
     ap.add_argument("--accuracy", action="store_true",

@@ -158,6 +158,20 @@ typedef struct mss_rom_params {
 mss_status mss_build_roms(const mss_partition *p, const mss_rom_params *prm, const int32_t *cell_m,
                           void *stream, mss_rom **out);
 
+/* Per-cell number of S-fraction layers by the rule of the dipping-layer workload (the paper fixes
+ * m_i per cell, Section 7, without the rule; this one is a reading of it): cell_m[i] = the smallest
+ * m in [m_lo, m_hi] whose ROM transfer function F^m(z) = S_m^T (A_m + z I)^{-1} S_m (Eq. tfprj) is
+ * within tol of F^{m_hi} at the n_freq damped test points z_j = -w_j^2 + i w_j omega_max / 10,
+ * w_j = j omega_max / n_freq (relative Frobenius error, largest over j); err[i] (may be NULL) that
+ * error (0 at m_hi).  A_m, S_m are the leading m K_i rows/columns of the m_hi projection built as
+ * mss_build_roms builds it (FP64 on the GPU; the block Krylov spaces are nested); the transfer
+ * functions are evaluated on the host in FP64 complex arithmetic, one block LDL^T of A + z I by
+ * K_i x K_i blocks per point giving every m at once.  cell_m, err: host, one entry per cell of p.
+ * Pass cell_m to mss_build_roms.  Errors: as mss_build_roms (m_hi K_i must fit the cell),
+ * INVALID_ARG, LANCZOS_BREAKDOWN (a singular pivot block). */
+mss_status mss_layer_rule(const mss_partition *p, const mss_rom_params *prm, int32_t m_lo, int32_t m_hi,
+                          double omega_max, double tol, int32_t n_freq, int32_t *cell_m, double *err, void *stream);
+
 /* Coefficient set given by the caller (host, FP64), for ROMs built elsewhere.
  * cell_m[C], cell_face_ptr[C+1], cell_faces[] (faces of each cell in boundary-vector order),
  * face_M[F], face_cells[2F] (lower cell first, -1 for a one-sided face);

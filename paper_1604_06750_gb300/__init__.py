@@ -87,6 +87,7 @@ _SIGS = [
     ("mss_partition_set_face_bases", C.c_int32, [_P, C.c_int32, _P, _P]),
     ("mss_partition_destroy", None, [_P]),
     ("mss_build_roms", C.c_int32, [_P, _P, _P, _P, _P]),
+    ("mss_layer_rule", C.c_int32, [_P, _P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, _P, _P, _P]),
     ("mss_rom_import", C.c_int32, [_P, _P]),
     ("mss_rom_info", C.c_int32, [_P, _P]),
     ("mss_rom_export", C.c_int32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -330,6 +331,19 @@ class Rom(_Handle):
                                     C.byref(self._h)))
         self.part = part
         return self
+
+    @staticmethod
+    def layer_rule(part: Partition, n_modes: int, shift: float, omega_max: float, m_range=(3, 6), tol: float = 1e-4,
+                   n_freq: int = 8, cg_tol: float = 1e-12, cg_maxit: int = 5000, stream=None):
+        """Per-cell layer counts (mss_layer_rule): returns (cell_m int32[C], err float64[C])."""
+        p = _RomParams(m=int(m_range[1]), n_modes=int(n_modes), shift=float(shift), cg_tol=float(cg_tol),
+                       cg_maxit=int(cg_maxit), reserved=0)
+        n = int(part.info()[0])
+        cm = np.zeros(n, np.int32)
+        err = np.zeros(n, np.float64)
+        _check(lib().mss_layer_rule(part._h, C.byref(p), int(m_range[0]), int(m_range[1]), C.c_double(omega_max),
+                                    C.c_double(tol), int(n_freq), _ptr(cm), _ptr(err), _stream(stream)))
+        return cm, err
 
     @classmethod
     def skeleton(cls, part: Partition, m: int, n_modes: int, shift: float, cg_tol: float = 1e-12,

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <thread>
 
 #include "cuda_util.h"
 
@@ -640,10 +641,151 @@ inline unsigned nblk(int64_t n) { return (unsigned)((n + kThreads - 1) / kThread
 
 }  // namespace
 
+// ------------------------------------------------------------------ per-cell layer-count rule
+// Inputs of the rule of the dipping-layer workload (reading R22), and its per-cell answers.
+struct LayerRule {
+  int m_lo, m_hi, n_freq;
+  double omega_max, tol;
+  int32_t *cell_m;   // per cell of the partition
+  double *err;       // per cell (may be null)
+};
+
+struct cplx {
+  double re, im;
+};
+static inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// X (K x K, complex, row-major) <- X^{-1} by Gauss-Jordan elimination with partial pivoting; false
+// if a pivot vanishes.  work: K x K.
+static bool cinvert(std::vector<cplx> &X, int K, std::vector<cplx> &work) {
+  work.assign((size_t)K * K, cplx{0, 0});
+  for (int i = 0; i < K; ++i) work[(size_t)i * K + i] = {1, 0};
+  for (int c = 0; c < K; ++c) {
+    int piv = c;
+    double best = 0;
+    for (int r = c; r < K; ++r) {
+      const cplx v = X[(size_t)r * K + c];
+      const double a = v.re * v.re + v.im * v.im;
+      if (a > best) { best = a; piv = r; }
+    }
+    if (!(best > 0)) return false;
+    if (piv != c)
+      for (int j = 0; j < K; ++j) {
+        std::swap(X[(size_t)piv * K + j], X[(size_t)c * K + j]);
+        std::swap(work[(size_t)piv * K + j], work[(size_t)c * K + j]);
+      }
+    const cplx d = X[(size_t)c * K + c];
+    const double dn = d.re * d.re + d.im * d.im;
+    const cplx inv = {d.re / dn, -d.im / dn};
+    for (int j = 0; j < K; ++j) {
+      X[(size_t)c * K + j] = cmul(X[(size_t)c * K + j], inv);
+      work[(size_t)c * K + j] = cmul(work[(size_t)c * K + j], inv);
+    }
+    for (int r = 0; r < K; ++r) {
+      if (r == c) continue;
+      const cplx f = X[(size_t)r * K + c];
+      if (f.re == 0 && f.im == 0) continue;
+      for (int j = 0; j < K; ++j) {
+        const cplx a = cmul(f, X[(size_t)c * K + j]), b = cmul(f, work[(size_t)c * K + j]);
+        X[(size_t)r * K + j].re -= a.re;
+        X[(size_t)r * K + j].im -= a.im;
+        work[(size_t)r * K + j].re -= b.re;
+        work[(size_t)r * K + j].im -= b.im;
+      }
+    }
+  }
+  X.swap(work);
+  return true;
+}
+
+// C (p x q) -= A (p x r) B (r x q), complex row-major with leading dimensions; transB: B given as
+// its transpose (q x r, element (k, j) at Bt[j * ldb + k]).
+static void cgemm_sub(cplx *C, int ldc, const cplx *A, int lda, const cplx *B, int ldb, bool transB, int p, int q, int r) {
+  for (int i = 0; i < p; ++i)
+    for (int k = 0; k < r; ++k) {
+      const cplx a = A[(size_t)i * lda + k];
+      if (a.re == 0 && a.im == 0) continue;
+      for (int j = 0; j < q; ++j) {
+        const cplx b = transB ? B[(size_t)j * ldb + k] : B[(size_t)k * ldb + j];
+        C[(size_t)i * ldc + j].re -= a.re * b.re - a.im * b.im;
+        C[(size_t)i * ldc + j].im -= a.re * b.im + a.im * b.re;
+      }
+    }
+}
+
+// The rule for one cell from its m_hi-layer projection A (n x n), S (n x K), n = m_hi K: the ROM
+// transfer function of m layers is F^m(z) = S_m^T (A_m + z I)^{-1} S_m with A_m, S_m the leading
+// m K rows and columns (nested Krylov spaces).  Per test point, one block LDL^T of A + z I by K x K
+// blocks (complex symmetric; every leading block A_m + z I is nonsingular since Im z > 0 and A_m is
+// real symmetric) gives every m at once: with Y = L^{-1} S, F^m = sum_{b < m} Y_b^T D_b^{-1} Y_b.
+// errs[m] = max over the points of ||F^m - F^{m_hi}||_F / ||F^{m_hi}||_F.  False if a pivot block
+// is singular.
+static bool layer_rule_cell(const double *A, const double *S, int K, const LayerRule &lr, std::vector<double> &errs) {
+  const int mh = lr.m_hi, n = mh * K;
+  errs.assign(mh + 1, 0.0);
+  std::vector<cplx> M((size_t)n * n), Y((size_t)n * K), D, Dinv, work, T((size_t)K * K), Lib((size_t)K * K);
+  std::vector<std::vector<cplx>> F(mh + 1, std::vector<cplx>((size_t)K * K));
+  for (int jz = 1; jz <= lr.n_freq; ++jz) {
+    const double w = jz * lr.omega_max / lr.n_freq;
+    const cplx z = {-w * w, w * lr.omega_max / 10.0};
+    for (size_t i = 0; i < (size_t)n * n; ++i) M[i] = {A[i], 0.0};
+    for (int i = 0; i < n; ++i) {
+      M[(size_t)i * n + i].re += z.re;
+      M[(size_t)i * n + i].im += z.im;
+    }
+    for (size_t i = 0; i < (size_t)n * K; ++i) Y[i] = {S[i], 0.0};
+    std::vector<cplx> Fc((size_t)K * K, cplx{0, 0});
+    for (int b = 0; b < mh; ++b) {
+      cplx *Mbb = M.data() + (size_t)b * K * n + (size_t)b * K;
+      Dinv.resize((size_t)K * K);
+      for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) Dinv[(size_t)i * K + j] = Mbb[(size_t)i * n + j];
+      if (!cinvert(Dinv, K, work)) return false;
+      // F^{b+1} = F^b + Y_b^T D_b^{-1} Y_b
+      const cplx *Yb = Y.data() + (size_t)b * K * K;
+      std::fill(T.begin(), T.end(), cplx{0, 0});
+      cgemm_sub(T.data(), K, Dinv.data(), K, Yb, K, false, K, K, K);     // T = -D^{-1} Y_b
+      for (int i = 0; i < K; ++i)
+        for (int k = 0; k < K; ++k) {
+          const cplx yt = Yb[(size_t)k * K + i];                           // (Y_b^T)_{ik}
+          for (int j = 0; j < K; ++j) {
+            const cplx t = T[(size_t)k * K + j];
+            Fc[(size_t)i * K + j].re -= yt.re * t.re - yt.im * t.im;
+            Fc[(size_t)i * K + j].im -= yt.re * t.im + yt.im * t.re;
+          }
+        }
+      F[b + 1] = Fc;
+      // eliminate block column b below the diagonal (lower triangle of blocks kept current)
+      for (int i = b + 1; i < mh; ++i) {
+        const cplx *Mib = M.data() + (size_t)i * K * n + (size_t)b * K;
+        std::fill(Lib.begin(), Lib.end(), cplx{0, 0});
+        cgemm_sub(Lib.data(), K, Mib, n, Dinv.data(), K, false, K, K, K);  // Lib = -M_ib D^{-1}
+        for (int i2 = 0; i2 < K * K; ++i2) Lib[i2] = {-Lib[i2].re, -Lib[i2].im};
+        for (int jj = b + 1; jj <= i; ++jj)                                  // M_ij -= L_ib M_jb^T
+          cgemm_sub(M.data() + (size_t)i * K * n + (size_t)jj * K, n, Lib.data(), K,
+                    M.data() + (size_t)jj * K * n + (size_t)b * K, n, true, K, K, K);
+        cgemm_sub(Y.data() + (size_t)i * K * K, K, Lib.data(), K, Yb, K, false, K, K, K);
+      }
+    }
+    double nref = 0;
+    for (const cplx &v : F[mh]) nref += v.re * v.re + v.im * v.im;
+    nref = std::sqrt(nref);
+    for (int m = lr.m_lo; m < mh; ++m) {
+      double d = 0;
+      for (size_t i = 0; i < (size_t)K * K; ++i) {
+        const double a = F[m][i].re - F[mh][i].re, c = F[m][i].im - F[mh][i].im;
+        d += a * a + c * c;
+      }
+      errs[m] = std::max(errs[m], std::sqrt(d) / std::max(nref, 1e-300));
+    }
+  }
+  return true;
+}
+
 // Chunk of cells processed together on the device.
 static void build_chunk(const Partition &P, const std::vector<int> &cells, const std::vector<int> &Kt_all,
                         const std::vector<int> &m_all, const std::vector<std::vector<double>> &Cb_all, double shift,
-                        double cg_tol, int cg_maxit, Rom &R, cudaStream_t st) {
+                        double cg_tol, int cg_maxit, Rom &R, cudaStream_t st, const LayerRule *rule = nullptr) {
   const int nc = (int)cells.size();
   int W = 0, mmax = 0;
   for (int c : cells) {
@@ -790,6 +932,34 @@ static void build_chunk(const Partition &P, const std::vector<int> &cells, const
     }
     k_pack_sm<<<nc, kThreads, 0, st>>>(d_sm.as<double>(), d_smoff.as<int64_t>(), V[j2].as<double>(), d_Cb.as<double>(),
                                        d_cboff.as<int64_t>(), r0, d_Kb.as<int32_t>(), kt, d_mc.as<int32_t>(), W, j2);
+  }
+  if (rule) {
+    // the layer-count rule on the host from the projections (cells on host threads), then done
+    std::vector<double> am(am_off[nc]), sm(sm_off[nc]);
+    MSS_CUDA(cudaMemcpyAsync(am.data(), d_am.p, am.size() * 8, cudaMemcpyDeviceToHost, st));
+    MSS_CUDA(cudaMemcpyAsync(sm.data(), d_sm.p, sm.size() * 8, cudaMemcpyDeviceToHost, st));
+    MSS_CUDA(cudaStreamSynchronize(st));
+    const int nt = std::max(1, std::min<int>(nc, (int)std::min(32u, std::max(1u, std::thread::hardware_concurrency()))));
+    std::vector<int> bad(nt, 0);
+    std::vector<std::thread> pool;
+    for (int th = 0; th < nt; ++th)
+      pool.emplace_back([&, th] {
+        std::vector<double> errs;
+        for (int i = th; i < nc; i += nt) {
+          if (!layer_rule_cell(am.data() + am_off[i], sm.data() + sm_off[i], Kt[i], *rule, errs)) {
+            bad[th] = 1;
+            continue;
+          }
+          int mpick = rule->m_hi;
+          for (int m = rule->m_lo; m <= rule->m_hi; ++m)
+            if (errs[m] <= rule->tol) { mpick = m; break; }
+          rule->cell_m[cells[i]] = mpick;
+          if (rule->err) rule->err[cells[i]] = errs[mpick];
+        }
+      });
+    for (auto &t : pool) t.join();
+    for (int b : bad) MSS_REQUIRE(b == 0, MSS_ERR_LANCZOS_BREAKDOWN, "singular pivot block in the layer-count rule");
+    return;
   }
   // lift rows: V^T e_n of every lift node of these cells (m blocks of the node's row of V_j)
   std::vector<int32_t> lptr(nc + 1, 0);
@@ -1475,6 +1645,45 @@ namespace mss {
 }  // namespace mss
 
 using namespace mss;
+
+extern "C" mss_status mss_layer_rule(const mss_partition *p, const mss_rom_params *prm, int32_t m_lo, int32_t m_hi,
+                                     double omega_max, double tol, int32_t n_freq, int32_t *cell_m, double *err,
+                                     void *stream) {
+  return guard([&] {
+    const Range nvtx_range("mss_layer_rule");
+    MSS_REQUIRE(p && prm && cell_m, MSS_ERR_INVALID_ARG, "null argument");
+    MSS_REQUIRE(m_lo >= 1 && m_hi >= m_lo && omega_max > 0 && tol > 0 && n_freq >= 1, MSS_ERR_INVALID_ARG,
+                "need 1 <= m_lo <= m_hi, omega_max > 0, tol > 0, n_freq >= 1");
+    Partition &P = const_cast<Partition &>(p->p);
+    const LayerRule rule{m_lo, m_hi, n_freq, omega_max, tol, cell_m, err};
+    // the m_hi-layer projection of every cell, as mss_build_roms makes it (chunks bounded by memory)
+    std::vector<int32_t> mh(P.n_cells, m_hi);
+    Rom R;
+    std::vector<int> Kt, mv;
+    std::vector<std::vector<double>> Cb;
+    rom_topology(P, *prm, mh.data(), R, Kt, mv, Cb);
+    size_t free_b = 0, total_b = 0;
+    MSS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    int Wmax = 0;
+    for (int c = 0; c < P.n_cells; ++c) Wmax = std::max(Wmax, Kt[c]);
+    const double budget = std::min<double>(0.5 * (double)free_b, 48e9);
+    const cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> chunk;
+    double used = 0;
+    for (int c = 0; c < P.n_cells; ++c) {
+      const double need = (double)P.cells[c].nodes.size() * Wmax * 8.0 * (m_hi + 7) +
+                          8.0 * ((double)m_hi * Kt[c]) * ((double)m_hi * Kt[c]) * 3;
+      if (!chunk.empty() && used + need > budget) {
+        build_chunk(P, chunk, Kt, mv, Cb, prm->shift, prm->cg_tol, prm->cg_maxit, R, st, &rule);
+        chunk.clear();
+        used = 0;
+      }
+      chunk.push_back(c);
+      used += need;
+    }
+    if (!chunk.empty()) build_chunk(P, chunk, Kt, mv, Cb, prm->shift, prm->cg_tol, prm->cg_maxit, R, st, &rule);
+  });
+}
 
 extern "C" mss_status mss_build_roms(const mss_partition *p, const mss_rom_params *prm, const int32_t *cell_m, void *stream,
                                      mss_rom **out) {
