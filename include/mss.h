@@ -171,6 +171,13 @@ mss_status mss_build_roms(const mss_partition *p, const mss_rom_params *prm, con
  * INVALID_ARG, LANCZOS_BREAKDOWN (a singular pivot block). */
 mss_status mss_layer_rule(const mss_partition *p, const mss_rom_params *prm, int32_t m_lo, int32_t m_hi,
                           double omega_max, double tol, int32_t n_freq, int32_t *cell_m, double *err, void *stream);
+/* The host part of the rule for one cell, on a projection given by the caller: A (n x n, symmetric)
+ * and S (n x K), n = m_hi K, row-major FP64 host buffers, leading m K rows/columns being the m-layer
+ * ROM.  errs[m] (host, m_hi + 1 entries) = the rule's error of m for m_lo <= m <= m_hi (0 at m_hi
+ * and below m_lo); *m_out = the chosen m.  No device work.  Errors: INVALID_ARG,
+ * LANCZOS_BREAKDOWN (a singular pivot block). */
+mss_status mss_layer_rule_cell(const double *A, const double *S, int32_t K, int32_t m_lo, int32_t m_hi,
+                               double omega_max, double tol, int32_t n_freq, int32_t *m_out, double *errs);
 
 /* Coefficient set given by the caller (host, FP64), for ROMs built elsewhere.
  * cell_m[C], cell_face_ptr[C+1], cell_faces[] (faces of each cell in boundary-vector order),

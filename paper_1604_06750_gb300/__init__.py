@@ -88,6 +88,8 @@ _SIGS = [
     ("mss_partition_destroy", None, [_P]),
     ("mss_build_roms", C.c_int32, [_P, _P, _P, _P, _P]),
     ("mss_layer_rule", C.c_int32, [_P, _P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, _P, _P, _P]),
+    ("mss_layer_rule_cell", C.c_int32, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32,
+                                        _P, _P]),
     ("mss_rom_import", C.c_int32, [_P, _P]),
     ("mss_rom_info", C.c_int32, [_P, _P]),
     ("mss_rom_export", C.c_int32, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -344,6 +346,17 @@ class Rom(_Handle):
         _check(lib().mss_layer_rule(part._h, C.byref(p), int(m_range[0]), int(m_range[1]), C.c_double(omega_max),
                                     C.c_double(tol), int(n_freq), _ptr(cm), _ptr(err), _stream(stream)))
         return cm, err
+
+    @staticmethod
+    def layer_rule_cell(A, S, K: int, omega_max: float, m_range=(3, 6), tol: float = 1e-4, n_freq: int = 8):
+        """mss_layer_rule_cell on a given projection (host only): returns (m, errs[m_hi + 1])."""
+        A = _arr(A, np.float64)
+        S = _arr(S, np.float64)
+        mo = np.zeros(1, np.int32)
+        errs = np.zeros(int(m_range[1]) + 1, np.float64)
+        _check(lib().mss_layer_rule_cell(_ptr(A), _ptr(S), int(K), int(m_range[0]), int(m_range[1]),
+                                         C.c_double(omega_max), C.c_double(tol), int(n_freq), _ptr(mo), _ptr(errs)))
+        return int(mo[0]), errs
 
     @classmethod
     def skeleton(cls, part: Partition, m: int, n_modes: int, shift: float, cg_tol: float = 1e-12,

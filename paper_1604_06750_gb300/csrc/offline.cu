@@ -1646,6 +1646,23 @@ namespace mss {
 
 using namespace mss;
 
+extern "C" mss_status mss_layer_rule_cell(const double *A, const double *S, int32_t K, int32_t m_lo, int32_t m_hi,
+                                          double omega_max, double tol, int32_t n_freq, int32_t *m_out, double *errs) {
+  return guard([&] {
+    MSS_REQUIRE(A && S && m_out && errs && K >= 1, MSS_ERR_INVALID_ARG, "null argument or K < 1");
+    MSS_REQUIRE(m_lo >= 1 && m_hi >= m_lo && omega_max > 0 && tol > 0 && n_freq >= 1, MSS_ERR_INVALID_ARG,
+                "need 1 <= m_lo <= m_hi, omega_max > 0, tol > 0, n_freq >= 1");
+    const LayerRule rule{m_lo, m_hi, n_freq, omega_max, tol, nullptr, nullptr};
+    std::vector<double> e;
+    MSS_REQUIRE(layer_rule_cell(A, S, K, rule, e), MSS_ERR_LANCZOS_BREAKDOWN, "singular pivot block");
+    int mpick = m_hi;
+    for (int m = m_lo; m <= m_hi; ++m)
+      if (e[m] <= tol) { mpick = m; break; }
+    for (int m = 0; m <= m_hi; ++m) errs[m] = m >= m_lo ? e[m] : 0.0;
+    *m_out = mpick;
+  });
+}
+
 extern "C" mss_status mss_layer_rule(const mss_partition *p, const mss_rom_params *prm, int32_t m_lo, int32_t m_hi,
                                      double omega_max, double tol, int32_t n_freq, int32_t *cell_m, double *err,
                                      void *stream) {
