@@ -43,6 +43,8 @@ def test_io_entries_sit_on_one_sided_faces():
 
 def test_exported_rom_round_trips_the_coefficients():
     import paper_1604_06750_gb300 as P
+    from paper_1604_06750_gb300 import build
+    build.build()
     P.lib()
     topo = synth.box_topology((2, 2, 1), modes=3, m=[1, 2, 3, 2], io_cells=[(1, 2)], seed=4, ragged_modes=True)
     co = synth.random_coefficients(topo, seed=4)
