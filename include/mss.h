@@ -89,6 +89,21 @@ typedef struct mss_operator mss_operator;
  * sigma, rho: host, prod(n) doubles, > 0.  Unknowns: kept nodes in node order.
  * Errors: INVALID_ARG (sizes), NOT_SPD (a sigma or rho <= 0 or not finite). */
 mss_status mss_assemble(const mss_grid *g, const double *sigma, const double *rho, mss_operator **out);
+/* Elastic operator of the paper's anisotropic elastic experiment (Section 7: u_tt = div sigma with
+ * sigma_ij = C_ijkl u_k,l), as a symmetric non-positive pencil (Section 1): A = -K, K the stiffness
+ * of trilinear finite elements on the voxel grid, exact for a constant stiffness per voxel (2 x 2 x 2
+ * Gauss points); B the lumped mass, rho_v h^3/8 from each voxel to each of its corners, per
+ * component.  Unknowns: 3 per kept node, node-major: 3k + p is displacement component p (physical
+ * axis x, y, z = array axis 2, 1, 0) of the k-th kept node (nodes in node order; Dirichlet walls
+ * remove their nodes as in mss_assemble).  C: host, prod(n) x 36 doubles, per voxel (C order) the
+ * 6 x 6 Voigt stiffness, row-major, order (xx, yy, zz, yz, xz, xy) in physical axes, symmetric
+ * positive definite (a VTI medium from Thomsen's parameters, or any other); rho: host, prod(n)
+ * doubles.  dim must be 3.  The operator serves mss_operator_info / export / lambda_max and
+ * mss_operator_node (which returns the unknown of component 0); the partition and the fine-grid
+ * kernels take one unknown per node and refuse it (vector faces are not built).
+ * Errors: INVALID_ARG (dim, sizes, walls, C not symmetric), NOT_SPD (C not positive definite,
+ * rho <= 0, a value not finite). */
+mss_status mss_assemble_elastic(const mss_grid *g, const double *C, const double *rho, mss_operator **out);
 /* info[0] = unknowns N, info[1] = nonzeros of A (CSR, diagonal included). */
 mss_status mss_operator_info(const mss_operator *op, int64_t info[2]);
 /* Copy A as CSR (rowptr[N+1], col[nnz], val[nnz], columns ascending) and diag(B)[N] to host buffers. */

@@ -86,6 +86,7 @@ _SIGS = [
     ("mss_partition_cell", C.c_int32, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
     ("mss_partition_set_face_bases", C.c_int32, [_P, C.c_int32, _P, _P]),
     ("mss_partition_destroy", None, [_P]),
+    ("mss_assemble_elastic", C.c_int32, [_P, _P, _P, _P]),
     ("mss_build_roms", C.c_int32, [_P, _P, _P, _P, _P]),
     ("mss_layer_rule", C.c_int32, [_P, _P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, _P, _P, _P]),
     ("mss_layer_rule_cell", C.c_int32, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32,
@@ -217,6 +218,28 @@ class Operator(_Handle):
         info = np.zeros(2, np.int64)
         _check(lib().mss_operator_info(self._h, _ptr(info)))
         self.N, self.nnz = int(info[0]), int(info[1])
+
+    @classmethod
+    def elastic(cls, grid, stiffness: np.ndarray, rho: np.ndarray) -> "Operator":
+        """mss_assemble_elastic: per-voxel Voigt stiffness (n0, n1, n2, 6, 6) and density."""
+        self = cls.__new__(cls)
+        _Handle.__init__(self)
+        g = _Grid()
+        g.dim = len(grid.n)
+        for a in range(g.dim):
+            g.n[a] = int(grid.n[a])
+            for s in range(2):
+                g.bc[a][s] = NEUMANN if grid.bc[a][s] == "N" else DIRICHLET
+        g.h = float(grid.h)
+        self.grid = grid
+        self._stiffness = _arr(stiffness, np.float64).ravel()
+        self._rho = _arr(rho, np.float64).ravel()
+        self._sigma = self._rho        # no scalar coefficient; the partition refuses this operator anyway
+        _check(lib().mss_assemble_elastic(C.byref(g), _ptr(self._stiffness), _ptr(self._rho), C.byref(self._h)))
+        info = np.zeros(2, np.int64)
+        _check(lib().mss_operator_info(self._h, _ptr(info)))
+        self.N, self.nnz = int(info[0]), int(info[1])
+        return self
 
     def export(self):
         """(rowptr, col, val, bdiag) as numpy arrays."""

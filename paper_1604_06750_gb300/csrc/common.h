@@ -72,6 +72,7 @@ struct Operator {
   Csr A;
   std::vector<double> B;
   int64_t nshape[3] = {1, 1, 1};   // node grid extents per array axis
+  int comps = 1;                   // unknowns per kept node: 1 (acoustic) or 3 (elastic, node-major)
 };
 
 // ------------------------------------------------------------------ partition

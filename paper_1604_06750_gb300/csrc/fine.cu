@@ -257,6 +257,7 @@ mss_status mss_fine_create(const mss_operator *op, int32_t precision, double tau
     MSS_REQUIRE(precision == MSS_FP64 || precision == MSS_FP32, MSS_ERR_INVALID_ARG, "precision must be FP64 or FP32");
     MSS_REQUIRE(tau > 0 && std::isfinite(tau), MSS_ERR_CFL, "tau must be positive");
     const Operator &o = op->o;
+    MSS_REQUIRE(o.comps == 1, MSS_ERR_INVALID_ARG, "the fine-grid kernels take one unknown per node (acoustic operator)");
     auto f = std::make_unique<mss_fine>();
     MSS_CUDA(cudaStreamCreateWithFlags(&f->cap, cudaStreamNonBlocking));
     MSS_CUDA(cudaEventCreateWithFlags(&f->ev_in, cudaEventDisableTiming));

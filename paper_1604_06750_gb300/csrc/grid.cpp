@@ -128,6 +128,176 @@ static void assemble(Operator &o, const mss_grid &g, const double *sigma, const 
   }
 }
 
+// ------------------------------------------------------------------ elastic assembly
+// Element stiffness of a voxel of edge h for each unit Voigt entry: Eab[a][b] (24 x 24, dof 3 c + p
+// = displacement component p, physical axis, at corner c in C order over the array axes) is
+// the integral over the voxel of sum_{q,s} T_pqrs dN_c/dx_q dN_d/dx_s with T the stiffness tensor
+// of the Voigt matrix whose only non-zero entry is (a, b).  Trilinear N_c: the 2 x 2 x 2 Gauss rule
+// integrates these products (quadratic per axis) exactly.  Array axis a is physical axis 2 - a.
+static void elastic_unit_stiffness(double h, std::vector<double> &Eab) {
+  static const int vo[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};   // Voigt index of (i, j), physical
+  Eab.assign((size_t)36 * 576, 0.0);
+  const double g[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
+  const double w = h * h * h / 8.0;
+  for (int gp = 0; gp < 8; ++gp) {
+    const double xi[3] = {g[gp >> 2 & 1], g[gp >> 1 & 1], g[gp & 1]};   // array axes 0, 1, 2
+    double G[8][3];                                                       // [corner][physical axis]
+    for (int c = 0; c < 8; ++c) {
+      const int cc[3] = {c >> 2 & 1, c >> 1 & 1, c & 1};
+      double f[3];
+      for (int a = 0; a < 3; ++a) f[a] = cc[a] ? xi[a] : 1.0 - xi[a];
+      for (int a = 0; a < 3; ++a) G[c][2 - a] = (cc[a] ? 1.0 : -1.0) / h * f[(a + 1) % 3] * f[(a + 2) % 3];
+    }
+    for (int c = 0; c < 8; ++c)
+      for (int d = 0; d < 8; ++d)
+        for (int pp = 0; pp < 3; ++pp)
+          for (int q = 0; q < 3; ++q)
+            for (int r = 0; r < 3; ++r)
+              for (int t = 0; t < 3; ++t) {
+                const int a = vo[pp][q], bb = vo[r][t];
+                Eab[((size_t)a * 6 + bb) * 576 + (size_t)(3 * c + pp) * 24 + 3 * d + r] += w * G[c][q] * G[d][t];
+              }
+  }
+}
+
+static void assemble_elastic(Operator &o, const mss_grid &g, const double *Cv, const double *rho) {
+  MSS_REQUIRE(g.dim == 3, MSS_ERR_INVALID_ARG, "the elastic operator is 3D");
+  MSS_REQUIRE(g.h > 0 && std::isfinite(g.h), MSS_ERR_INVALID_ARG, "grid step must be positive");
+  int64_t nvox = 1;
+  for (int a = 0; a < 3; ++a) {
+    MSS_REQUIRE(g.n[a] >= 1, MSS_ERR_INVALID_ARG, "voxel counts must be >= 1");
+    for (int sd = 0; sd < 2; ++sd)
+      MSS_REQUIRE(g.bc[a][sd] == MSS_DIRICHLET || g.bc[a][sd] == MSS_NEUMANN, MSS_ERR_INVALID_ARG, "bad wall type");
+    nvox *= g.n[a];
+  }
+  for (int64_t v = 0; v < nvox; ++v) {
+    const double *C = Cv + v * 36;
+    double L[36] = {0};
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) {
+        MSS_REQUIRE(std::isfinite(C[i * 6 + j]), MSS_ERR_NOT_SPD, "stiffness entries must be finite");
+        MSS_REQUIRE(std::fabs(C[i * 6 + j] - C[j * 6 + i]) <= 1e-12 * (std::fabs(C[i * 6 + j]) + std::fabs(C[j * 6 + i])),
+                    MSS_ERR_INVALID_ARG, "Voigt stiffness must be symmetric");
+      }
+    // positive definite: Cholesky of the 6 x 6 Voigt matrix
+    for (int j = 0; j < 6; ++j) {
+      double dj = C[j * 6 + j];
+      for (int k = 0; k < j; ++k) dj -= L[j * 6 + k] * L[j * 6 + k];
+      MSS_REQUIRE(dj > 0, MSS_ERR_NOT_SPD, "Voigt stiffness must be positive definite");
+      L[j * 6 + j] = std::sqrt(dj);
+      for (int i = j + 1; i < 6; ++i) {
+        double x = C[i * 6 + j];
+        for (int k = 0; k < j; ++k) x -= L[i * 6 + k] * L[j * 6 + k];
+        L[i * 6 + j] = x / L[j * 6 + j];
+      }
+    }
+    MSS_REQUIRE(rho[v] > 0 && std::isfinite(rho[v]), MSS_ERR_NOT_SPD, "rho must be positive and finite");
+  }
+  o.g = g;
+  int64_t ext[3], str[3];
+  node_strides(g, ext, str);
+  for (int a = 0; a < 3; ++a) o.nshape[a] = ext[a];
+  o.nodes = ext[0] * ext[1] * ext[2];
+  o.comps = 3;
+  // kept nodes (the scalar rule) and their numbers k; unknown 3 k + p
+  std::vector<int64_t> kept(o.nodes, -1), knode;
+  for (int64_t p = 0; p < o.nodes; ++p) {
+    const int64_t c0 = p / str[0], c1 = (p - c0 * str[0]) / str[1], c2 = p - c0 * str[0] - c1 * str[1];
+    if (wall_removed(g, 0, c0) || wall_removed(g, 1, c1) || wall_removed(g, 2, c2)) continue;
+    kept[p] = (int64_t)knode.size();
+    knode.push_back(p);
+  }
+  const int64_t nk = (int64_t)knode.size();
+  o.N = 3 * nk;
+  o.unknown.assign(o.nodes, -1);
+  o.node_of.assign(o.N, 0);
+  for (int64_t k = 0; k < nk; ++k) {
+    o.unknown[knode[k]] = 3 * k;
+    for (int p = 0; p < 3; ++p) o.node_of[3 * k + p] = knode[k];
+  }
+  // CSR structure: row 3k + p holds the three components of every kept node within one step along
+  // each axis (ascending node order = ascending columns); slot[27 k + offset] = that node's place
+  std::vector<int8_t> slot((size_t)27 * nk, -1);
+  o.A.n = o.N;
+  o.A.ptr.assign(o.N + 1, 0);
+  std::vector<int64_t> nb;
+  for (int64_t k = 0; k < nk; ++k) {
+    const int64_t p = knode[k];
+    const int64_t c[3] = {p / str[0], (p % str[0]) / str[1], p % str[1]};
+    int cnt = 0;
+    for (int o27 = 0; o27 < 27; ++o27) {
+      const int d[3] = {o27 / 9 - 1, (o27 / 3) % 3 - 1, o27 % 3 - 1};
+      bool in = true;
+      for (int a = 0; a < 3; ++a) in = in && c[a] + d[a] >= 0 && c[a] + d[a] <= g.n[a];
+      if (!in) continue;
+      const int64_t q = p + d[0] * str[0] + d[1] * str[1] + d[2] * str[2];
+      if (kept[q] < 0) continue;
+      slot[(size_t)27 * k + o27] = (int8_t)cnt++;
+      nb.push_back(kept[q]);
+    }
+    for (int pp = 0; pp < 3; ++pp) o.A.ptr[3 * k + pp + 1] = 3 * cnt;
+  }
+  for (int64_t u = 0; u < o.N; ++u) o.A.ptr[u + 1] += o.A.ptr[u];
+  o.A.col.assign(o.A.ptr[o.N], 0);
+  o.A.val.assign(o.A.ptr[o.N], 0.0);
+  {
+    int64_t off = 0;
+    for (int64_t k = 0; k < nk; ++k) {
+      const int cnt = (int)((o.A.ptr[3 * k + 1] - o.A.ptr[3 * k]) / 3);
+      for (int pp = 0; pp < 3; ++pp)
+        for (int i = 0; i < cnt; ++i)
+          for (int r = 0; r < 3; ++r) o.A.col[o.A.ptr[3 * k + pp] + 3 * i + r] = 3 * nb[off + i] + r;
+      off += cnt;
+    }
+  }
+  // A = -K voxel by voxel: K_e = sum over the symmetric Voigt pairs of C_ab (E_ab + E_ba) (a < b)
+  std::vector<double> Eab;
+  elastic_unit_stiffness(g.h, Eab);
+  std::vector<double> mass(o.nodes, 0.0), Ke(576);
+  const double mfac = g.h * g.h * g.h / 8.0;
+  int64_t v = 0;
+  for (int64_t i0 = 0; i0 < g.n[0]; ++i0)
+    for (int64_t i1 = 0; i1 < g.n[1]; ++i1)
+      for (int64_t i2 = 0; i2 < g.n[2]; ++i2, ++v) {
+        const double *C = Cv + v * 36;
+        std::fill(Ke.begin(), Ke.end(), 0.0);
+        for (int a = 0; a < 6; ++a)
+          for (int bb = a; bb < 6; ++bb) {
+            const double cab = C[a * 6 + bb];
+            if (cab == 0.0) continue;
+            const double *E1 = Eab.data() + ((size_t)a * 6 + bb) * 576;
+            const double *E2 = Eab.data() + ((size_t)bb * 6 + a) * 576;
+            if (a == bb)
+              for (int i = 0; i < 576; ++i) Ke[i] += cab * E1[i];
+            else
+              for (int i = 0; i < 576; ++i) Ke[i] += cab * (E1[i] + E2[i]);
+          }
+        const int64_t base = i0 * str[0] + i1 * str[1] + i2 * str[2];
+        int64_t cn[8];
+        for (int c = 0; c < 8; ++c) {
+          const int64_t q = base + (c >> 2 & 1) * str[0] + (c >> 1 & 1) * str[1] + (c & 1) * str[2];
+          mass[q] += rho[v] * mfac;
+          cn[c] = kept[q];
+        }
+        for (int c = 0; c < 8; ++c) {
+          if (cn[c] < 0) continue;
+          for (int d = 0; d < 8; ++d) {
+            if (cn[d] < 0) continue;
+            const int o27 = ((d >> 2 & 1) - (c >> 2 & 1) + 1) * 9 + ((d >> 1 & 1) - (c >> 1 & 1) + 1) * 3 +
+                            ((d & 1) - (c & 1) + 1);
+            const int sl = slot[(size_t)27 * cn[c] + o27];
+            for (int pp = 0; pp < 3; ++pp) {
+              double *row = o.A.val.data() + o.A.ptr[3 * cn[c] + pp] + 3 * sl;
+              for (int r = 0; r < 3; ++r) row[r] -= Ke[(size_t)(3 * c + pp) * 24 + 3 * d + r];
+            }
+          }
+        }
+      }
+  o.B.assign(o.N, 0.0);
+  for (int64_t k = 0; k < nk; ++k)
+    for (int pp = 0; pp < 3; ++pp) o.B[3 * k + pp] = mass[knode[k]];
+}
+
 static double lambda_max_lanczos(const Operator &o, double tol) {
   // Lanczos on B^{-1/2}(-A)B^{-1/2}; returns the largest Ritz value once it settles.
   const int64_t N = o.N;
@@ -543,6 +713,16 @@ mss_status mss_assemble(const mss_grid *g, const double *sigma, const double *rh
   });
 }
 
+mss_status mss_assemble_elastic(const mss_grid *g, const double *C, const double *rho, mss_operator **out) {
+  return guard([&] {
+    const Range nvtx_range("mss_assemble_elastic");
+    MSS_REQUIRE(g && C && rho && out, MSS_ERR_INVALID_ARG, "null argument");
+    auto h = std::make_unique<mss_operator>();
+    assemble_elastic(h->o, *g, C, rho);
+    *out = h.release();
+  });
+}
+
 mss_status mss_operator_info(const mss_operator *op, int64_t info[2]) {
   return guard([&] {
     MSS_REQUIRE(op && info, MSS_ERR_INVALID_ARG, "null argument");
@@ -592,6 +772,8 @@ mss_status mss_partition_create(const mss_operator *op, const double *sigma, con
     const Range nvtx_range("mss_partition_create");
     MSS_REQUIRE(op && sigma && rho && cell && out && n_io >= 0 && (n_io == 0 || io_nodes), MSS_ERR_INVALID_ARG,
                 "null argument");
+    MSS_REQUIRE(op->o.comps == 1, MSS_ERR_INVALID_ARG,
+                "the partition takes one unknown per node (vector faces of the elastic operator are not built)");
     auto h = std::make_unique<mss_partition>();
     partition(h->p, op->o, sigma, rho, cell, n_io, io_nodes);
     *out = h.release();
