@@ -301,7 +301,8 @@ typedef struct mss_sim mss_sim;
  * raised to that floor; stored as one K x K matrix W = L + L^T - diag(L), so the coefficient bytes
  * do not change.  Rounding the entries of a nearly singular Gamma^m -- a cell without a Dirichlet
  * node, whose constant mode makes it semidefinite, Eq. intrtstep_td with Lemma lemStil -- to FP32
- * can make it indefinite; a rounded factor keeps L L^T semidefinite.  Schedules GRAPH and PERSIST.
+ * can make it indefinite; a rounded factor keeps L L^T semidefinite.  With MSS_FP32: schedules
+ * GRAPH and PERSIST, and GRAPH_STREAM (the wide streamed kernel) when the source tile is 16.
  * COEF_NOT_SPD if a Gamma^m is indefinite beyond -1e-8 of its scale).  Needs I/O set on the ROM
  * (n_src >= 1).
  * The sim copies what it needs from the ROM (the ROM may be destroyed afterwards).
