@@ -58,7 +58,9 @@ enum {
 enum { MSS_DIRICHLET = 0, MSS_NEUMANN = 1 };
 /* Precisions of the on-line stage.  MSS_FP32_TC: FP32 state, cell products on the tensor cores
  * (tcgen05, BF16 operands split into hi + lo parts, three products, FP32 accumulation);
- * MSS_BF16_TC: the same with one BF16 product.  Tensor-core modes need K_i <= 128. */
+ * MSS_BF16_TC: the same with one BF16 product; both need K_i <= 128.  MSS_TF32_TC: FP32 state and
+ * coefficients, cell products on the tensor cores as TF32 with both operands split hi + lo (three
+ * products, FP32-class), the last coefficient applied as its Cholesky factor; K_i <= 384. */
 enum { MSS_FP64 = 0, MSS_FP32 = 1, MSS_FP32_TC = 2, MSS_BF16_TC = 3, MSS_TF32_TC = 4 };
 
 const char *mss_status_string(mss_status s);
