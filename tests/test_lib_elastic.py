@@ -111,3 +111,25 @@ def test_elastic_operator_refusals(P):
     L = P.Operator.elastic(g, C, rho)
     with pytest.raises(P.MssError):            # one unknown per node: the partition refuses it
         P.Partition(L, (1, 1, 1), np.zeros((0, 3), np.int32))
+
+
+def test_patch_test_linear_fields(P):
+    """A linear displacement u = E x carries exactly the strain energy of its uniform strain:
+    -u^T A u = V e^T C e, e the Voigt strain (xx, yy, zz, 2yz, 2xz, 2xy) of sym(E), V the block's
+    volume, on a free block with a different anisotropic stiffness in every voxel (the element
+    integration is exact for constant C per voxel, so the sum over voxels is exact too)."""
+    n = (2, 2, 3)
+    h = 0.4
+    g = synth.Grid(n=n, h=h, bc=(("N", "N"), ("N", "N"), ("N", "N")))
+    C, rho = _random_aniso(n, 11)
+    L = P.Operator.elastic(g, C, rho)
+    A, _, _, _ = _dense(L)
+    pts = np.array([[i2 * h, i1 * h, i0 * h] for i0, i1, i2 in np.ndindex(n[0] + 1, n[1] + 1, n[2] + 1)])
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        E = rng.standard_normal((3, 3))
+        u = (pts @ E.T).ravel()
+        eps = 0.5 * (E + E.T)
+        e = np.array([eps[0, 0], eps[1, 1], eps[2, 2], 2 * eps[1, 2], 2 * eps[0, 2], 2 * eps[0, 1]])
+        exact = sum(h ** 3 * e @ C[idx] @ e for idx in np.ndindex(*n))
+        assert abs(-u @ A @ u - exact) <= 1e-11 * abs(exact)
