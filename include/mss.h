@@ -426,6 +426,16 @@ typedef struct mss_fine mss_fine;
  * state layout [node][source].  precision: MSS_FP64 or MSS_FP32. */
 mss_status mss_fine_create(const mss_operator *op, int32_t precision, double tau, int32_t n_src,
                            const int32_t *src_nodes, int32_t n_rcv, const int32_t *rcv_nodes, mss_fine **out);
+/* The same leapfrog for any operator, the elastic one included (Section 7's elastic experiment uses
+ * it as the reference), on the operator's CSR rows: point sources and receivers at unknowns
+ * (host, int64, 0 <= u < N; for the elastic operator unknown 3k + p is component p of kept node k),
+ * unit weights; state layout [unknown][source].  One thread per (row, source) forms the row's
+ * product in column order.  precision: MSS_FP64 or MSS_FP32.  mss_fine_reset / step / destroy
+ * apply unchanged.  Errors: INVALID_ARG (counts, unknowns out of range, precision), CFL (tau <= 0),
+ * CUDA, OOM. */
+mss_status mss_fine_create_unknowns(const mss_operator *op, int32_t precision, double tau, int32_t n_src,
+                                    const int64_t *src_unknowns, int32_t n_rcv, const int64_t *rcv_unknowns,
+                                    mss_fine **out);
 mss_status mss_fine_reset(mss_fine *f, void *stream);
 /* Same waveform/trace conventions as mss_step. */
 mss_status mss_fine_step(mss_fine *f, int64_t n_steps, const double *waveform, void *traces, int32_t use_graph,

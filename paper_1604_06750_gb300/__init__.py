@@ -111,6 +111,7 @@ _SIGS = [
     ("mss_sim_load_state", C.c_int32, [_P, _P, _P, C.c_int64]),
     ("mss_sim_destroy", None, [_P]),
     ("mss_fine_create", C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, _P, C.c_int32, _P, _P]),
+    ("mss_fine_create_unknowns", C.c_int32, [_P, C.c_int32, C.c_double, C.c_int32, _P, C.c_int32, _P, _P]),
     ("mss_fine_reset", C.c_int32, [_P, _P]),
     ("mss_fine_step", C.c_int32, [_P, C.c_int64, _P, _P, C.c_int32, _P]),
     ("mss_fine_destroy", None, [_P]),
@@ -716,6 +717,19 @@ class FineSim(_Handle):
                                      int(r.shape[0]), _ptr(r), C.byref(self._h)))
         self.precision = precision
         self.n_src, self.n_rcv = int(s.shape[0]), int(r.shape[0])
+
+    @classmethod
+    def at_unknowns(cls, op: Operator, precision: int, tau: float, src_unknowns, rcv_unknowns) -> "FineSim":
+        """mss_fine_create_unknowns: the CSR leapfrog, sources and receivers given as unknowns."""
+        self = cls.__new__(cls)
+        _Handle.__init__(self)
+        s = _arr(src_unknowns, np.int64)
+        r = _arr(rcv_unknowns, np.int64)
+        _check(lib().mss_fine_create_unknowns(op._h, int(precision), C.c_double(tau), int(s.shape[0]), _ptr(s),
+                                              int(r.shape[0]), _ptr(r), C.byref(self._h)))
+        self.precision = precision
+        self.n_src, self.n_rcv = int(s.shape[0]), int(r.shape[0])
+        return self
 
     def reset(self, stream=None):
         _check(lib().mss_fine_reset(self._h, _stream(stream)))

@@ -138,6 +138,43 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_v(const FineArgs<T> a, co
   }
 }
 
+// Same leapfrog on the operator's CSR rows, for any operator (the elastic one has 3 unknowns per
+// node and a 27-node stencil): state [unknown][source]; thread (row u, source s) forms the row's
+// product in column order; the extra threads past N S write the traces.
+template <typename T>
+struct FineCsrArgs {
+  const int64_t *rp, *col;
+  const T *val, *binv;
+  const int64_t *src, *rcv;   // unknowns
+  T *u0, *u1;
+  int64_t N;
+  int S, R;
+  T tau2;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kFineThreads) k_fine_csr(const FineCsrArgs<T> a, const int cur, const double *w,
+                                                           T *traces) {
+  const int64_t total = a.N * a.S;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const T *u = cur ? a.u1 : a.u0;
+  T *uo = cur ? a.u0 : a.u1;
+  if (i < total) {
+    const int64_t r = i / a.S;
+    const int s = (int)(i - r * a.S);
+    T acc = T(0);
+    for (int64_t k = a.rp[r]; k < a.rp[r + 1]; ++k) acc += a.val[k] * u[a.col[k] * a.S + s];
+    if (a.src[s] == r) acc -= (T)(*w);
+    uo[i] = T(2) * u[i] - uo[i] + a.tau2 * a.binv[r] * acc;
+  } else {
+    const int64_t j = i - ((total + kFineThreads - 1) / kFineThreads) * kFineThreads;
+    if (j < 0 || j >= (int64_t)a.R * a.S) return;
+    const int64_t r = j / a.S;
+    const int s = (int)(j - r * a.S);
+    traces[j] = u[a.rcv[r] * a.S + s];
+  }
+}
+
 struct FineGraphKey {
   int64_t n;
   const void *w, *t;
@@ -157,6 +194,9 @@ struct mss_fine {
   int64_t nodes = 0, str[3] = {0, 0, 0}, steps = 0;
   double tau = 0;
   mss::DevMem diag, cp[3], binv, src, rcv, u[2];
+  int csr = 0;                      // 1: the CSR kernel on unknowns (mss_fine_create_unknowns)
+  int64_t N = 0;
+  mss::DevMem rp, col, val;
   std::map<mss::FineGraphKey, cudaGraphExec_t> graphs;
   cudaStream_t cap = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -195,6 +235,29 @@ static FineArgs<T> fine_args(const mss_fine &f) {
 
 template <typename T>
 static void fine_launch(mss_fine &f, int64_t n, const double *w, T *traces, cudaStream_t st) {
+  if (f.csr) {
+    FineCsrArgs<T> c;
+    c.rp = f.rp.as<int64_t>();
+    c.col = f.col.as<int64_t>();
+    c.val = f.val.as<T>();
+    c.binv = f.binv.as<T>();
+    c.src = f.src.as<int64_t>();
+    c.rcv = f.rcv.as<int64_t>();
+    c.u0 = f.u[0].as<T>();
+    c.u1 = f.u[1].as<T>();
+    c.N = f.N;
+    c.S = f.S;
+    c.R = f.R;
+    c.tau2 = (T)(f.tau * f.tau);
+    const int64_t nb = (f.N * f.S + kFineThreads - 1) / kFineThreads + ((int64_t)f.R * f.S + kFineThreads - 1) / kFineThreads;
+    int cur = f.cur;
+    for (int64_t j = 0; j < n; ++j) {
+      k_fine_csr<T><<<(unsigned)nb, kFineThreads, 0, st>>>(c, cur, w + j, traces + j * (int64_t)f.R * f.S);
+      cur ^= 1;
+    }
+    MSS_CUDA(cudaGetLastError());
+    return;
+  }
   const FineArgs<T> a = fine_args<T>(f);
   constexpr int VN = FineVec<T>::n;
   const bool vec = f.S % VN == 0;
@@ -310,6 +373,51 @@ mss_status mss_fine_create(const mss_operator *op, int32_t precision, double tau
     const size_t es = precision == MSS_FP64 ? 8 : 4;
     for (int l = 0; l < 2; ++l) {
       f->u[l].alloc((size_t)o.nodes * n_src * es);
+      MSS_CUDA(cudaMemset(f->u[l].p, 0, f->u[l].bytes));
+    }
+    *out = f.release();
+  });
+}
+
+mss_status mss_fine_create_unknowns(const mss_operator *op, int32_t precision, double tau, int32_t n_src,
+                                    const int64_t *src_unknowns, int32_t n_rcv, const int64_t *rcv_unknowns,
+                                    mss_fine **out) {
+  return guard([&] {
+    MSS_REQUIRE(op && out && n_src >= 1 && src_unknowns && n_rcv >= 0 && (n_rcv == 0 || rcv_unknowns),
+                MSS_ERR_INVALID_ARG, "bad argument");
+    MSS_REQUIRE(precision == MSS_FP64 || precision == MSS_FP32, MSS_ERR_INVALID_ARG, "precision must be FP64 or FP32");
+    MSS_REQUIRE(tau > 0 && std::isfinite(tau), MSS_ERR_CFL, "tau must be positive");
+    const Operator &o = op->o;
+    for (int32_t j = 0; j < n_src; ++j)
+      MSS_REQUIRE(src_unknowns[j] >= 0 && src_unknowns[j] < o.N, MSS_ERR_INVALID_ARG, "source unknown out of range");
+    for (int32_t j = 0; j < n_rcv; ++j)
+      MSS_REQUIRE(rcv_unknowns[j] >= 0 && rcv_unknowns[j] < o.N, MSS_ERR_INVALID_ARG, "receiver unknown out of range");
+    auto f = std::make_unique<mss_fine>();
+    MSS_CUDA(cudaStreamCreateWithFlags(&f->cap, cudaStreamNonBlocking));
+    MSS_CUDA(cudaEventCreateWithFlags(&f->ev_in, cudaEventDisableTiming));
+    MSS_CUDA(cudaEventCreateWithFlags(&f->ev_out, cudaEventDisableTiming));
+    f->prec = precision;
+    f->csr = 1;
+    f->N = o.N;
+    f->S = n_src;
+    f->R = n_rcv;
+    f->tau = tau;
+    upload(f->rp, o.A.ptr);
+    upload(f->col, o.A.col);
+    std::vector<double> binv(o.N);
+    for (int64_t u = 0; u < o.N; ++u) binv[u] = 1.0 / o.B[u];
+    if (precision == MSS_FP64) {
+      upload(f->val, o.A.val);
+      upload(f->binv, binv);
+    } else {
+      upload(f->val, std::vector<float>(o.A.val.begin(), o.A.val.end()));
+      upload(f->binv, std::vector<float>(binv.begin(), binv.end()));
+    }
+    upload(f->src, std::vector<int64_t>(src_unknowns, src_unknowns + n_src));
+    upload(f->rcv, n_rcv ? std::vector<int64_t>(rcv_unknowns, rcv_unknowns + n_rcv) : std::vector<int64_t>(1, 0));
+    const size_t es = precision == MSS_FP64 ? 8 : 4;
+    for (int l = 0; l < 2; ++l) {
+      f->u[l].alloc((size_t)o.N * n_src * es);
       MSS_CUDA(cudaMemset(f->u[l].p, 0, f->u[l].bytes));
     }
     *out = f.release();
